@@ -1,0 +1,223 @@
+"""Seeded synthetic inputs shaped like the paper's regression and leverage workloads.
+
+This module is shared by the tests, the CPU oracle and the benchmark.  It holds
+no arithmetic of the sketching method (no hashing, no bucketing, no sketch):
+only random sparse / dense matrices, right-hand sides and Gaussian matrices.
+Everything is drawn with torch generators seeded from the documented integer
+seeds, on the device the caller names (``"cpu"`` for the CPU test suite,
+``"cuda"`` for the full-size workloads, which would take minutes on the host).
+A given (function, arguments, device) always returns the same arrays.
+
+Recipes (the tall regression setting of Section 7 and the leverage setting of
+Section 6 of the paper):
+
+* ``csr_fixed_k``: every row has exactly ``k`` distinct columns, sampled without
+  replacement with probabilities ``p`` over the ``d`` columns (uniform, or
+  Zipf(s): p_c proportional to c^-s for c = 1..d).  Sampling without
+  replacement uses exponential keys (Efraimidis and Spirakis, 2006): column c
+  gets E_c / p_c with E_c ~ Exp(1) and the k smallest keys win, which has the
+  same law as drawing columns one at a time and rejecting repeats.  Columns are
+  stored ascending within a row.  Values are N(0,1) drawn in float64 and
+  stored as float32.
+* ``csr_random_lengths``: row lengths uniform in [kmin, kmax] (optionally a
+  fraction of empty rows), uniform distinct columns.
+* ``dense_lowrank``: A = U diag(sigma) V^T with U (n x d) and V (d x d) the
+  sign-fixed Q factors of Gaussian matrices (Haar distributed), float32.
+* ``rhs``: b = A x0 + noise * N(0,1), x0 ~ N(0,1)^d, float32.
+* ``gaussian``: G ~ N(0,1)^{d x k}, float64.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+__all__ = [
+    "CSR",
+    "csr_fixed_k",
+    "csr_uniform",
+    "csr_zipf",
+    "csr_random_lengths",
+    "rhs",
+    "dense_lowrank",
+    "dense_gaussian",
+    "gaussian",
+    "geometric_sigma",
+    "zipf_probs",
+]
+
+_CHUNK = 1 << 18
+
+
+def _gen(seed, device):
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return g
+
+
+class CSR:
+    """CSR matrix with int32 row_ptr / col and float32 val torch tensors, shape (n, d)."""
+
+    def __init__(self, n, d, row_ptr, col, val):
+        self.n = int(n)
+        self.d = int(d)
+        self.row_ptr = row_ptr.to(torch.int32).contiguous()
+        self.col = col.to(torch.int32).contiguous()
+        self.val = val.to(torch.float32).contiguous()
+
+    @property
+    def nnz(self):
+        return int(self.col.numel())
+
+    @property
+    def device(self):
+        return self.val.device
+
+    def to(self, device):
+        return CSR(self.n, self.d, self.row_ptr.to(device), self.col.to(device), self.val.to(device))
+
+    def numpy(self):
+        """(row_ptr, col, val) as host numpy arrays."""
+        return (self.row_ptr.cpu().numpy(), self.col.cpu().numpy(), self.val.cpu().numpy())
+
+    def rows(self, r0, r1):
+        """The sub-matrix of rows [r0, r1) as a new CSR (row_ptr rebased to 0)."""
+        rp = self.row_ptr[r0:r1 + 1].to(torch.int64)
+        s, e = int(rp[0]), int(rp[-1])
+        return CSR(r1 - r0, self.d, (rp - s).to(torch.int32), self.col[s:e], self.val[s:e])
+
+    def to_dense(self, dtype=torch.float64):
+        out = torch.zeros(self.n, self.d, dtype=dtype, device=self.device)
+        lens = (self.row_ptr[1:] - self.row_ptr[:-1]).to(torch.int64)
+        rows = torch.repeat_interleave(torch.arange(self.n, device=self.device), lens)
+        out.index_put_((rows, self.col.to(torch.int64)), self.val.to(dtype), accumulate=True)
+        return out
+
+    def matvec(self, x):
+        """y = A x in float64 (x of length d)."""
+        x = torch.as_tensor(x, dtype=torch.float64, device=self.device)
+        lens = (self.row_ptr[1:] - self.row_ptr[:-1]).to(torch.int64)
+        rows = torch.repeat_interleave(torch.arange(self.n, device=self.device), lens)
+        prod = self.val.to(torch.float64) * x[self.col.to(torch.int64)]
+        y = torch.zeros(self.n, dtype=torch.float64, device=self.device)
+        y.index_add_(0, rows, prod)
+        return y
+
+
+def zipf_probs(d, s):
+    c = torch.arange(1, d + 1, dtype=torch.float64)
+    p = c ** (-float(s))
+    return p / p.sum()
+
+
+def csr_fixed_k(n, d, k, p, seed, device="cpu"):
+    """n x d CSR with exactly k distinct columns per row drawn without replacement from p."""
+    if not 0 <= k <= d:
+        raise ValueError("need 0 <= k <= d")
+    g = _gen(seed, device)
+    inv_p = (1.0 / torch.as_tensor(p, dtype=torch.float64)).to(torch.float32).to(device)
+    col = torch.empty(n * k, dtype=torch.int32, device=device)
+    for s in range(0, n, _CHUNK):
+        e = min(n, s + _CHUNK)
+        keys = torch.empty(e - s, d, dtype=torch.float32, device=device).exponential_(generator=g)
+        keys *= inv_p
+        idx = keys.topk(k, dim=1, largest=False).indices.sort(dim=1).values
+        col[s * k:e * k] = idx.reshape(-1).to(torch.int32)
+    val = torch.randn(n * k, dtype=torch.float64, device=device, generator=g).to(torch.float32)
+    row_ptr = torch.arange(n + 1, dtype=torch.int64, device=device) * k
+    return CSR(n, d, row_ptr.to(torch.int32), col, val)
+
+
+def csr_uniform(n, d, k, seed, device="cpu"):
+    """Exactly k distinct uniformly chosen columns per row, N(0,1) values."""
+    return csr_fixed_k(n, d, k, torch.full((d,), 1.0 / d, dtype=torch.float64), seed, device)
+
+
+def csr_zipf(n, d, k, s, seed, device="cpu"):
+    """Exactly k distinct columns per row from Zipf(s) over d columns, N(0,1) values."""
+    return csr_fixed_k(n, d, k, zipf_probs(d, s), seed, device)
+
+
+def csr_random_lengths(n, d, kmin, kmax, seed, empty_frac=0.0, device="cpu"):
+    """Row lengths uniform in [kmin, kmax], a fraction ``empty_frac`` of rows empty."""
+    g = _gen(seed, device)
+    lens = torch.randint(kmin, kmax + 1, (n,), generator=g, device=device)
+    if empty_frac > 0:
+        lens = torch.where(torch.rand(n, generator=g, device=device) < empty_frac,
+                           torch.zeros_like(lens), lens)
+    lens = lens.clamp(max=d)
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    row_ptr[1:] = torch.cumsum(lens, 0)
+    nnz = int(row_ptr[-1])
+    # per row: the first len_i columns of a uniformly random key order (distinct, uniform)
+    col = torch.empty(nnz, dtype=torch.int32, device=device)
+    kmax_eff = int(lens.max()) if n else 0
+    for s in range(0, n, _CHUNK):
+        e = min(n, s + _CHUNK)
+        if kmax_eff == 0:
+            break
+        keys = torch.rand(e - s, d, generator=g, device=device)
+        idx = keys.topk(kmax_eff, dim=1, largest=False).indices
+        L = lens[s:e]
+        take = torch.arange(kmax_eff, device=device)[None, :] < L[:, None]
+        big = torch.where(take, idx, torch.full_like(idx, d))
+        big = big.sort(dim=1).values
+        col[int(row_ptr[s]):int(row_ptr[e])] = big[take].to(torch.int32)
+    val = torch.randn(nnz, dtype=torch.float64, device=device, generator=g).to(torch.float32)
+    return CSR(n, d, row_ptr.to(torch.int32), col, val)
+
+
+def rhs(A, noise, seed):
+    """b = A x0 + noise * N(0,1) with x0 ~ N(0,1)^d.  Returns (b float32, x0 float64).
+
+    ``A`` is a CSR or a dense float32 tensor; b lives on A's device.
+    """
+    dev = A.device
+    g = _gen(seed, dev)
+    if isinstance(A, CSR):
+        d = A.d
+        x0 = torch.randn(d, dtype=torch.float64, device=dev, generator=g)
+        y = A.matvec(x0)
+        n = A.n
+    else:
+        n, d = A.shape
+        x0 = torch.randn(d, dtype=torch.float64, device=dev, generator=g)
+        y = torch.empty(n, dtype=torch.float64, device=dev)
+        for s in range(0, n, _CHUNK):
+            e = min(n, s + _CHUNK)
+            y[s:e] = A[s:e].to(torch.float64) @ x0
+    b = y + noise * torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+    return b.to(torch.float32), x0
+
+
+def _haar(rows, cols, g, device):
+    q, r = torch.linalg.qr(torch.randn(rows, cols, dtype=torch.float64, device=device, generator=g))
+    s = torch.sign(torch.diagonal(r))
+    s[s == 0] = 1.0
+    return q * s
+
+
+def geometric_sigma(d, lo):
+    """sigma_j = lo^((j-1)/(d-1)), j = 1..d: geometric from 1 down to lo (float64)."""
+    if d == 1:
+        return torch.ones(1, dtype=torch.float64)
+    return torch.tensor(float(lo), dtype=torch.float64) ** (torch.arange(d, dtype=torch.float64) / (d - 1))
+
+
+def dense_lowrank(n, d, sigma, seed, device="cpu"):
+    """A = U diag(sigma) V^T with U (n x d) and V (d x d) Haar; float32 (n, d) row-major."""
+    g = _gen(seed, device)
+    V = _haar(d, d, g, device)
+    U = _haar(n, d, g, device)
+    A = (U * torch.as_tensor(sigma, dtype=torch.float64, device=device)) @ V.T
+    return A.to(torch.float32).contiguous()
+
+
+def dense_gaussian(n, d, seed, device="cpu"):
+    g = _gen(seed, device)
+    return torch.randn(n, d, dtype=torch.float64, device=device, generator=g).to(torch.float32)
+
+
+def gaussian(d, k, seed, device="cpu"):
+    """G ~ N(0,1)^{d x k}, float64 (the Johnson-Lindenstrauss matrix of Section 6)."""
+    g = _gen(seed, device)
+    return torch.randn(d, k, dtype=torch.float64, device=device, generator=g)
