@@ -1,0 +1,186 @@
+/*
+ * cw.h - C ABI of the GB300 (sm_103a) sparse-embedding library.
+ *
+ * The library applies the sparse embedding matrix S = Phi D of Clarkson and
+ * Woodruff, "Low Rank Approximation and Regression in Input Sparsity Time"
+ * (Section 2): Phi is t x n with a single 1 per column, Phi[h(i), i] = 1, and
+ * D = diag(sigma) holds random signs, so S has one +-1 per column and
+ * SA = Phi D A is computed in O(nnz(A)) (Theorem 1).  On top of SA it solves
+ * least squares by sketch-and-solve (Theorem "lin reg", with the QR solve of
+ * the proof of Theorem "renRegAlg"), by LSQR preconditioned with R from the
+ * QR of SA (Section 7.6, Theorem "it reg"), and it approximates leverage
+ * scores as row norms of A R^-1 Pi_2 (Section 6, Theorem "icml").
+ *
+ * The random map.  The paper draws h uniformly and the signs independently;
+ * this library fixes a seeded 4-wise independent family.  With p = 2^61 - 1
+ * and the SplitMix64 stream (Steele, Lea and Flood, 2014) started at `seed`,
+ * each 64-bit draw z gives a coefficient c = z & (2^61 - 1) (the value p is
+ * rejected and drawn again); draws 0..3 are c0..c3 of the bucket polynomial,
+ * draws 4..7 those of the sign polynomial, g(x) = c3 x^3 + c2 x^2 + c1 x + c0
+ * mod p at x = the 0-based row index, and
+ *     h(i) = g_bucket(i) mod m,    sigma(i) = +1 if g_sign(i) is even else -1.
+ * S is unscaled (entries exactly +-1), as in the paper's definition.
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers owned by the caller unless marked
+ *    "host".  Nothing is retained after the call returns (or, for
+ *    asynchronous calls, after the stream reaches the call's end).
+ *  - Matrices are row-major.  CSR uses int32 row_ptr[n+1] and col[nnz] and
+ *    float32 val[nnz]; column indices within a row must be distinct and in
+ *    [0, d); row_ptr must start at 0 and be non-decreasing.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
+ *    stream).  Calls without host outputs are asynchronous; calls with host
+ *    outputs synchronise `stream` before returning.
+ *  - Scratch memory is allocated stream-ordered (cudaMallocAsync) and freed
+ *    stream-ordered before the call returns.
+ *  - Arguments are validated on the host before any launch; a bad argument
+ *    returns a negative status and enqueues nothing.  Violations only visible
+ *    on the device (a column index out of range, a repeated column in a row, a
+ *    decreasing row_ptr, a non-finite value where one is rejected) set a
+ *    per-device sticky flag that cw_device_status() reports.
+ *  - Results are deterministic: the same inputs, seed and sizes give bitwise
+ *    identical outputs (fixed summation orders, no floating-point atomics).
+ */
+#ifndef CW_H
+#define CW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *cw_stream; /* identical to cudaStream_t */
+
+/* Status codes returned by every entry point. */
+enum {
+    CW_OK = 0,
+    CW_ERR_ARG = -1,       /* null pointer, bad flag, bad tolerance             */
+    CW_ERR_SHAPE = -2,     /* inconsistent or unsupported sizes                 */
+    CW_ERR_OVERFLOW = -3,  /* a size exceeds the library's index range          */
+    CW_ERR_CUDA = -4,      /* a CUDA runtime call or launch failed              */
+    CW_ERR_RANK = -5,      /* R has |R_jj| <= d * 2^-52 * max|R_ii|             */
+    CW_ERR_NOCONV = -6,    /* LSQR reached max_iter without meeting its test    */
+    CW_ERR_TIMEOUT = -7,   /* a bounded device wait expired                     */
+    CW_ERR_NONFINITE = -8, /* NaN / Inf met where a finite value is required    */
+    CW_ERR_DEVICE = -9     /* the device flagged invalid input (see above)      */
+};
+
+/* CSR matrix, n x d with nnz stored entries (all device pointers). */
+typedef struct {
+    int64_t n, d, nnz;
+    const int32_t *row_ptr; /* n + 1 entries, row_ptr[0] = 0, row_ptr[n] = nnz */
+    const int32_t *col;     /* nnz entries in [0, d), distinct within a row    */
+    const float *val;       /* nnz entries                                     */
+} cw_csr;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *cw_status_string(int status);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int cw_version(void);
+
+/*
+ * Synchronise `stream`, then return and clear the calling device's sticky
+ * device-side flag: CW_OK, or CW_ERR_DEVICE if some kernel of this library
+ * met invalid input since the last call, or CW_ERR_CUDA if the sync failed.
+ */
+int cw_device_status(cw_stream stream);
+
+/*
+ * cw_hash - the map (h, sigma) defining S (paper Section 2).
+ * bucket[k] = h(i0 + k) in [0, m), sign[k] = sigma(i0 + k) in {+1, -1} for
+ * k < count.  Requirements: m >= 1, 0 <= i0, i0 + count <= 2^62.  Either
+ * output may be NULL.  Asynchronous.
+ */
+int cw_hash(uint64_t seed, int64_t m, int64_t i0, int64_t count, int32_t *bucket, int8_t *sign,
+            cw_stream stream);
+
+/*
+ * cw_sketch_csr - SA = S A and Sb = S b for CSR A (paper Section 2; Theorem
+ * "lin reg" sketches A and b with the same S).
+ * A: n x d CSR (n <= 2^31 - 1, nnz <= 2^31 - 1, 1 <= d <= 2^20).
+ * b: n floats or NULL.  m: sketch rows, 1 <= m <= 2^19.
+ * SA: m x d floats, row-major, fully overwritten (empty buckets give zeros).
+ * Sb: m floats, overwritten; may be NULL (ignored when b is NULL).
+ * Each SA entry is the float32 sum of its bucket's signed entries in a fixed
+ * order.  Asynchronous.
+ */
+int cw_sketch_csr(const cw_csr *A, const float *b, int64_t m, uint64_t seed, float *SA,
+                  float *Sb, cw_stream stream);
+
+/*
+ * cw_sketch_csr_rows - as cw_sketch_csr for a row shard: local row i of A is
+ * global row i0 + i of the full matrix and is hashed with that global index,
+ * so the sum over shards of their SA equals the SA of the whole matrix
+ * (the exchange step when rows are spread over several devices).
+ */
+int cw_sketch_csr_rows(const cw_csr *A, int64_t i0, const float *b, int64_t m, uint64_t seed,
+                       float *SA, float *Sb, cw_stream stream);
+
+/*
+ * cw_sketch_dense - SA and Sb for dense row-major A (n x d, leading dimension
+ * lda >= d).  Same limits and outputs as cw_sketch_csr.  Asynchronous.
+ */
+int cw_sketch_dense(const float *A, int64_t n, int64_t d, int64_t lda, const float *b, int64_t m,
+                    uint64_t seed, float *SA, float *Sb, cw_stream stream);
+
+/* cw_sketch_vec - Sx for an n-vector x (the d = 1 case).  Asynchronous. */
+int cw_sketch_vec(const float *x, int64_t n, int64_t m, uint64_t seed, float *Sx,
+                  cw_stream stream);
+
+/*
+ * cw_qr - Householder QR of the m x d float32 matrix SA in float64 (the
+ * factorisation used in the proof of Theorem "renRegAlg").
+ * R: d x d row-major float64, upper triangular with a positive diagonal.
+ * c: d float64, c = Q^T Sb (skipped when Sb or c is NULL).
+ * Requires 1 <= d <= m, d <= 1024.  Returns CW_ERR_RANK for a numerically
+ * rank-deficient SA (R still written).  Synchronises the stream.
+ */
+int cw_qr(const float *SA, int64_t m, int64_t d, const float *Sb, double *R, double *c,
+          cw_stream stream);
+
+/*
+ * cw_solve_sketch - sketch-and-solve least squares (Theorem "lin reg"):
+ * x' = argmin_x ||S A x - S b||_2 computed as R^-1 Q^T S b.
+ * x: d float64 (device).  R: d x d float64 (device, upper, positive diagonal)
+ * or NULL.  Requires d <= m.  Synchronises the stream.
+ */
+int cw_solve_sketch(const cw_csr *A, const float *b, int64_t m, uint64_t seed, double *x,
+                    double *R, cw_stream stream);
+
+/* cw_solve_sketch_dense - as cw_solve_sketch for dense row-major A. */
+int cw_solve_sketch_dense(const float *A, int64_t n, int64_t d, int64_t lda, const float *b,
+                          int64_t m, uint64_t seed, double *x, double *R, cw_stream stream);
+
+/*
+ * cw_lsqr_precond - least squares by LSQR on y -> A R^-1 y with R from the
+ * QR of SA (Section 7.6, Theorem "it reg"), started at the sketch-and-solve
+ * solution, returning x = R^-1 y.
+ * Stops when ||(A R^-1)^T r|| / (||A R^-1||_F ||r||) <= rtol or
+ * ||r|| <= rtol (||b|| + ||A R^-1||_F ||y||) (LSQR's own estimates of the
+ * norms except ||b|| and ||y||).  rtol > 0, max_iter >= 0.
+ * x: d float64 (device).  iters, final_test: host (may be NULL); final_test
+ * receives the last value of the first ratio.  Returns CW_ERR_NOCONV (with x
+ * written) when max_iter iterations did not meet the test.  Synchronises.
+ */
+int cw_lsqr_precond(const cw_csr *A, const float *b, int64_t m, uint64_t seed, double rtol,
+                    int32_t max_iter, double *x, int32_t *iters, double *final_test,
+                    cw_stream stream);
+
+/*
+ * cw_leverage - approximate leverage scores (Section 6, Theorem "icml"):
+ * lev[i] = ||(A R^-1 G)_i||^2 / k, with R from the QR of SA (S with m rows
+ * and `seed`) and G a d x k float64 Gaussian matrix supplied by the caller
+ * (Pi_2 = G / sqrt(k)).  A: dense row-major n x d, lda >= d, d <= m.
+ * lev: n floats.  Synchronises the stream.
+ */
+int cw_leverage(const float *A, int64_t n, int64_t d, int64_t lda, int64_t m, uint64_t seed,
+                int32_t k, const double *G, float *lev, cw_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CW_H */

@@ -1,0 +1,250 @@
+"""Python binding of libcw.so, the sm_103a sparse-embedding (CountSketch) library.
+
+Argument marshalling only: every step of every call runs in the library's CUDA
+kernels.  Tensors must already live on the current CUDA device; the current
+torch stream is passed to the library.  The functions keep the C names of
+``include/cw.h`` (cw_sketch_csr, cw_solve_sketch, ...), raise ``CWError`` on a
+non-zero status, and fail loudly when the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import _build
+
+__all__ = [
+    "CWError", "lib", "load", "status_string", "device_status",
+    "cw_hash", "cw_sketch_csr", "cw_sketch_csr_rows", "cw_sketch_dense", "cw_sketch_vec",
+    "cw_qr", "cw_solve_sketch", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
+    "EXPORTS", "HEADER",
+]
+
+HEADER = os.path.join(_build.ROOT, "include", "cw.h")
+EXPORTS = (
+    "cw_status_string", "cw_version", "cw_device_status", "cw_hash", "cw_sketch_csr",
+    "cw_sketch_csr_rows", "cw_sketch_dense", "cw_sketch_vec", "cw_qr", "cw_solve_sketch",
+    "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
+)
+
+
+class CWError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = int(status)
+        super().__init__("%s: %s" % (where, status_string(status)))
+
+
+class _CSR(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+_i64, _u64, _i32, _f64, _p = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
+_SIGS = {
+    "cw_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "cw_version": ([], ctypes.c_int),
+    "cw_device_status": ([_p], ctypes.c_int),
+    "cw_hash": ([_u64, _i64, _i64, _i64, _p, _p, _p], ctypes.c_int),
+    "cw_sketch_csr": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
+    "cw_sketch_csr_rows": ([ctypes.POINTER(_CSR), _i64, _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
+    "cw_sketch_dense": ([_p, _i64, _i64, _i64, _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
+    "cw_sketch_vec": ([_p, _i64, _i64, _u64, _p, _p], ctypes.c_int),
+    "cw_qr": ([_p, _i64, _i64, _p, _p, _p, _p], ctypes.c_int),
+    "cw_solve_sketch": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
+    "cw_solve_sketch_dense": ([_p, _i64, _i64, _i64, _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
+    "cw_lsqr_precond": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _f64, _i32, _p,
+                         ctypes.POINTER(_i32), ctypes.POINTER(_f64), _p], ctypes.c_int),
+    "cw_leverage": ([_p, _i64, _i64, _i64, _i64, _u64, _i32, _p, _p, _p], ctypes.c_int),
+}
+
+
+def load(path=None):
+    """Load libcw.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if path is None:
+            path = _build.LIB
+            if not _build.up_to_date():
+                _build.build()
+        if not os.path.exists(path):
+            raise ImportError("libcw.so not found at %s; run __graft_entry__.build()" % path)
+        lib = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(lib, name, None)
+            if f is None:
+                continue  # reported by tests/test_abi.py
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def lib():
+    return load()
+
+
+def status_string(status):
+    try:
+        return load().cw_status_string(int(status)).decode()
+    except Exception:  # pragma: no cover - library missing
+        return "status %d" % status
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor (the library has no CPU path)" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(st, where):
+    if st != 0:
+        raise CWError(st, where)
+
+
+def _csr(A):
+    """A: object with n, d, row_ptr, col, val (e.g. workloads.CSR on a CUDA device)."""
+    c = _CSR()
+    c.n, c.d = int(A.n), int(A.d)
+    c.nnz = int(A.col.numel())
+    c.row_ptr = _ptr(A.row_ptr, torch.int32, "row_ptr")
+    c.col = _ptr(A.col, torch.int32, "col") if c.nnz else None
+    c.val = _ptr(A.val, torch.float32, "val") if c.nnz else None
+    return c
+
+
+def device_status():
+    """Synchronises the current stream; raises if a kernel flagged invalid input."""
+    _check(load().cw_device_status(_stream()), "cw_device_status")
+
+
+# ---------------------------------------------------------------- entry points
+
+def cw_hash(seed, m, i0, count, device=None):
+    """(bucket int32, sign int8) for rows i0 .. i0+count-1."""
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    bucket = torch.empty(count, dtype=torch.int32, device=dev)
+    sign = torch.empty(count, dtype=torch.int8, device=dev)
+    _check(load().cw_hash(seed, m, i0, count, _ptr(bucket), _ptr(sign), _stream()), "cw_hash")
+    return bucket, sign
+
+
+def cw_sketch_csr(A, b, m, seed, SA=None, Sb=None):
+    dev = A.val.device
+    SA = torch.empty(m, A.d, dtype=torch.float32, device=dev) if SA is None else SA
+    if b is not None and Sb is None:
+        Sb = torch.empty(m, dtype=torch.float32, device=dev)
+    c = _csr(A)
+    _check(load().cw_sketch_csr(ctypes.byref(c), _ptr(b, torch.float32, "b"), m, seed,
+                                _ptr(SA, torch.float32, "SA"), _ptr(Sb, torch.float32, "Sb"), _stream()),
+           "cw_sketch_csr")
+    return SA, Sb
+
+
+def cw_sketch_csr_rows(A, i0, b, m, seed, SA=None, Sb=None):
+    dev = A.val.device
+    SA = torch.empty(m, A.d, dtype=torch.float32, device=dev) if SA is None else SA
+    if b is not None and Sb is None:
+        Sb = torch.empty(m, dtype=torch.float32, device=dev)
+    c = _csr(A)
+    _check(load().cw_sketch_csr_rows(ctypes.byref(c), i0, _ptr(b, torch.float32, "b"), m, seed,
+                                     _ptr(SA, torch.float32, "SA"), _ptr(Sb, torch.float32, "Sb"), _stream()),
+           "cw_sketch_csr_rows")
+    return SA, Sb
+
+
+def cw_sketch_dense(A, b, m, seed, SA=None, Sb=None, lda=None):
+    n, d = A.shape
+    lda = A.stride(0) if lda is None else lda
+    if A.stride(1) != 1:
+        raise ValueError("A must be row-major")
+    SA = torch.empty(m, d, dtype=torch.float32, device=A.device) if SA is None else SA
+    if b is not None and Sb is None:
+        Sb = torch.empty(m, dtype=torch.float32, device=A.device)
+    if A.dtype != torch.float32 or not A.is_cuda:
+        raise TypeError("A must be a float32 CUDA tensor")
+    _check(load().cw_sketch_dense(ctypes.c_void_p(A.data_ptr()), n, d, lda, _ptr(b, torch.float32, "b"), m,
+                                  seed, _ptr(SA, torch.float32, "SA"), _ptr(Sb, torch.float32, "Sb"),
+                                  _stream()), "cw_sketch_dense")
+    return SA, Sb
+
+
+def cw_sketch_vec(x, m, seed, Sx=None):
+    Sx = torch.empty(m, dtype=torch.float32, device=x.device) if Sx is None else Sx
+    _check(load().cw_sketch_vec(_ptr(x, torch.float32, "x"), x.numel(), m, seed,
+                                _ptr(Sx, torch.float32, "Sx"), _stream()), "cw_sketch_vec")
+    return Sx
+
+
+def cw_qr(SA, Sb=None):
+    """(R float64 d x d, c float64 d or None) from the float64 Householder QR of SA."""
+    m, d = SA.shape
+    R = torch.empty(d, d, dtype=torch.float64, device=SA.device)
+    c = torch.empty(d, dtype=torch.float64, device=SA.device) if Sb is not None else None
+    _check(load().cw_qr(_ptr(SA, torch.float32, "SA"), m, d, _ptr(Sb, torch.float32, "Sb"),
+                        _ptr(R, torch.float64, "R"), _ptr(c, torch.float64, "c"), _stream()), "cw_qr")
+    return R, c
+
+
+def cw_solve_sketch(A, b, m, seed, want_R=False):
+    dev = A.val.device
+    x = torch.empty(A.d, dtype=torch.float64, device=dev)
+    R = torch.empty(A.d, A.d, dtype=torch.float64, device=dev) if want_R else None
+    c = _csr(A)
+    _check(load().cw_solve_sketch(ctypes.byref(c), _ptr(b, torch.float32, "b"), m, seed,
+                                  _ptr(x, torch.float64, "x"), _ptr(R, torch.float64, "R"), _stream()),
+           "cw_solve_sketch")
+    return (x, R) if want_R else x
+
+
+def cw_solve_sketch_dense(A, b, m, seed, want_R=False):
+    n, d = A.shape
+    x = torch.empty(d, dtype=torch.float64, device=A.device)
+    R = torch.empty(d, d, dtype=torch.float64, device=A.device) if want_R else None
+    _check(load().cw_solve_sketch_dense(_ptr(A, torch.float32, "A"), n, d, A.stride(0),
+                                        _ptr(b, torch.float32, "b"), m, seed, _ptr(x, torch.float64, "x"),
+                                        _ptr(R, torch.float64, "R"), _stream()), "cw_solve_sketch_dense")
+    return (x, R) if want_R else x
+
+
+def cw_lsqr_precond(A, b, m, seed, rtol=1e-6, max_iter=100, allow_noconv=False):
+    """Returns (x float64 d, iterations, final test value)."""
+    dev = A.val.device
+    x = torch.empty(A.d, dtype=torch.float64, device=dev)
+    it = ctypes.c_int32(0)
+    ft = ctypes.c_double(0.0)
+    c = _csr(A)
+    st = load().cw_lsqr_precond(ctypes.byref(c), _ptr(b, torch.float32, "b"), m, seed, float(rtol), int(max_iter),
+                                _ptr(x, torch.float64, "x"), ctypes.byref(it), ctypes.byref(ft), _stream())
+    if not (allow_noconv and st == -6):
+        _check(st, "cw_lsqr_precond")
+    return x, it.value, ft.value
+
+
+def cw_leverage(A, m, seed, G):
+    """lev[i] = ||(A R^-1 G)_i||^2 / k for dense float32 A (n x d) and float64 G (d x k)."""
+    n, d = A.shape
+    k = G.shape[1]
+    lev = torch.empty(n, dtype=torch.float32, device=A.device)
+    _check(load().cw_leverage(_ptr(A, torch.float32, "A"), n, d, A.stride(0), m, seed, k,
+                              _ptr(G, torch.float64, "G"), _ptr(lev, torch.float32, "lev"), _stream()),
+           "cw_leverage")
+    return lev

@@ -1,0 +1,224 @@
+// Shared device/host helpers of the sm_103a sparse-embedding library.
+//
+// The seeded map (h, sigma) that defines S = Phi D (paper Section 2) is
+// evaluated here: two cubic polynomials over GF(p), p = 2^61 - 1, whose
+// coefficients are SplitMix64 draws (Steele, Lea and Flood, 2014) masked to
+// 61 bits.  Rows handled by one thread are evaluated by forward differences
+// of the cubic (three modular additions per polynomial per row) after an
+// initial Horner evaluation at four points.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+
+#include "cw.h"
+
+namespace cw {
+
+constexpr uint64_t kP61 = (1ull << 61) - 1;
+
+// ---------------------------------------------------------------- host side
+
+struct HashParams {
+    uint64_t cb[4];   // bucket polynomial c0..c3
+    uint64_t cs[4];   // sign polynomial c0..c3
+    uint64_t m;       // number of buckets
+    uint64_t minv;    // floor((2^64 - 1) / m) for the Barrett remainder
+    uint32_t mmask;   // m - 1 when m is a power of two
+    uint32_t pow2;    // 1 when m is a power of two
+};
+
+// SplitMix64 step as published (state advance by the golden gamma, then the
+// two xor-shift-multiply rounds and a final xor-shift).
+inline uint64_t splitmix64_next(uint64_t& state) {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+inline HashParams make_hash_params(uint64_t seed, int64_t m) {
+    HashParams hp;
+    uint64_t st = seed;
+    uint64_t c[8];
+    for (int k = 0; k < 8;) {
+        uint64_t v = splitmix64_next(st) & kP61;
+        if (v == kP61) continue;  // p itself is not a field element; draw again
+        c[k++] = v;
+    }
+    for (int k = 0; k < 4; ++k) {
+        hp.cb[k] = c[k];
+        hp.cs[k] = c[4 + k];
+    }
+    hp.m = (uint64_t)m;
+    hp.minv = ~0ull / (uint64_t)m;
+    hp.pow2 = ((uint64_t)m & ((uint64_t)m - 1)) == 0 ? 1u : 0u;
+    hp.mmask = hp.pow2 ? (uint32_t)((uint64_t)m - 1) : 0u;
+    return hp;
+}
+
+// ---------------------------------------------------------------- device field arithmetic
+
+__device__ __forceinline__ uint64_t addmod61(uint64_t a, uint64_t b) {
+    uint64_t r = a + b;  // a, b < p  =>  r < 2p < 2^62
+    return r >= kP61 ? r - kP61 : r;
+}
+
+__device__ __forceinline__ uint64_t submod61(uint64_t a, uint64_t b) {
+    return a >= b ? a - b : a + (kP61 - b);
+}
+
+// a * b mod p for a, b < p: the 122-bit product is split at bit 61 and the two
+// halves are added (2^61 = 1 mod p), followed by one more fold.
+__device__ __forceinline__ uint64_t mulmod61(uint64_t a, uint64_t b) {
+    uint64_t lo = a * b;
+    uint64_t hi = __umul64hi(a, b);                    // < 2^58
+    uint64_t r = (lo & kP61) + ((hi << 3) | (lo >> 61));  // < 2^62
+    r = (r & kP61) + (r >> 61);
+    return r >= kP61 ? r - kP61 : r;
+}
+
+__device__ __forceinline__ uint64_t reduce61(uint64_t x) {
+    uint64_t r = (x & kP61) + (x >> 61);
+    return r >= kP61 ? r - kP61 : r;
+}
+
+__device__ __forceinline__ uint64_t horner61(const uint64_t c[4], uint64_t x) {
+    x = reduce61(x);
+    uint64_t acc = c[3];
+    acc = addmod61(mulmod61(acc, x), c[2]);
+    acc = addmod61(mulmod61(acc, x), c[1]);
+    acc = addmod61(mulmod61(acc, x), c[0]);
+    return acc;
+}
+
+// Cubic evaluated along x0, x0 + s, x0 + 2s, ... by forward differences.
+struct CubicWalk {
+    uint64_t g, d1, d2, d3;
+    __device__ __forceinline__ void init(const uint64_t c[4], uint64_t x0, uint64_t s) {
+        uint64_t g0 = horner61(c, x0);
+        uint64_t g1 = horner61(c, x0 + s);
+        uint64_t g2 = horner61(c, x0 + 2 * s);
+        uint64_t g3 = horner61(c, x0 + 3 * s);
+        uint64_t a1 = submod61(g1, g0), a2 = submod61(g2, g1), a3 = submod61(g3, g2);
+        uint64_t b1 = submod61(a2, a1), b2 = submod61(a3, a2);
+        g = g0;
+        d1 = a1;
+        d2 = b1;
+        d3 = submod61(b2, b1);
+    }
+    __device__ __forceinline__ void step() {
+        g = addmod61(g, d1);
+        d1 = addmod61(d1, d2);
+        d2 = addmod61(d2, d3);
+    }
+};
+
+__device__ __forceinline__ uint32_t bucket_of(uint64_t g, const HashParams& hp) {
+    if (hp.pow2) return (uint32_t)g & hp.mmask;
+    uint64_t q = __umul64hi(g, hp.minv);
+    uint64_t r = g - q * hp.m;
+    if (r >= hp.m) r -= hp.m;
+    return (uint32_t)r;
+}
+
+// key = bucket | (sign bit << 31); the sign bit is set when sigma = -1.
+__device__ __forceinline__ uint32_t make_key(uint64_t gb, uint64_t gs, const HashParams& hp) {
+    return bucket_of(gb, hp) | ((uint32_t)(gs & 1u) << 31);
+}
+
+// Walks both polynomials together and yields keys.
+struct KeyWalk {
+    CubicWalk b, s;
+    __device__ __forceinline__ void init(const HashParams& hp, uint64_t x0, uint64_t step) {
+        b.init(hp.cb, x0, step);
+        s.init(hp.cs, x0, step);
+    }
+    __device__ __forceinline__ uint32_t key(const HashParams& hp) const { return make_key(b.g, s.g, hp); }
+    __device__ __forceinline__ void step() {
+        b.step();
+        s.step();
+    }
+};
+
+// ---------------------------------------------------------------- errors and status
+
+// Device-side sticky flag bits (one word per device).
+enum : unsigned {
+    kDevBadColumn = 1u,
+    kDevDupColumn = 2u,
+    kDevBadRowPtr = 4u,
+    kDevNonFinite = 8u,
+};
+
+// Per-device status word (allocated once per device, never freed).
+unsigned* device_status_word();
+
+__device__ __forceinline__ void flag_error(unsigned* st, unsigned bit) {
+    if (st) atomicOr(st, bit);
+}
+
+#define CW_CUDA_TRY(expr)                          \
+    do {                                           \
+        cudaError_t _e = (expr);                   \
+        if (_e != cudaSuccess) {                   \
+            (void)cudaGetLastError();              \
+            return CW_ERR_CUDA;                    \
+        }                                          \
+    } while (0)
+
+#define CW_LAUNCH_CHECK()                          \
+    do {                                           \
+        cudaError_t _e = cudaGetLastError();       \
+        if (_e != cudaSuccess) return CW_ERR_CUDA; \
+    } while (0)
+
+// ---------------------------------------------------------------- stream-ordered scratch
+
+// Scratch arena: one cudaMallocAsync on the call's stream, carved into
+// 256-byte aligned pieces, released with cudaFreeAsync on the same stream.
+class Scratch {
+  public:
+    explicit Scratch(cudaStream_t s) : s_(s) {}
+    ~Scratch() { release(); }
+    Scratch(const Scratch&) = delete;
+    Scratch& operator=(const Scratch&) = delete;
+
+    // Reserve `bytes` (call before alloc()); returns the offset.
+    size_t reserve(size_t bytes) {
+        size_t off = size_;
+        size_ += (bytes + 255) & ~size_t(255);
+        return off;
+    }
+    cudaError_t alloc() {
+        if (size_ == 0) return cudaSuccess;
+        return cudaMallocAsync(&base_, size_, s_);
+    }
+    template <class T>
+    T* at(size_t off) const {
+        return reinterpret_cast<T*>(static_cast<char*>(base_) + off);
+    }
+    void release() {
+        if (base_) {
+            cudaFreeAsync(base_, s_);
+            base_ = nullptr;
+        }
+    }
+
+  private:
+    cudaStream_t s_;
+    void* base_ = nullptr;
+    size_t size_ = 0;
+};
+
+inline int num_sms() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+}  // namespace cw
