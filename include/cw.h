@@ -35,9 +35,9 @@
  *    stream-ordered before the call returns.
  *  - Arguments are validated on the host before any launch; a bad argument
  *    returns a negative status and enqueues nothing.  Violations only visible
- *    on the device (a column index out of range, a repeated column in a row, a
- *    decreasing row_ptr, a non-finite value where one is rejected) set a
- *    per-device sticky flag that cw_device_status() reports.
+ *    on the device (a column index out of range, a decreasing row_ptr) set a
+ *    per-device sticky flag that cw_device_status() reports; cw_csr_check()
+ *    validates a CSR matrix completely.
  *  - Results are deterministic: the same inputs, seed and sizes give bitwise
  *    identical outputs (fixed summation orders, no floating-point atomics).
  */
@@ -96,6 +96,16 @@ int cw_device_status(cw_stream stream);
  */
 int cw_hash(uint64_t seed, int64_t m, int64_t i0, int64_t count, int32_t *bucket, int8_t *sign,
             cw_stream stream);
+
+/*
+ * cw_csr_check - validate the CSR structure the sketch kernels assume:
+ * row_ptr[0] = 0, row_ptr[n] = nnz, row_ptr non-decreasing, every column in
+ * [0, d) and no column twice within a row.  Returns CW_OK or CW_ERR_ARG.
+ * The sketch kernels themselves detect out-of-range columns and decreasing
+ * row_ptr (sticky device flag) but not repeated columns, which would make a
+ * row's updates race.  Synchronises the stream.
+ */
+int cw_csr_check(const cw_csr *A, cw_stream stream);
 
 /*
  * cw_sketch_csr - SA = S A and Sb = S b for CSR A (paper Section 2; Theorem

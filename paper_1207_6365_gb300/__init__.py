@@ -17,7 +17,7 @@ import torch
 from . import _build
 
 __all__ = [
-    "CWError", "lib", "load", "status_string", "device_status",
+    "CWError", "lib", "load", "status_string", "device_status", "cw_csr_check",
     "cw_hash", "cw_sketch_csr", "cw_sketch_csr_rows", "cw_sketch_dense", "cw_sketch_vec",
     "cw_qr", "cw_solve_sketch", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
     "EXPORTS", "HEADER",
@@ -25,7 +25,7 @@ __all__ = [
 
 HEADER = os.path.join(_build.ROOT, "include", "cw.h")
 EXPORTS = (
-    "cw_status_string", "cw_version", "cw_device_status", "cw_hash", "cw_sketch_csr",
+    "cw_status_string", "cw_version", "cw_device_status", "cw_csr_check", "cw_hash", "cw_sketch_csr",
     "cw_sketch_csr_rows", "cw_sketch_dense", "cw_sketch_vec", "cw_qr", "cw_solve_sketch",
     "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
 )
@@ -49,6 +49,7 @@ _SIGS = {
     "cw_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "cw_version": ([], ctypes.c_int),
     "cw_device_status": ([_p], ctypes.c_int),
+    "cw_csr_check": ([ctypes.POINTER(_CSR), _p], ctypes.c_int),
     "cw_hash": ([_u64, _i64, _i64, _i64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_csr": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_csr_rows": ([ctypes.POINTER(_CSR), _i64, _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
@@ -137,6 +138,12 @@ def device_status():
 
 
 # ---------------------------------------------------------------- entry points
+
+def cw_csr_check(A):
+    """Raises CWError unless A is a valid CSR (monotone row_ptr, columns in range, distinct per row)."""
+    c = _csr(A)
+    _check(load().cw_csr_check(ctypes.byref(c), _stream()), "cw_csr_check")
+
 
 def cw_hash(seed, m, i0, count, device=None):
     """(bucket int32, sign int8) for rows i0 .. i0+count-1."""

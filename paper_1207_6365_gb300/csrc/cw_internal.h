@@ -1,0 +1,28 @@
+// Internal (non-exported) entry points shared between translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cw {
+
+enum SketchModeId { kSketchCSR = 0, kSketchDense = 1, kSketchVec = 2 };
+
+// SA / Sb of a CSR, dense or vector input (see sketch.cu).
+int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const int32_t* row_ptr,
+                const int32_t* col, const float* val, const float* A, const float* b, int64_t m,
+                uint64_t seed, float* SA, float* Sb, int32_t* bucket_ptr_out, cudaStream_t stream,
+                double* SA64 = nullptr);
+int validate_common(int64_t n, int64_t d, int64_t m);
+
+// float64 Householder QR of [SA | Sb]; synchronises.  SA64 (row-major float64)
+// replaces SA when given.
+int qr64(const float* SA, int64_t m, int d, const float* Sb, double* R, double* c, cudaStream_t stream,
+         const double* SA64 = nullptr);
+// Cholesky factor of the Gram matrix of SA (fast preconditioner); synchronises.
+int gram_cholesky(const float* SA, int64_t m, int d, const float* Sb, double* R, double* c,
+                  cudaStream_t stream);
+int trsv_upper(const double* R, int d, const double* rhs, double* x, cudaStream_t stream);
+int trsm_upper(const double* R, int d, const double* B, int k, double* X, cudaStream_t stream);
+
+}  // namespace cw

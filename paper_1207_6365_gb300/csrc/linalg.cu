@@ -1,0 +1,486 @@
+// Small dense linear algebra on the sketch SA (m x d, m >> d):
+//
+//  * Householder QR of [SA | Sb] in float64 (the solve of the proof of
+//    Theorem "renRegAlg": a QR factorisation of SA, then R^-1 Q^T SB).  One
+//    persistent cooperative kernel; each CTA owns a contiguous block of rows of
+//    the column-major float64 copy and every column step uses three grid-wide
+//    barriers (norm -> reflector dots -> update).  Barriers spin with an
+//    iteration limit and report CW_ERR_TIMEOUT instead of hanging.
+//  * Gram matrix [SA | Sb]^T [SA | Sb] (float32 products, per-chunk float32
+//    partial sums combined in float64 in a fixed order) and its Cholesky
+//    factor: the fast R used to precondition LSQR, whose quality only needs to
+//    be a constant factor (Section 7.6: kappa(R^T A^T A R) <= (1+e0)^2/(1-e0)^2).
+//  * Triangular solves and the triangular inverse in float64.
+#include <cmath>
+#include <cstring>
+
+#include "cw_common.cuh"
+#include "cw_internal.h"
+
+namespace cw {
+
+// ---------------------------------------------------------------- bounded grid barrier
+
+constexpr long long kBarrierSpinLimit = 1ll << 24;  // ~1 s with 64 ns sleeps
+
+// bar[0] = arrival count, bar[1] = generation.  Returns false (after flagging
+// the status word) when the wait exceeded its limit; the caller must return.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* timeout_flag) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        __threadfence();
+        const unsigned gen = atomicAdd(&bar[1], 0u);
+        const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
+        if (arrived == nblocks) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            long long it = 0;
+            while (atomicAdd(&bar[1], 0u) == gen) {
+                __nanosleep(64);
+                if (++it > kBarrierSpinLimit) {
+                    atomicExch(timeout_flag, 1u);
+                    ok = 0;
+                    break;
+                }
+            }
+            if (ok && atomicAdd(timeout_flag, 0u)) ok = 0;
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// ---------------------------------------------------------------- layout conversion
+
+// W (column-major m x nc, float64) <- [SA | Sb] (SA row-major float32).
+template <class T>
+__global__ void k_to_colmajor64(const T* __restrict__ SA, const float* __restrict__ Sb, int64_t m, int d,
+                                int nc, double* __restrict__ W) {
+    __shared__ double tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+        const int64_t r = r0 + q;
+        const int c = c0 + threadIdx.x;
+        double v = 0.0;
+        if (r < m) {
+            if (c < d) v = (double)SA[r * d + c];
+            else if (c == d && Sb) v = (double)Sb[r];
+        }
+        tile[q][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+        const int c = c0 + q;
+        const int64_t r = r0 + threadIdx.x;
+        if (c < nc && r < m) W[(int64_t)c * m + r] = tile[threadIdx.x][q];
+    }
+}
+
+// ---------------------------------------------------------------- Householder QR (float64)
+
+struct QrArgs {
+    double* W;        // column-major m x nc
+    int64_t m;
+    int d;            // columns to factor
+    int nc;           // d or d + 1 (the last one is carried: c = Q^T Sb)
+    double* normp;    // [grid] partial squared norms
+    double* dotp;     // [grid][nc] partial reflector dots
+    double* wv;       // [nc] tau * (v^T W[:, k])
+    unsigned* bar;    // barrier words (2)
+    unsigned* tflag;  // timeout flag
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_qr_householder(QrArgs a) {
+    extern __shared__ double sv[];  // this block's reflector entries (rows r0..r1)
+    __shared__ double s_red[8];
+    const unsigned G = gridDim.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int64_t per = (a.m + G - 1) / G;
+    const int64_t r0 = (per * blockIdx.x < a.m) ? per * blockIdx.x : a.m;
+    const int64_t r1 = (r0 + per < a.m) ? r0 + per : a.m;
+    const int64_t rows = r1 - r0;
+
+    // squared norm of column 0 over this block's rows
+    {
+        double s = 0.0;
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            const double x = a.W[i];
+            s += x * x;
+        }
+        s = warp_sum(s);
+        if (lane == 0) s_red[warp] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nwarps; ++w) t += s_red[w];
+            a.normp[blockIdx.x] = t;
+        }
+    }
+    if (!grid_barrier(a.bar, G, a.tflag)) return;
+
+    for (int j = 0; j < a.d; ++j) {
+        // reflector for column j: every block forms the same scalars
+        double sig2 = 0.0;
+        for (unsigned c = 0; c < G; ++c) sig2 += a.normp[c];  // fixed order
+        const double ajj = a.W[(int64_t)j * a.m + j];
+        double beta, tau, vscale;
+        if (sig2 == 0.0) {
+            beta = 0.0;
+            tau = 0.0;
+            vscale = 0.0;
+        } else {
+            const double sig = sqrt(sig2);
+            beta = ajj >= 0.0 ? -sig : sig;
+            tau = (beta - ajj) / beta;
+            vscale = 1.0 / (ajj - beta);
+        }
+        // v for my rows (0 above the diagonal, 1 at it)
+        const double* colj = a.W + (int64_t)j * a.m;
+        for (int64_t q = threadIdx.x; q < rows; q += blockDim.x) {
+            const int64_t i = r0 + q;
+            sv[q] = (i < j) ? 0.0 : (i == j ? 1.0 : colj[i] * vscale);
+        }
+        __syncthreads();
+        // partial dots v^T W[:, k] for k > j
+        for (int k = j + 1 + warp; k < a.nc; k += nwarps) {
+            const double* colk = a.W + (int64_t)k * a.m;
+            double s = 0.0;
+            for (int64_t q = lane; q < rows; q += 32) s += sv[q] * colk[r0 + q];
+            s = warp_sum(s);
+            if (lane == 0) a.dotp[(size_t)blockIdx.x * a.nc + k] = s;
+        }
+        if (!grid_barrier(a.bar, G, a.tflag)) return;
+        // distributed reduction over blocks (fixed order)
+        for (int k = j + 1 + blockIdx.x * nwarps + warp; k < a.nc; k += G * nwarps) {
+            double s = 0.0;
+            for (unsigned c = lane; c < G; c += 32) s += a.dotp[(size_t)c * a.nc + k];
+            s = warp_sum(s);
+            if (lane == 0) a.wv[k] = tau * s;
+        }
+        if (!grid_barrier(a.bar, G, a.tflag)) return;
+        // update W[:, k] -= v * wv[k]; norm of the next column
+        double nrm = 0.0;
+        for (int k = j + 1 + warp; k < a.nc; k += nwarps) {
+            double* colk = a.W + (int64_t)k * a.m;
+            const double wk = a.wv[k];
+            double s = 0.0;
+            for (int64_t q = lane; q < rows; q += 32) {
+                const int64_t i = r0 + q;
+                double x = colk[i];
+                if (i >= j) {
+                    x -= sv[q] * wk;
+                    colk[i] = x;
+                }
+                if (k == j + 1 && i >= j + 1) s += x * x;
+            }
+            if (k == j + 1) nrm = warp_sum(s);
+        }
+        if (lane == 0) s_red[warp] = nrm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nwarps; ++w) t += s_red[w];
+            a.normp[blockIdx.x] = t;
+            if (j >= r0 && j < r1) a.W[(int64_t)j * a.m + j] = beta;  // R_jj
+        }
+        if (!grid_barrier(a.bar, G, a.tflag)) return;
+    }
+}
+
+// R (row-major d x d, positive diagonal) and c = Q^T Sb from the factored W;
+// flags rank deficiency |R_jj| <= d * 2^-52 * max |R_ii|.
+__global__ void k_qr_finalize(const double* __restrict__ W, int64_t m, int d, int nc, double* __restrict__ R,
+                              double* __restrict__ c, unsigned* rank_flag) {
+    __shared__ double dmax;
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        for (int j = 0; j < d; ++j) mx = fmax(mx, fabs(W[(int64_t)j * m + j]));
+        dmax = mx;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const double rjj = W[(int64_t)j * m + j];
+        const double s = rjj < 0.0 ? -1.0 : 1.0;
+        if (fabs(rjj) <= (double)d * 2.220446049250313e-16 * dmax) atomicExch(rank_flag, 1u);
+        if (R)
+            for (int k = 0; k < d; ++k) R[(int64_t)j * d + k] = (k < j) ? 0.0 : s * W[(int64_t)k * m + j];
+        if (c && nc > d) c[j] = s * W[(int64_t)d * m + j];
+    }
+}
+
+// ---------------------------------------------------------------- triangular solves (float64)
+
+// x = R^-1 rhs for upper-triangular row-major R (one CTA, column sweep).
+__global__ void k_trsv_upper(const double* __restrict__ R, int d, const double* __restrict__ rhs,
+                             double* __restrict__ x) {
+    extern __shared__ double sx[];
+    for (int i = threadIdx.x; i < d; i += blockDim.x) sx[i] = rhs[i];
+    __syncthreads();
+    for (int j = d - 1; j >= 0; --j) {
+        if (threadIdx.x == 0) sx[j] = sx[j] / R[(int64_t)j * d + j];
+        __syncthreads();
+        const double xj = sx[j];
+        for (int i = threadIdx.x; i < j; i += blockDim.x) sx[i] -= R[(int64_t)i * d + j] * xj;
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < d; i += blockDim.x) x[i] = sx[i];
+}
+
+// X = R^-1 B for upper-triangular R (d x d) and B (d x k), both row-major; one
+// CTA per column of B.
+__global__ void k_trsm_upper(const double* __restrict__ R, int d, const double* __restrict__ B, int k,
+                             double* __restrict__ X) {
+    extern __shared__ double sx[];
+    const int col = blockIdx.x;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) sx[i] = B ? B[(int64_t)i * k + col] : (i == col ? 1.0 : 0.0);
+    __syncthreads();
+    for (int j = d - 1; j >= 0; --j) {
+        if (threadIdx.x == 0) sx[j] = sx[j] / R[(int64_t)j * d + j];
+        __syncthreads();
+        const double xj = sx[j];
+        if (xj != 0.0)
+            for (int i = threadIdx.x; i < j; i += blockDim.x) sx[i] -= R[(int64_t)i * d + j] * xj;
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < d; i += blockDim.x) X[(int64_t)i * k + col] = sx[i];
+}
+
+// ---------------------------------------------------------------- Gram matrix (fast R)
+
+constexpr int kGramTile = 64;
+constexpr int kGramRowsPerChunk = 2048;
+
+// Partial Gram of the columns [ti*64, ti*64+64) x [tj*64, tj*64+64) of
+// X = [SA | Sb] over one chunk of rows; float32 products and sums within the
+// chunk, stored as float64 partials [chunk][nc][nc].
+__global__ void __launch_bounds__(256) k_gram_partial(const float* __restrict__ SA, const float* __restrict__ Sb,
+                                                     int64_t m, int d, int nc, int ntile,
+                                                     double* __restrict__ part) {
+    __shared__ float Xi[32][kGramTile + 1];
+    __shared__ float Xj[32][kGramTile + 1];
+    // upper-triangular tile index -> (ti, tj)
+    int t = blockIdx.x, ti = 0;
+    while (t >= ntile - ti) {
+        t -= ntile - ti;
+        ++ti;
+    }
+    const int tj = ti + t;
+    const int chunk = blockIdx.y;
+    const int64_t rb = (int64_t)chunk * kGramRowsPerChunk;
+    const int64_t re = (rb + kGramRowsPerChunk < m) ? rb + kGramRowsPerChunk : m;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 4 x 4 outputs each
+    float acc[4][4] = {};
+    for (int64_t r = rb; r < re; r += 32) {
+        for (int q = threadIdx.x; q < 32 * kGramTile; q += blockDim.x) {
+            const int rr = q / kGramTile, cc = q % kGramTile;
+            const int64_t row = r + rr;
+            const int ci = ti * kGramTile + cc, cj = tj * kGramTile + cc;
+            float vi = 0.f, vj = 0.f;
+            if (row < re) {
+                vi = ci < d ? SA[row * d + ci] : (ci == d && Sb ? Sb[row] : 0.f);
+                vj = cj < d ? SA[row * d + cj] : (cj == d && Sb ? Sb[row] : 0.f);
+            }
+            Xi[rr][cc] = vi;
+            Xj[rr][cc] = vj;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+            float a[4], b[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                a[p] = Xi[rr][ty * 4 + p];
+                b[p] = Xj[rr][tx * 4 + p];
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
+        }
+        __syncthreads();
+    }
+    double* out = part + (size_t)chunk * nc * nc;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int ci = ti * kGramTile + ty * 4 + p, cj = tj * kGramTile + tx * 4 + q;
+            if (ci < nc && cj < nc && ci <= cj) out[(size_t)ci * nc + cj] = (double)acc[p][q];
+        }
+}
+
+__global__ void k_gram_reduce(const double* __restrict__ part, int nchunk, int nc, double* __restrict__ Gm) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nc * nc) return;
+    const int ci = (int)(idx / nc), cj = (int)(idx % nc);
+    if (ci > cj) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * nc * nc + idx];
+    Gm[(int64_t)ci * nc + cj] = s;
+    Gm[(int64_t)cj * nc + ci] = s;
+}
+
+// In-place upper Cholesky G = R^T R of the leading d x d block (float64, one
+// CTA, right-looking).  Also forms c = R^-T g for g = G[0:d, d] when nc > d.
+// Flags a non-positive pivot in *bad.
+__global__ void __launch_bounds__(1024) k_cholesky_upper(double* __restrict__ Gm, int d, int nc, double* __restrict__ R,
+                                                        double* __restrict__ c, unsigned* bad) {
+    for (int j = 0; j < d; ++j) {
+        __syncthreads();
+        const double piv = Gm[(int64_t)j * nc + j];
+        if (!(piv > 0.0)) {
+            if (threadIdx.x == 0) atomicExch(bad, 1u);
+            return;
+        }
+        const double rjj = sqrt(piv);
+        __syncthreads();
+        // row j of R: G[j, k] / rjj for k >= j (including the carried column)
+        for (int k = j + threadIdx.x; k < nc; k += blockDim.x) Gm[(int64_t)j * nc + k] = (k == j) ? rjj : Gm[(int64_t)j * nc + k] / rjj;
+        __syncthreads();
+        // trailing update G[i, k] -= R[j, i] R[j, k] for j < i <= k
+        const int rem = d - j - 1;
+        const int64_t tot = (int64_t)rem * (nc - j - 1);
+        for (int64_t q = threadIdx.x; q < tot; q += blockDim.x) {
+            const int i = j + 1 + (int)(q / (nc - j - 1));
+            const int k = j + 1 + (int)(q % (nc - j - 1));
+            if (k >= i) Gm[(int64_t)i * nc + k] -= Gm[(int64_t)j * nc + i] * Gm[(int64_t)j * nc + k];
+        }
+    }
+    __syncthreads();
+    for (int64_t q = threadIdx.x; q < (int64_t)d * d; q += blockDim.x) {
+        const int i = (int)(q / d), k = (int)(q % d);
+        R[q] = (k < i) ? 0.0 : Gm[(int64_t)i * nc + k];
+    }
+    if (c && nc > d)
+        for (int i = threadIdx.x; i < d; i += blockDim.x) c[i] = Gm[(int64_t)i * nc + d];
+}
+
+// ---------------------------------------------------------------- host drivers
+
+namespace {
+
+int qr_grid(int64_t m, int threads, size_t smem) {
+    int dev = 0, per = 0;
+    cudaGetDevice(&dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_qr_householder, threads, smem) != cudaSuccess)
+        per = 1;
+    per = per < 1 ? 1 : (per > 2 ? 2 : per);
+    int g = num_sms() * per;
+    const int64_t want = (m + 63) / 64;  // at least 64 rows per block
+    if (want < g) g = (int)(want < 1 ? 1 : want);
+    return g;
+}
+
+}  // namespace
+
+// Householder QR of [SA | Sb] in float64.  R (device, row-major d x d) and c
+// (device, d) may be NULL.  Synchronises the stream.  Returns CW_ERR_RANK for
+// a numerically rank-deficient SA (outputs still written).
+int qr64(const float* SA, int64_t m, int d, const float* Sb, double* R, double* c, cudaStream_t stream,
+         const double* SA64) {
+    const int nc = d + (Sb ? 1 : 0);
+    const int threads = 256;
+    int G = qr_grid(m, threads, 48 * 1024);
+    const size_t smem = sizeof(double) * (size_t)((m + G - 1) / G);
+    if (smem > 200 * 1024) return CW_ERR_SHAPE;  // m too large for the resident-grid design
+    Scratch ws(stream);
+    const size_t oW = ws.reserve(sizeof(double) * (size_t)m * nc);
+    const size_t oN = ws.reserve(sizeof(double) * (size_t)G);
+    const size_t oD = ws.reserve(sizeof(double) * (size_t)G * nc);
+    const size_t oV = ws.reserve(sizeof(double) * (size_t)nc);
+    const size_t oB = ws.reserve(sizeof(unsigned) * 4);
+    CW_CUDA_TRY(ws.alloc());
+    double* W = ws.at<double>(oW);
+    unsigned* bar = ws.at<unsigned>(oB);
+    CW_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned) * 4, stream));
+    dim3 tb(32, 8), tg((unsigned)((m + 31) / 32), (unsigned)((nc + 31) / 32));
+    if (SA64)
+        k_to_colmajor64<double><<<tg, tb, 0, stream>>>(SA64, Sb, m, d, nc, W);
+    else
+        k_to_colmajor64<float><<<tg, tb, 0, stream>>>(SA, Sb, m, d, nc, W);
+    CW_LAUNCH_CHECK();
+    QrArgs a{W, m, d, nc, ws.at<double>(oN), ws.at<double>(oD), ws.at<double>(oV), bar, bar + 2};
+    CW_CUDA_TRY(cudaFuncSetAttribute(k_qr_householder, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr_householder, threads, smem));
+    if ((int64_t)per_sm * num_sms() < G) G = per_sm * num_sms();
+    if (G < 1) return CW_ERR_CUDA;
+    void* args[] = {&a};
+    CW_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_qr_householder, dim3(G), dim3(threads), args, smem, stream));
+    k_qr_finalize<<<1, 256, 0, stream>>>(W, m, d, nc, R, c, bar + 3);
+    CW_LAUNCH_CHECK();
+    unsigned flags[2] = {0, 0};
+    CW_CUDA_TRY(cudaMemcpyAsync(flags, bar + 2, sizeof(unsigned) * 2, cudaMemcpyDeviceToHost, stream));
+    CW_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (flags[0]) return CW_ERR_TIMEOUT;
+    if (flags[1]) return CW_ERR_RANK;
+    return CW_OK;
+}
+
+// Fast R: upper Cholesky factor of the Gram matrix of SA (float32 products,
+// float64 accumulation across row chunks), and c = R^-T SA^T Sb when Sb is
+// given.  Returns CW_ERR_RANK when a pivot is not positive.  Asynchronous
+// except for the final flag read (synchronises).
+int gram_cholesky(const float* SA, int64_t m, int d, const float* Sb, double* R, double* c, cudaStream_t stream) {
+    const int nc = d + (Sb ? 1 : 0);
+    const int ntile = (nc + kGramTile - 1) / kGramTile;
+    const int nchunk = (int)((m + kGramRowsPerChunk - 1) / kGramRowsPerChunk);
+    Scratch ws(stream);
+    const size_t oP = ws.reserve(sizeof(double) * (size_t)nchunk * nc * nc);
+    const size_t oG = ws.reserve(sizeof(double) * (size_t)nc * nc);
+    const size_t oF = ws.reserve(sizeof(unsigned) * 2);
+    CW_CUDA_TRY(ws.alloc());
+    double* part = ws.at<double>(oP);
+    double* Gm = ws.at<double>(oG);
+    unsigned* bad = ws.at<unsigned>(oF);
+    CW_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned) * 2, stream));
+    dim3 gg((unsigned)(ntile * (ntile + 1) / 2), (unsigned)nchunk);
+    k_gram_partial<<<gg, 256, 0, stream>>>(SA, Sb, m, d, nc, ntile, part);
+    CW_LAUNCH_CHECK();
+    const int64_t tot = (int64_t)nc * nc;
+    k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(part, nchunk, nc, Gm);
+    CW_LAUNCH_CHECK();
+    k_cholesky_upper<<<1, 1024, 0, stream>>>(Gm, d, nc, R, c, bad);
+    CW_LAUNCH_CHECK();
+    unsigned h = 0;
+    CW_CUDA_TRY(cudaMemcpyAsync(&h, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
+    CW_CUDA_TRY(cudaStreamSynchronize(stream));
+    return h ? CW_ERR_RANK : CW_OK;
+}
+
+int trsv_upper(const double* R, int d, const double* rhs, double* x, cudaStream_t stream) {
+    k_trsv_upper<<<1, 256, sizeof(double) * d, stream>>>(R, d, rhs, x);
+    CW_LAUNCH_CHECK();
+    return CW_OK;
+}
+
+// X = R^-1 B (B d x k row-major; B == NULL gives the inverse, k == d).
+int trsm_upper(const double* R, int d, const double* B, int k, double* X, cudaStream_t stream) {
+    k_trsm_upper<<<k, 256, sizeof(double) * d, stream>>>(R, d, B, k, X);
+    CW_LAUNCH_CHECK();
+    return CW_OK;
+}
+
+}  // namespace cw
+
+using namespace cw;
+
+extern "C" int cw_qr(const float* SA, int64_t m, int64_t d, const float* Sb, double* R, double* c,
+                     cw_stream stream) {
+    if (!SA) return CW_ERR_ARG;
+    if (d < 1 || d > 1024 || m < d) return CW_ERR_SHAPE;
+    if (m > 0x7FFFFFFFll) return CW_ERR_OVERFLOW;
+    return qr64(SA, m, (int)d, c ? Sb : nullptr, R, c, stream);
+}

@@ -22,6 +22,7 @@
 #include <cmath>
 
 #include "cw_common.cuh"
+#include "cw_internal.h"
 
 namespace cw {
 
@@ -69,6 +70,7 @@ __global__ void k_scan_chunk_sums(const uint32_t* __restrict__ H, int ntiles, in
     if (b >= nbins) return;
     const int t0 = c * kScanChunk, t1 = min(ntiles, t0 + kScanChunk);
     uint32_t s = 0;
+#pragma unroll 16
     for (int t = t0; t < t1; ++t) s += H[(size_t)t * nbins + b];
     P[(size_t)c * nbins + b] = s;
 }
@@ -141,10 +143,13 @@ __global__ void k_scan_tiles(uint32_t* __restrict__ H, const uint32_t* __restric
     if (b >= nbins) return;
     const int t0 = c * kScanChunk, t1 = min(ntiles, t0 + kScanChunk);
     uint32_t run = P[(size_t)c * nbins + b];
-    for (int t = t0; t < t1; ++t) {
-        const uint32_t v = H[(size_t)t * nbins + b];
-        H[(size_t)t * nbins + b] = run;
-        run += v;
+    uint32_t v[kScanChunk];
+#pragma unroll
+    for (int q = 0; q < kScanChunk; ++q) v[q] = (t0 + q < t1) ? H[(size_t)(t0 + q) * nbins + b] : 0u;
+#pragma unroll
+    for (int q = 0; q < kScanChunk; ++q) {
+        if (t0 + q < t1) H[(size_t)(t0 + q) * nbins + b] = run;
+        run += v[q];
     }
 }
 
@@ -469,9 +474,6 @@ __global__ void __launch_bounds__(512) k_apply_csr(CsrApplyArgs a) {
                             c = __ldg(a.col + st[u] + t);
                             v = __ldg(a.val + st[u] + t);
                         }
-                        const unsigned am = __activemask();
-                        const unsigned same = __match_any_sync(am, ((unsigned)sub << 21) | ((unsigned)c & 0x1FFFFFu));
-                        if (__popc(same) > 1) flag_error(a.status, kDevDupColumn);
                         if ((unsigned)c < (unsigned)a.d)
                             myacc[c] += neg ? -v : v;
                         else
@@ -520,12 +522,22 @@ struct DenseApplyArgs {
     int d;
     int gshift;
     int cap;
-    int vec4;  // 1 when A rows and d allow 16-byte loads
+    int vec4;      // 1 when A rows and d allow 16-byte loads
+    double* SA64;  // PRECISE: float64 output of the two-word sums
 };
 
 // Each warp owns a bucket; lane l holds columns {4l + 128 v .. +3} (vec4) or
 // {l + 32 v} in registers; rows are added in ascending order.
-template <int NV, int U, bool HAS_B>
+// PRECISE: each accumulator is a float32 pair (hi, lo) updated by an exact
+// two-sum, so SA is exact to ~2^-48 relative and is written in float64.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+    const float t = hi + x;
+    const float bp = t - hi;
+    lo += (hi - (t - bp)) + (x - bp);
+    hi = t;
+}
+
+template <int NV, int U, bool HAS_B, bool PRECISE>
 __global__ void __launch_bounds__(512) k_apply_dense(DenseApplyArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int nwarps = blockDim.x >> 5;
@@ -605,8 +617,11 @@ __global__ void __launch_bounds__(512) k_apply_dense(DenseApplyArgs a) {
                 for (int k = s; k < e; ++k) sbacc += s_b[k];
             for (int cbase = 0; cbase < a.d; cbase += COLS_PER_PASS) {
                 float4 acc[NV];
+                float4 accl[PRECISE ? NV : 1];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int v = 0; v < (PRECISE ? NV : 1); ++v) accl[v] = make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int k0 = s; k0 < e; k0 += U) {
                     float4 x[U][NV];
                     uint32_t rr[U];
@@ -639,7 +654,13 @@ __global__ void __launch_bounds__(512) k_apply_dense(DenseApplyArgs a) {
                         const bool neg = (rr[u] >> 31) != 0;
 #pragma unroll
                         for (int v = 0; v < NV; ++v) {
-                            if (neg) {
+                            if (PRECISE) {
+                                const float sg = neg ? -1.f : 1.f;
+                                two_sum_acc(acc[v].x, accl[v].x, sg * x[u][v].x);
+                                two_sum_acc(acc[v].y, accl[v].y, sg * x[u][v].y);
+                                two_sum_acc(acc[v].z, accl[v].z, sg * x[u][v].z);
+                                two_sum_acc(acc[v].w, accl[v].w, sg * x[u][v].w);
+                            } else if (neg) {
                                 acc[v].x -= x[u][v].x; acc[v].y -= x[u][v].y;
                                 acc[v].z -= x[u][v].z; acc[v].w -= x[u][v].w;
                             } else {
@@ -648,6 +669,23 @@ __global__ void __launch_bounds__(512) k_apply_dense(DenseApplyArgs a) {
                             }
                         }
                     }
+                }
+                if (PRECISE) {
+                    double* row64 = a.SA64 + (size_t)(b0 + bk) * a.d;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        const float hv[4] = {acc[v].x, acc[v].y, acc[v].z, acc[v].w};
+                        const float lv[4] = {accl[v].x, accl[v].y, accl[v].z, accl[v].w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int cq = a.vec4 ? cbase + v * 128 + lane * 4 + q : cbase + v * 128 + lane + 32 * q;
+                            if (cq < a.d) {
+                                const double val = (double)hv[q] + (double)lv[q];
+                                row64[cq] = first ? val : row64[cq] + val;
+                            }
+                        }
+                    }
+                    continue;
                 }
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
@@ -847,10 +885,12 @@ static cudaError_t set_smem(F* f, size_t bytes) {
 // stable permutation); NULL uses internal scratch.
 int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const int32_t* row_ptr,
                 const int32_t* col, const float* val, const float* A, const float* b, int64_t m,
-                uint64_t seed, float* SA, float* Sb, int32_t* bucket_ptr_out, cudaStream_t stream) {
+                uint64_t seed, float* SA, float* Sb, int32_t* bucket_ptr_out, cudaStream_t stream,
+                double* SA64) {
     const bool has_b = b != nullptr && (mode == kModeVec || Sb != nullptr);
     if (n == 0) {
         if (SA && d > 0) CW_CUDA_TRY(cudaMemsetAsync(SA, 0, sizeof(float) * (size_t)m * (size_t)d, stream));
+        if (SA64 && d > 0) CW_CUDA_TRY(cudaMemsetAsync(SA64, 0, sizeof(double) * (size_t)m * (size_t)d, stream));
         if (Sb) CW_CUDA_TRY(cudaMemsetAsync(Sb, 0, sizeof(float) * (size_t)m, stream));
         if (bucket_ptr_out) CW_CUDA_TRY(cudaMemsetAsync(bucket_ptr_out, 0, sizeof(int32_t) * (size_t)(m + 1), stream));
         return CW_OK;
@@ -928,16 +968,25 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     } else if (mode == kModeDense) {
         const bool vec4 = (lda % 4 == 0) && (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
                           ((reinterpret_cast<uintptr_t>(SA) & 15) == 0);
-        DenseApplyArgs a{rkey, ra, rb, CP, A, lda, SA, Sb, bptr, m, (int)d, p.gshift, p.cap, vec4 ? 1 : 0};
+        DenseApplyArgs a{rkey, ra, rb, CP, A, lda, SA, Sb, bptr, m, (int)d, p.gshift, p.cap, vec4 ? 1 : 0, SA64};
         const int threads = p.warps * 32;
         const int nv = d <= 128 ? 1 : d <= 256 ? 2 : d <= 512 ? 4 : 8;
 #define CW_K4D(NV, U, HB)                                                 \
     do {                                                                  \
-        auto kf = k_apply_dense<NV, U, HB>;                               \
+        auto kf = k_apply_dense<NV, U, HB, false>;                        \
         CW_CUDA_TRY(set_smem(kf, p.smem));                                \
         kf<<<p.nbins, threads, p.smem, stream>>>(a);                      \
     } while (0)
-        if (has_b) {
+#define CW_K4P(NV, U)                                                     \
+    do {                                                                  \
+        auto kf = k_apply_dense<NV, U, false, true>;                      \
+        CW_CUDA_TRY(set_smem(kf, p.smem));                                \
+        kf<<<p.nbins, threads, p.smem, stream>>>(a);                      \
+    } while (0)
+        if (SA64) {
+            if (nv == 1) CW_K4P(1, 8); else if (nv == 2) CW_K4P(2, 4);
+            else if (nv == 4) CW_K4P(4, 4); else CW_K4P(8, 2);
+        } else if (has_b) {
             if (nv == 1) CW_K4D(1, 8, true); else if (nv == 2) CW_K4D(2, 4, true);
             else if (nv == 4) CW_K4D(4, 4, true); else CW_K4D(8, 2, true);
         } else {
@@ -945,6 +994,7 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
             else if (nv == 4) CW_K4D(4, 4, false); else CW_K4D(8, 2, false);
         }
 #undef CW_K4D
+#undef CW_K4P
     } else {
         auto kf = k_apply_vec;
         CW_CUDA_TRY(set_smem(kf, p.smem));
@@ -978,7 +1028,7 @@ extern "C" int cw_sketch_csr_rows(const cw_csr* A, int64_t i0, const float* b, i
     if (i0 < 0 || i0 > (1ll << 62)) return CW_ERR_OVERFLOW;
     if (A->n > 0 && (!A->row_ptr || (A->nnz > 0 && (!A->col || !A->val)))) return CW_ERR_ARG;
     return sketch_impl(kModeCSR, A->n, A->d, 0, i0, A->row_ptr, A->col, A->val, nullptr, b, m, seed, SA,
-                       b ? Sb : nullptr, nullptr, stream);
+                       b ? Sb : nullptr, nullptr, stream, nullptr);
 }
 
 extern "C" int cw_sketch_csr(const cw_csr* A, const float* b, int64_t m, uint64_t seed, float* SA, float* Sb,
@@ -993,7 +1043,7 @@ extern "C" int cw_sketch_dense(const float* A, int64_t n, int64_t d, int64_t lda
     if (st != CW_OK) return st;
     if (d < 1 || lda < d) return CW_ERR_SHAPE;
     return sketch_impl(kModeDense, n, d, lda, 0, nullptr, nullptr, nullptr, A, b, m, seed, SA,
-                       b ? Sb : nullptr, nullptr, stream);
+                       b ? Sb : nullptr, nullptr, stream, nullptr);
 }
 
 extern "C" int cw_sketch_vec(const float* x, int64_t n, int64_t m, uint64_t seed, float* Sx, cw_stream stream) {
@@ -1001,5 +1051,62 @@ extern "C" int cw_sketch_vec(const float* x, int64_t n, int64_t m, uint64_t seed
     int st = validate_common(n, 1, m);
     if (st != CW_OK) return st;
     return sketch_impl(kModeVec, n, 0, 0, 0, nullptr, nullptr, nullptr, nullptr, x, m, seed, nullptr, Sx,
-                       nullptr, stream);
+                       nullptr, stream, nullptr);
+}
+
+// ---------------------------------------------------------------- CSR structure check
+
+namespace cw {
+
+// One warp per row: row_ptr non-decreasing, columns in [0, d), no column twice
+// in a row.  Sets bits of *bad (1: row_ptr, 2: column range, 4: duplicate).
+__global__ void k_csr_check(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t n,
+                            int64_t d, int64_t nnz, unsigned* bad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (w0 == 0 && lane == 0 && (row_ptr[0] != 0 || (int64_t)row_ptr[n] != nnz)) atomicOr(bad, 1u);
+    for (int64_t r = w0; r < n; r += nw) {
+        const int32_t s = row_ptr[r], e = row_ptr[r + 1];
+        if (e < s || s < 0 || (int64_t)e > nnz) {
+            if (lane == 0) atomicOr(bad, 1u);
+            continue;
+        }
+        for (int32_t a0 = s; a0 < e; a0 += 32) {
+            const int32_t ka = a0 + lane;
+            const int32_t ca = ka < e ? col[ka] : -1;
+            if (ka < e && (ca < 0 || (int64_t)ca >= d)) atomicOr(bad, 2u);
+            for (int32_t b0 = a0; b0 < e; b0 += 32) {
+                const int32_t kb = b0 + lane;
+                const int32_t cb = kb < e ? col[kb] : -2;
+                for (int q = 0; q < 32; ++q) {
+                    const int32_t other = __shfl_sync(0xFFFFFFFFu, cb, q);
+                    const int32_t ko = b0 + q;
+                    if (ka < e && ko < e && ko > ka && other == ca) atomicOr(bad, 4u);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace cw
+
+extern "C" int cw_csr_check(const cw_csr* A, cw_stream stream) {
+    if (!A) return CW_ERR_ARG;
+    if (A->n < 0 || A->d < 0 || A->nnz < 0) return CW_ERR_SHAPE;
+    if (A->n > 0x7FFFFFFFll - 1 || A->nnz > 0x7FFFFFFFll) return CW_ERR_OVERFLOW;
+    if (!A->row_ptr || (A->nnz > 0 && !A->col)) return CW_ERR_ARG;
+    Scratch ws(stream);
+    const size_t o = ws.reserve(sizeof(unsigned));
+    CW_CUDA_TRY(ws.alloc());
+    unsigned* bad = ws.at<unsigned>(o);
+    CW_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned), stream));
+    const int64_t warps = A->n > 0 ? A->n : 1;
+    const int64_t blocks = std::min<int64_t>((warps + 7) / 8, 65535);
+    k_csr_check<<<(unsigned)blocks, 256, 0, stream>>>(A->row_ptr, A->col, A->n, A->d, A->nnz, bad);
+    CW_LAUNCH_CHECK();
+    unsigned h = 0;
+    CW_CUDA_TRY(cudaMemcpyAsync(&h, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
+    CW_CUDA_TRY(cudaStreamSynchronize(stream));
+    return h ? CW_ERR_ARG : CW_OK;
 }

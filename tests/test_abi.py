@@ -1,0 +1,74 @@
+"""The C-ABI library loads and exports every function include/cw.h declares.
+
+Runs without a GPU: loading libcw.so needs only the CUDA runtime library, and
+the argument checks below return before any device call.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1207_6365_gb300 as cw
+
+HEADER = cw.HEADER
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cw_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("cw_sketch_csr", "cw_sketch_dense", "cw_sketch_vec", "cw_solve_sketch", "cw_lsqr_precond",
+              "cw_leverage", "cw_hash", "cw_qr"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = cw.load()
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(cw.EXPORTS) <= set(_declared())
+
+
+def test_status_strings_and_version():
+    lib = cw.load()
+    assert lib.cw_version() >= 100
+    for code in range(-9, 1):
+        assert cw.status_string(code).startswith("CW_")
+    assert "unknown" in cw.status_string(-42)
+
+
+def test_host_side_validation_rejects_bad_arguments():
+    lib = cw.load()
+    null = None
+    # m < 1, negative counts, overflowing index ranges: rejected before any launch
+    assert lib.cw_hash(1, 0, 0, 10, null, null, null) == -2
+    assert lib.cw_hash(1, 10, -1, 10, null, null, null) == -3
+    assert lib.cw_hash(1, 10, 2**62, 10, null, null, null) == -3
+    assert lib.cw_sketch_csr(null, null, 10, 1, null, null, null) == -1
+    c = cw._CSR()
+    c.n, c.d, c.nnz = 10, 4, 10
+    assert lib.cw_sketch_csr(ctypes.byref(c), null, 0, 1, ctypes.c_void_p(16), null, null) == -2
+    assert lib.cw_sketch_csr(ctypes.byref(c), null, 1 << 20, 1, ctypes.c_void_p(16), null, null) == -2
+    c.nnz = 2**31
+    assert lib.cw_sketch_csr(ctypes.byref(c), null, 8, 1, ctypes.c_void_p(16), null, null) == -3
+    assert lib.cw_sketch_dense(null, 10, 4, 2, null, 8, 1, ctypes.c_void_p(16), null, null) == -1
+    assert lib.cw_sketch_dense(ctypes.c_void_p(16), 10, 4, 2, null, 8, 1, ctypes.c_void_p(16), null, null) == -2
+    assert lib.cw_qr(ctypes.c_void_p(16), 4, 8, null, null, null, null) == -2
+    it = ctypes.c_int32(0)
+    ft = ctypes.c_double(0)
+    c.nnz = 10
+    assert lib.cw_lsqr_precond(ctypes.byref(c), ctypes.c_void_p(16), 64, 1, -1.0, 10, ctypes.c_void_p(16),
+                               ctypes.byref(it), ctypes.byref(ft), null) == -1
+    assert lib.cw_leverage(ctypes.c_void_p(16), 100, 8, 8, 64, 1, 0, ctypes.c_void_p(16), ctypes.c_void_p(16),
+                           null) == -2
+
+
+def test_built_for_sm103a():
+    from paper_1207_6365_gb300 import _build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
+    assert os.path.exists(_build.LIB)
