@@ -1,0 +1,460 @@
+#!/usr/bin/env python
+"""Benchmark of the sparse-embedding least-squares hot path on GB300.
+
+Workload (the large sparse regression configuration): CSR A with n = 2^24 rows,
+d = 256 columns, exactly 16 distinct columns per row drawn from Zipf(1.1),
+N(0,1) float32 values, b = A x0 + 0.01 N(0,1); CountSketch with m = 65536
+rows (hash seed 1); least squares by LSQR preconditioned with R from SA, to
+the relative normal-equation residual 1e-6.
+
+One step = one call of cw_lsqr_precond: hash + bucket sort + SA/Sb + R + the
+sketch-and-solve start + LSQR iterations, i.e. every step of the path on one
+synthetic input already resident in HBM.  value = nnz(A) processed per second
+(summed over ranks).  e2e = the same through the C ABI with the CSR arrays and
+b copied from pinned host memory every step and x copied back.
+
+Under torchrun each rank solves its own replica (weak scaling; the path needs
+no collective when problems are independent).  ``--impl reference`` times the
+float64 CPU oracle on a bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("SA nnz/s and HBM GB/s vs peak; solve time at residual ratio ≤1+ε, learned vs plain sketch")
+WORKLOAD = ("large sparse regression: CSR n=2^24 x d=256, 16 distinct Zipf(1.1) columns/row, N(0,1) fp32, "
+            "b=A x0+0.01 noise, CountSketch m=65536 seed 1, LSQR preconditioned by R from SA to rtol 1e-6")
+N_ROWS, D, K_NNZ, ZIPF_S, M, SEED, RTOL = 1 << 24, 256, 16, 1.1, 65536, 1, 1e-6
+DATA_SEED_A, DATA_SEED_B = 1002, 2002
+SAMPLE_ROWS_BASELINE = 1 << 22   # cpu_baseline leg: rows of the same workload
+SAMPLE_ROWS_REFERENCE = 1 << 20  # --impl reference: rows per step
+
+# kernels reported in the stage breakdown, with their algorithmic bytes per launch
+# (a function of the workload): each byte of A read once, vectors read/written once
+def _alg_bytes(kernel, n, d, nnz, m):
+    if kernel == "k_lsqr_pass":
+        # col + val, row_ptr, z (or b) read, z written
+        return nnz * 8 + (n + 1) * 4 + n * 4 + n * 4
+    if kernel == "k_apply_csr":
+        # col + val gathered once, SA and Sb written
+        return nnz * 8 + m * d * 4 + m * 4
+    if kernel == "k_coarse_scatter":
+        # row_ptr and b read (the per-row records it writes are sort overhead)
+        return (n + 1) * 4 + n * 4
+    return None
+
+
+TIMED_KERNELS = ("k_lsqr_pass", "k_apply_csr", "k_coarse_scatter", "k_tile_hist", "k_lsqr_post",
+                 "k_gram_partial", "k_cholesky_upper", "k_qr_householder", "k_scan_tiles", "k_scan_bins",
+                 "k_scan_chunk_sums", "k_trsm_upper", "k_trsv_upper", "k_gram_reduce")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("cw", "reference"), default="cw")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+
+
+def barrier(world, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    """Largest value of x over all ranks (plain float for world == 1)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world, device=None):
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "cw_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                mx.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- peaks and profiles
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1207_6365_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch recorded by an ncu capture of the current sources, else None."""
+    path = os.path.join(ROOT, "profiles", "%s__large_sparse.md" % kernel)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    mh = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    mt = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not mh or not mt or mh.group(1) != source_hash():
+        return None
+    return float(mt.group(1))
+
+
+# ---------------------------------------------------------------- workload
+
+def make_problem(device, rows=N_ROWS, replica=0):
+    import workloads as W
+    A = W.csr_zipf(rows, D, K_NNZ, ZIPF_S, seed=DATA_SEED_A + 7919 * replica, device=device)
+    b, _ = W.rhs(A, 0.01, seed=DATA_SEED_B + 7919 * replica)
+    return A, b
+
+
+# ---------------------------------------------------------------- oracle (CPU) timing
+
+def oracle_step(A_np, b_np, d, m, seed, rtol):
+    """The float64 CPU oracle's version of one step; returns LSQR iterations."""
+    import oracle
+    rp, col, val = A_np
+    SA, Sb = oracle.sketch_csr(rp, col, val, d, b_np, m, seed)
+    x0, R = oracle.solve_sketch(SA, Sb)
+    x, it, test, conv, _ = oracle.lsqr_precond_csr(rp, col, val, d, b_np, R, x0, rtol, 100)
+    return it
+
+
+def oracle_worker(rows, steps):
+    """Runs in a child process with single-threaded BLAS; prints one JSON line."""
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    A, b = make_problem(dev, rows=rows)
+    A_np = A.numpy()
+    b_np = b.cpu().numpy()
+    import oracle
+    oracle.build()
+    ts, its = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        its.append(oracle_step(A_np, b_np, D, M, SEED, RTOL))
+        ts.append(time.perf_counter() - t0)
+    nnz = int(A_np[0][-1])
+    print(json.dumps({"rows": rows, "nnz": nnz, "times": ts, "iters": its}))
+
+
+def run_oracle_child(rows, steps):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        env.pop(k, None)
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", str(rows),
+                          "--oracle-steps", str(steps)], env=env, capture_output=True, text=True, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError("oracle worker failed:\n" + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_block(res, sample_desc):
+    tot = sum(res["times"])
+    return {"value": res["nnz"] * len(res["times"]) / tot, "unit": "nnz/s", "cores": 1, "kind": "oracle",
+            "sample": sample_desc, "seconds": tot, "lsqr_iters": res["iters"][-1]}
+
+
+# ---------------------------------------------------------------- main arms
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    steps, warm = max(1, args.steps), max(0, args.warmup)
+    res = run_oracle_child(SAMPLE_ROWS_REFERENCE, steps + warm)
+    res["times"] = res["times"][warm:]
+    sample = ("first 2^20 rows of the workload per step (same d, m, seed, Zipf columns, rtol); float64 CPU "
+              "oracle: C sketch loop, LAPACK QR, LSQR with C matvecs; 1 thread")
+    cb = cpu_baseline_block(res, sample)
+    v = cb["value"]
+    ms = 1000.0 * sum(res["times"]) / len(res["times"])
+    line = {"metric": METRIC, "value": v, "unit": "nnz/s", "n_gpus": world, "steps": steps, "warmup": warm,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_rows": SAMPLE_ROWS_REFERENCE, "n": N_ROWS, "d": D,
+                       "m": M, "rtol": RTOL},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_cw(args):
+    import torch
+    import paper_1207_6365_gb300 as cw
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist_init(world, "nccl")
+    cw.load()
+
+    A, b = make_problem("cuda", replica=rank)
+    n, nnz = A.n, A.nnz
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return cw.cw_lsqr_precond(A, b, M, SEED, rtol=RTOL, max_iter=100)
+
+    for _ in range(args.warmup):
+        x, it, test = step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    cw.profile_reset()
+    cw.profile_enable(True)
+    l0 = cw.launch_count()
+    barrier(world, device)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        x, it, test = step()
+        iters.append(it)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world, device)
+    clk = clocks.stop()
+    cw.profile_enable(False)
+    launches = cw.launch_count() - l0
+    ms_local = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms_local, world, device)
+    launches_all = sum_over_ranks(launches, world, device)
+    value = nnz * args.steps * world / (ms_max / 1000.0)
+
+    stages = {}
+    for kname in TIMED_KERNELS:
+        cnt, tot = cw.profile_get(kname)
+        if cnt:
+            stages[kname] = {"launches_per_step": cnt / args.steps, "ms_per_step": tot / args.steps,
+                             "avg_ms": tot / cnt}
+    dom = max(stages, key=lambda k: stages[k]["ms_per_step"]) if stages else None
+    peak, peak_kind = measured_peak_hbm()
+    roofline = None
+    if dom is not None and _alg_bytes(dom, n, D, nnz, M) is not None:
+        alg = _alg_bytes(dom, n, D, nnz, M)
+        ach = alg / (stages[dom]["avg_ms"] / 1000.0) / 1e9
+        tr = ncu_traffic(dom)
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "peak_source": peak_kind, "alg_bytes_per_launch": alg,
+                    "traffic": tr}
+    for kname, st in stages.items():
+        ab = _alg_bytes(kname, n, D, nnz, M)
+        if ab is not None:
+            st["alg_GBps"] = ab / (st["avg_ms"] / 1000.0) / 1e9
+            st["frac_of_peak"] = st["alg_GBps"] / peak
+
+    # sketch alone (SA + Sb through cw_sketch_csr), for the SA nnz/s figure
+    SA = torch.empty(M, D, device=device)
+    Sb = torch.empty(M, device=device)
+    for _ in range(2):
+        cw.cw_sketch_csr(A, b, M, SEED, SA, Sb)
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    reps = 5
+    for _ in range(reps):
+        cw.cw_sketch_csr(A, b, M, SEED, SA, Sb)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    sk_ms = s0.elapsed_time(s1) / reps
+    sk_bytes = nnz * 8 + (n + 1) * 4 + n * 4 + M * D * 4 + M * 4
+    del SA, Sb
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        rp_h = A.row_ptr.cpu().pin_memory()
+        col_h = A.col.cpu().pin_memory()
+        val_h = A.val.cpu().pin_memory()
+        b_h = b.cpu().pin_memory()
+        import workloads as W
+        Ad = W.CSR(n, D, torch.empty_like(A.row_ptr), torch.empty_like(A.col), torch.empty_like(A.val))
+        bd = torch.empty_like(b)
+        h2d = rp_h.numel() * 4 + col_h.numel() * 4 + val_h.numel() * 4 + b_h.numel() * 4
+        d2h = D * 8
+
+        def e2e_step():
+            Ad.row_ptr.copy_(rp_h, non_blocking=True)
+            Ad.col.copy_(col_h, non_blocking=True)
+            Ad.val.copy_(val_h, non_blocking=True)
+            bd.copy_(b_h, non_blocking=True)
+            xx, _, _ = cw.cw_lsqr_precond(Ad, bd, M, SEED, rtol=RTOL, max_iter=100)
+            return xx.cpu()
+
+        e2e_step()
+        torch.cuda.synchronize()
+        esteps = max(1, min(args.steps, 5))
+        barrier(world, device)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(esteps):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world, device)
+        ems = max_over_ranks(f0.elapsed_time(f1), world, device)
+        e2e = {"value": nnz * esteps * world / (ems / 1000.0), "unit": "nnz/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": esteps, "ms_per_step": ems / esteps}
+        del Ad, bd, rp_h, col_h, val_h, b_h
+
+    cpu_baseline = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            res = run_oracle_child(SAMPLE_ROWS_BASELINE, 1)
+            cpu_baseline = cpu_baseline_block(
+                res, "first 2^22 rows of the workload (same d, m, seed, Zipf columns, rtol): float64 CPU oracle "
+                     "(C sketch loop, LAPACK QR, LSQR with C matvecs), one step, 1 thread")
+        except Exception as exc:  # report, do not hide, a failed baseline
+            cpu_baseline = {"error": str(exc)[-300:]}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": n, "d": D, "nnz": nnz, "m": M, "rtol": RTOL,
+                           "l2": "inputs (2.3 GB of CSR and b) larger than the 129 MB L2; no flush",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clk,
+                "gpu_launches": int(launches_all), "lsqr_iters": iters[-1] if iters else None,
+                "sketch": {"ms": sk_ms, "nnz_per_s": nnz / (sk_ms / 1000.0),
+                           "alg_GBps": sk_bytes / (sk_ms / 1000.0) / 1e9,
+                           "frac_of_peak": sk_bytes / (sk_ms / 1000.0) / 1e9 / peak},
+                "stages": stages}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.oracle_worker:
+        oracle_worker(args.oracle_worker, args.oracle_steps)
+        return 0
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_cw(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -189,6 +189,21 @@ int cw_lsqr_precond(const cw_csr *A, const float *b, int64_t m, uint64_t seed, d
 int cw_leverage(const float *A, int64_t n, int64_t d, int64_t lda, int64_t m, uint64_t seed,
                 int32_t k, const double *G, float *lev, cw_stream stream);
 
+/*
+ * Measurement hooks (not part of the paper's method).
+ * cw_launch_count: number of kernels this library has launched in the process.
+ * cw_profile_enable: while enabled, every kernel launch of the library is
+ *   bracketed by two CUDA events recorded on its launching stream.
+ * cw_profile_get: launches and summed event-measured milliseconds of the named
+ *   kernel (e.g. "k_lsqr_pass", "k_apply_csr") since the last reset; waits for
+ *   the recorded events.  Unknown names give zero.
+ * cw_profile_reset: forget all recorded durations.
+ */
+long long cw_launch_count(void);
+int cw_profile_enable(int enable);
+int cw_profile_get(const char *kernel, long long *launches, double *total_ms);
+int cw_profile_reset(void);
+
 #ifdef __cplusplus
 }
 #endif

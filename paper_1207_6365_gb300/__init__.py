@@ -27,7 +27,8 @@ HEADER = os.path.join(_build.ROOT, "include", "cw.h")
 EXPORTS = (
     "cw_status_string", "cw_version", "cw_device_status", "cw_csr_check", "cw_hash", "cw_sketch_csr",
     "cw_sketch_csr_rows", "cw_sketch_dense", "cw_sketch_vec", "cw_qr", "cw_solve_sketch",
-    "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
+    "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage", "cw_launch_count", "cw_profile_enable",
+    "cw_profile_get", "cw_profile_reset",
 )
 
 
@@ -61,6 +62,10 @@ _SIGS = {
     "cw_lsqr_precond": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _f64, _i32, _p,
                          ctypes.POINTER(_i32), ctypes.POINTER(_f64), _p], ctypes.c_int),
     "cw_leverage": ([_p, _i64, _i64, _i64, _i64, _u64, _i32, _p, _p, _p], ctypes.c_int),
+    "cw_launch_count": ([], ctypes.c_longlong),
+    "cw_profile_enable": ([ctypes.c_int], ctypes.c_int),
+    "cw_profile_get": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_f64)], ctypes.c_int),
+    "cw_profile_reset": ([], ctypes.c_int),
 }
 
 
@@ -255,3 +260,26 @@ def cw_leverage(A, m, seed, G):
                               _ptr(G, torch.float64, "G"), _ptr(lev, torch.float32, "lev"), _stream()),
            "cw_leverage")
     return lev
+
+
+# ---------------------------------------------------------------- measurement hooks
+
+def launch_count():
+    """Kernels launched by the library so far in this process."""
+    return int(load().cw_launch_count())
+
+
+def profile_enable(on=True):
+    load().cw_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    load().cw_profile_reset()
+
+
+def profile_get(kernel):
+    """(launches, total milliseconds) of a named library kernel since the last reset."""
+    n = ctypes.c_longlong(0)
+    ms = ctypes.c_double(0.0)
+    _check(load().cw_profile_get(kernel.encode(), ctypes.byref(n), ctypes.byref(ms)), "cw_profile_get")
+    return int(n.value), float(ms.value)

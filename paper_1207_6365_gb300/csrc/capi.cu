@@ -1,5 +1,11 @@
-// Status strings, version and the per-device sticky status word.
+// Status strings, version, the per-device sticky status word, and the
+// measurement hooks (kernel launch counter, CUDA-event timing of named kernels).
+#include <atomic>
+#include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
+#include <vector>
 
 #include "cw_common.cuh"
 
@@ -31,9 +37,101 @@ unsigned* device_status_word() {
     return g_status[dev];
 }
 
+// ---------------------------------------------------------------- measurement hooks
+
+namespace {
+std::atomic<long long> g_launches{0};
+std::atomic<int> g_prof_on{0};
+std::mutex g_prof_mu;
+struct Pending {
+    std::string name;
+    cudaEvent_t a, b;
+};
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_free_events;
+struct Tot {
+    long long launches = 0;
+    double ms = 0.0;
+};
+std::map<std::string, Tot> g_tot;
+
+cudaEvent_t take_event() {
+    if (!g_free_events.empty()) {
+        cudaEvent_t e = g_free_events.back();
+        g_free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void resolve_pending_locked() {
+    for (auto& p : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            Tot& t = g_tot[p.name];
+            t.launches += 1;
+            t.ms += ms;
+        } else {
+            (void)cudaGetLastError();
+        }
+        g_free_events.push_back(p.a);
+        g_free_events.push_back(p.b);
+    }
+    g_pending.clear();
+}
+}  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+ProfScope::ProfScope(const char* name, cudaStream_t s) : name_(name), s_(s), a_(nullptr) {
+    count_launch();
+    if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    a_ = take_event();
+    if (a_) cudaEventRecord((cudaEvent_t)a_, s_);
+}
+
+ProfScope::~ProfScope() {
+    if (!a_) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEvent_t b = take_event();
+    if (!b) return;
+    cudaEventRecord(b, s_);
+    g_pending.push_back(Pending{name_, (cudaEvent_t)a_, b});
+}
+
 }  // namespace cw
 
 extern "C" {
+
+long long cw_launch_count(void) { return cw::g_launches.load(); }
+
+int cw_profile_enable(int enable) {
+    cw::g_prof_on.store(enable ? 1 : 0);
+    return CW_OK;
+}
+
+int cw_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(cw::g_prof_mu);
+    cw::resolve_pending_locked();
+    cw::g_tot.clear();
+    return CW_OK;
+}
+
+int cw_profile_get(const char* kernel, long long* launches, double* total_ms) {
+    if (!kernel) return CW_ERR_ARG;
+    std::lock_guard<std::mutex> lk(cw::g_prof_mu);
+    cw::resolve_pending_locked();
+    auto it = cw::g_tot.find(kernel);
+    if (launches) *launches = it == cw::g_tot.end() ? 0 : it->second.launches;
+    if (total_ms) *total_ms = it == cw::g_tot.end() ? 0.0 : it->second.ms;
+    return CW_OK;
+}
 
 const char* cw_status_string(int status) {
     switch (status) {

@@ -176,6 +176,29 @@ __device__ __forceinline__ void flag_error(unsigned* st, unsigned bit) {
         if (_e != cudaSuccess) return CW_ERR_CUDA; \
     } while (0)
 
+// ---------------------------------------------------------------- measurement hooks
+
+// Every kernel launch of the library sits inside a ProfScope: it counts the
+// launch and, while profiling is enabled, brackets it with CUDA events recorded
+// on the launching stream (durations accumulate per kernel name).
+void count_launch();
+class ProfScope {
+  public:
+    ProfScope(const char* name, cudaStream_t s);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+
+  private:
+    const char* name_;
+    cudaStream_t s_;
+    void* a_;
+};
+
+#define CW_PROF_CAT2(a, b) a##b
+#define CW_PROF_CAT(a, b) CW_PROF_CAT2(a, b)
+#define CW_PROF(name, stream) ::cw::ProfScope CW_PROF_CAT(_cw_prof_scope_, __LINE__)(name, stream)
+
 // ---------------------------------------------------------------- stream-ordered scratch
 
 // Scratch arena: one cudaMallocAsync on the call's stream, carved into

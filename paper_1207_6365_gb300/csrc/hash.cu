@@ -39,7 +39,10 @@ extern "C" int cw_hash(uint64_t seed, int64_t m, int64_t i0, int64_t count, int3
     const int64_t warps = (count + cw::kHashRowsPerWarp - 1) / cw::kHashRowsPerWarp;
     const int64_t blocks = (warps + 7) / 8;
     if (blocks > 0x7FFFFFFFll) return CW_ERR_OVERFLOW;
-    cw::k_hash<<<(unsigned)blocks, 256, 0, stream>>>(hp, i0, count, bucket, sign);
+    {
+        CW_PROF("k_hash", stream);
+        cw::k_hash<<<(unsigned)blocks, 256, 0, stream>>>(hp, i0, count, bucket, sign);
+    }
     CW_LAUNCH_CHECK();
     return CW_OK;
 }

@@ -150,7 +150,10 @@ extern "C" int cw_leverage(const float* A, int64_t n, int64_t d, int64_t lda, in
     st = trsm_upper(R, di, G, k, M, stream);
     if (st != CW_OK) return st;
     const int64_t cnt = (int64_t)di * k;
-    k_split_m<<<(unsigned)((cnt + 255) / 256), 256, 0, stream>>>(M, cnt, Mhi, Mlo);
+    {
+        CW_PROF("k_split_m", stream);
+        k_split_m<<<(unsigned)((cnt + 255) / 256), 256, 0, stream>>>(M, cnt, Mhi, Mlo);
+    }
     CW_LAUNCH_CHECK();
     if (n > 0) {
         const size_t smem = sizeof(float) * ((size_t)kLevJC * 32 * 2 + (size_t)kLevWarps * kLevRPW * kLevJC);
@@ -160,7 +163,10 @@ extern "C" int cw_leverage(const float* A, int64_t n, int64_t d, int64_t lda, in
         const int64_t groups = (n + kLevWarps * kLevRPW - 1) / (kLevWarps * kLevRPW);
         int64_t grid = (int64_t)num_sms() * (per > 0 ? per : 1);
         if (grid > groups) grid = groups;
-        k_leverage<<<(unsigned)grid, kLevWarps * 32, smem, stream>>>(A, n, di, lda, Mhi, Mlo, k, lev);
+        {
+            CW_PROF("k_leverage", stream);
+            k_leverage<<<(unsigned)grid, kLevWarps * 32, smem, stream>>>(A, n, di, lda, Mhi, Mlo, k, lev);
+        }
         CW_LAUNCH_CHECK();
     }
     CW_CUDA_TRY(cudaStreamSynchronize(stream));

@@ -407,9 +407,15 @@ int qr64(const float* SA, int64_t m, int d, const float* Sb, double* R, double* 
     CW_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned) * 4, stream));
     dim3 tb(32, 8), tg((unsigned)((m + 31) / 32), (unsigned)((nc + 31) / 32));
     if (SA64)
-        k_to_colmajor64<double><<<tg, tb, 0, stream>>>(SA64, Sb, m, d, nc, W);
+        {
+            CW_PROF("k_to_colmajor64", stream);
+            k_to_colmajor64<double><<<tg, tb, 0, stream>>>(SA64, Sb, m, d, nc, W);
+        }
     else
-        k_to_colmajor64<float><<<tg, tb, 0, stream>>>(SA, Sb, m, d, nc, W);
+        {
+            CW_PROF("k_to_colmajor64", stream);
+            k_to_colmajor64<float><<<tg, tb, 0, stream>>>(SA, Sb, m, d, nc, W);
+        }
     CW_LAUNCH_CHECK();
     QrArgs a{W, m, d, nc, ws.at<double>(oN), ws.at<double>(oD), ws.at<double>(oV), bar, bar + 2};
     CW_CUDA_TRY(cudaFuncSetAttribute(k_qr_householder, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -418,8 +424,14 @@ int qr64(const float* SA, int64_t m, int d, const float* Sb, double* R, double* 
     if ((int64_t)per_sm * num_sms() < G) G = per_sm * num_sms();
     if (G < 1) return CW_ERR_CUDA;
     void* args[] = {&a};
-    CW_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_qr_householder, dim3(G), dim3(threads), args, smem, stream));
-    k_qr_finalize<<<1, 256, 0, stream>>>(W, m, d, nc, R, c, bar + 3);
+    {
+        CW_PROF("k_qr_householder", stream);
+        CW_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_qr_householder, dim3(G), dim3(threads), args, smem, stream));
+    }
+    {
+        CW_PROF("k_qr_finalize", stream);
+        k_qr_finalize<<<1, 256, 0, stream>>>(W, m, d, nc, R, c, bar + 3);
+    }
     CW_LAUNCH_CHECK();
     unsigned flags[2] = {0, 0};
     CW_CUDA_TRY(cudaMemcpyAsync(flags, bar + 2, sizeof(unsigned) * 2, cudaMemcpyDeviceToHost, stream));
@@ -447,12 +459,21 @@ int gram_cholesky(const float* SA, int64_t m, int d, const float* Sb, double* R,
     unsigned* bad = ws.at<unsigned>(oF);
     CW_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned) * 2, stream));
     dim3 gg((unsigned)(ntile * (ntile + 1) / 2), (unsigned)nchunk);
-    k_gram_partial<<<gg, 256, 0, stream>>>(SA, Sb, m, d, nc, ntile, part);
+    {
+        CW_PROF("k_gram_partial", stream);
+        k_gram_partial<<<gg, 256, 0, stream>>>(SA, Sb, m, d, nc, ntile, part);
+    }
     CW_LAUNCH_CHECK();
     const int64_t tot = (int64_t)nc * nc;
-    k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(part, nchunk, nc, Gm);
+    {
+        CW_PROF("k_gram_reduce", stream);
+        k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(part, nchunk, nc, Gm);
+    }
     CW_LAUNCH_CHECK();
-    k_cholesky_upper<<<1, 1024, 0, stream>>>(Gm, d, nc, R, c, bad);
+    {
+        CW_PROF("k_cholesky_upper", stream);
+        k_cholesky_upper<<<1, 1024, 0, stream>>>(Gm, d, nc, R, c, bad);
+    }
     CW_LAUNCH_CHECK();
     unsigned h = 0;
     CW_CUDA_TRY(cudaMemcpyAsync(&h, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
@@ -461,14 +482,20 @@ int gram_cholesky(const float* SA, int64_t m, int d, const float* Sb, double* R,
 }
 
 int trsv_upper(const double* R, int d, const double* rhs, double* x, cudaStream_t stream) {
-    k_trsv_upper<<<1, 256, sizeof(double) * d, stream>>>(R, d, rhs, x);
+    {
+        CW_PROF("k_trsv_upper", stream);
+        k_trsv_upper<<<1, 256, sizeof(double) * d, stream>>>(R, d, rhs, x);
+    }
     CW_LAUNCH_CHECK();
     return CW_OK;
 }
 
 // X = R^-1 B (B d x k row-major; B == NULL gives the inverse, k == d).
 int trsm_upper(const double* R, int d, const double* B, int k, double* X, cudaStream_t stream) {
-    k_trsm_upper<<<k, 256, sizeof(double) * d, stream>>>(R, d, B, k, X);
+    {
+        CW_PROF("k_trsm_upper", stream);
+        k_trsm_upper<<<k, 256, sizeof(double) * d, stream>>>(R, d, B, k, X);
+    }
     CW_LAUNCH_CHECK();
     return CW_OK;
 }

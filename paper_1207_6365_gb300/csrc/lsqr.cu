@@ -428,9 +428,15 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     st = trsm_upper(R, d, nullptr, d, M, stream);  // M = R^-1
     if (st != CW_OK) return st;
     const int64_t dd = (int64_t)d * d;
-    k_to_f32_transposed<<<(unsigned)((dd + 255) / 256), 256, 0, stream>>>(M, d, M32T, vhat, x0);
+    {
+        CW_PROF("k_to_f32_transposed", stream);
+        k_to_f32_transposed<<<(unsigned)((dd + 255) / 256), 256, 0, stream>>>(M, d, M32T, vhat, x0);
+    }
     CW_LAUNCH_CHECK();
-    k_upper_matvec<<<(d + 127) / 128, 128, 0, stream>>>(R, d, x0, y0, nullptr);
+    {
+        CW_PROF("k_upper_matvec", stream);
+        k_upper_matvec<<<(d + 127) / 128, 128, 0, stream>>>(R, d, x0, y0, nullptr);
+    }
     CW_LAUNCH_CHECK();
 
     const size_t pass_smem = sizeof(float) * (size_t)dpad * (1 + nsub);
@@ -438,12 +444,18 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     CW_CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem));
     PassArgs pa{A->row_ptr, A->col, A->val, vhat, b, z, ws.at<double>(ogp), ws.at<double>(ozp), ws.at<double>(obp),
                 nullptr, status, n, d, dpad, 1.0f};
-    pk<<<grid, threads, pass_smem, stream>>>(pa);  // z = A x0 - b
+    {
+        CW_PROF("k_lsqr_pass", stream);
+        pk<<<grid, threads, pass_smem, stream>>>(pa);  // z = A x0 - b
+    }
     CW_LAUNCH_CHECK();
     PostArgs qa{ws.at<double>(ogp), ws.at<double>(ozp), ws.at<double>(obp), grid, d, M, M32T, y0,
                 ws.at<double>(ov), ws.at<double>(ow), ws.at<double>(ody), ws.at<double>(og), vhat, state, rtol,
                 max_iter, 1};
-    k_lsqr_post<<<1, 1024, 0, stream>>>(qa);
+    {
+        CW_PROF("k_lsqr_post", stream);
+        k_lsqr_post<<<1, 1024, 0, stream>>>(qa);
+    }
     CW_LAUNCH_CHECK();
     pa.zin = z;
     pa.st = state;
@@ -459,14 +471,23 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
         if (hs.done || launched >= max_iter) break;
         const int nb = (max_iter - launched) < batch ? (max_iter - launched) : batch;
         for (int q = 0; q < nb; ++q) {
-            pk<<<grid, threads, pass_smem, stream>>>(pa);
-            k_lsqr_post<<<1, 1024, 0, stream>>>(qa);
+            {
+                CW_PROF("k_lsqr_pass", stream);
+                pk<<<grid, threads, pass_smem, stream>>>(pa);
+            }
+            {
+                CW_PROF("k_lsqr_post", stream);
+                k_lsqr_post<<<1, 1024, 0, stream>>>(qa);
+            }
         }
         CW_LAUNCH_CHECK();
         launched += nb;
     }
     // x = x0 + M dy
-    k_upper_matvec<<<(d + 127) / 128, 128, 0, stream>>>(M, d, ws.at<double>(ody), x, x0);
+    {
+        CW_PROF("k_upper_matvec", stream);
+        k_upper_matvec<<<(d + 127) / 128, 128, 0, stream>>>(M, d, ws.at<double>(ody), x, x0);
+    }
     CW_LAUNCH_CHECK();
     CW_CUDA_TRY(cudaStreamSynchronize(stream));
     if (iters) *iters = hs.iters;

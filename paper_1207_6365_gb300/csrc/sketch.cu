@@ -921,14 +921,26 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     float* rb = has_b ? ws.at<float>(oB) : nullptr;
     int32_t* bptr = bucket_ptr_out ? bucket_ptr_out : ws.at<int32_t>(oBP);
 
-    k_tile_hist<<<p.ntiles, 256, 0, stream>>>(hp, i0, n, p.gshift, p.nbins, H);
+    {
+        CW_PROF("k_tile_hist", stream);
+        k_tile_hist<<<p.ntiles, 256, 0, stream>>>(hp, i0, n, p.gshift, p.nbins, H);
+    }
     CW_LAUNCH_CHECK();
     dim3 sg((p.nbins + 255) / 256, p.nchunks);
-    k_scan_chunk_sums<<<sg, 256, 0, stream>>>(H, p.ntiles, p.nbins, P);
+    {
+        CW_PROF("k_scan_chunk_sums", stream);
+        k_scan_chunk_sums<<<sg, 256, 0, stream>>>(H, p.ntiles, p.nbins, P);
+    }
     CW_LAUNCH_CHECK();
-    k_scan_bins<<<1, 1024, 0, stream>>>(P, p.nchunks, p.nbins, CP, (uint32_t)n);
+    {
+        CW_PROF("k_scan_bins", stream);
+        k_scan_bins<<<1, 1024, 0, stream>>>(P, p.nchunks, p.nbins, CP, (uint32_t)n);
+    }
     CW_LAUNCH_CHECK();
-    k_scan_tiles<<<sg, 256, 0, stream>>>(H, P, p.ntiles, p.nbins);
+    {
+        CW_PROF("k_scan_tiles", stream);
+        k_scan_tiles<<<sg, 256, 0, stream>>>(H, P, p.ntiles, p.nbins);
+    }
     CW_LAUNCH_CHECK();
 
     const size_t k3smem = sizeof(uint32_t) * kTileWarps * p.nbins;
@@ -936,6 +948,7 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     do {                                                                                            \
         auto kf = k_coarse_scatter<MODE, HB>;                                                       \
         CW_CUDA_TRY(set_smem(kf, k3smem));                                                          \
+        CW_PROF("k_coarse_scatter", stream);                                                        \
         kf<<<p.ntiles, 256, k3smem, stream>>>(hp, i0, n, p.gshift, p.nbins, H, row_ptr, b, rkey, ra, \
                                               rlen, rb, status);                                    \
     } while (0)
@@ -957,6 +970,7 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     do {                                                                  \
         auto kf = k_apply_csr<LPR, 8, HB>;                                \
         CW_CUDA_TRY(set_smem(kf, p.smem));                                \
+        CW_PROF("k_apply_csr", stream);                                   \
         kf<<<p.nbins, threads, p.smem, stream>>>(a);                      \
     } while (0)
         if (p.lpr == 16) {
@@ -975,12 +989,14 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     do {                                                                  \
         auto kf = k_apply_dense<NV, U, HB, false>;                        \
         CW_CUDA_TRY(set_smem(kf, p.smem));                                \
+        CW_PROF("k_apply_dense", stream);                                 \
         kf<<<p.nbins, threads, p.smem, stream>>>(a);                      \
     } while (0)
 #define CW_K4P(NV, U)                                                     \
     do {                                                                  \
         auto kf = k_apply_dense<NV, U, false, true>;                      \
         CW_CUDA_TRY(set_smem(kf, p.smem));                                \
+        CW_PROF("k_apply_dense_precise", stream);                         \
         kf<<<p.nbins, threads, p.smem, stream>>>(a);                      \
     } while (0)
         if (SA64) {
@@ -998,10 +1014,14 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     } else {
         auto kf = k_apply_vec;
         CW_CUDA_TRY(set_smem(kf, p.smem));
+        CW_PROF("k_apply_vec", stream);
         kf<<<p.nbins, p.warps * 32, p.smem, stream>>>(rkey, rb, CP, m, p.gshift, p.cap, Sb, bptr);
     }
     CW_LAUNCH_CHECK();
-    k_set_last<<<1, 1, 0, stream>>>(bptr, m, (int32_t)n);
+    {
+        CW_PROF("k_set_last", stream);
+        k_set_last<<<1, 1, 0, stream>>>(bptr, m, (int32_t)n);
+    }
     CW_LAUNCH_CHECK();
     return CW_OK;
 }
@@ -1103,7 +1123,10 @@ extern "C" int cw_csr_check(const cw_csr* A, cw_stream stream) {
     CW_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned), stream));
     const int64_t warps = A->n > 0 ? A->n : 1;
     const int64_t blocks = std::min<int64_t>((warps + 7) / 8, 65535);
-    k_csr_check<<<(unsigned)blocks, 256, 0, stream>>>(A->row_ptr, A->col, A->n, A->d, A->nnz, bad);
+    {
+        CW_PROF("k_csr_check", stream);
+        k_csr_check<<<(unsigned)blocks, 256, 0, stream>>>(A->row_ptr, A->col, A->n, A->d, A->nnz, bad);
+    }
     CW_LAUNCH_CHECK();
     unsigned h = 0;
     CW_CUDA_TRY(cudaMemcpyAsync(&h, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
