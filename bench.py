@@ -56,9 +56,23 @@ def _alg_bytes(kernel, n, d, nnz, m):
     return None
 
 
-TIMED_KERNELS = ("k_lsqr_pass", "k_apply_csr", "k_coarse_scatter", "k_tile_hist", "k_lsqr_post",
-                 "k_gram_partial", "k_cholesky_upper", "k_qr_householder", "k_scan_tiles", "k_scan_bins",
-                 "k_scan_chunk_sums", "k_trsm_upper", "k_trsv_upper", "k_gram_reduce")
+# bytes each sketch kernel actually has to move (algorithmic + the sort's own
+# records): the per-kernel bandwidth figure reported beside the algorithmic one
+def _moved_bytes(kernel, n, d, nnz, m):
+    if kernel == "k_coarse_scatter":
+        return (n + 1) * 4 + n * 4 + n * 16
+    if kernel == "k_fine_sort":
+        return n * 16 * 2 + n * 12 + m * 4
+    if kernel == "k_apply_csr":
+        return nnz * 8 + n * 12 + m * d * 4 + m * 4 + m * 4
+    return None
+
+
+TIMED_KERNELS = ("k_lsqr_pass", "k_apply_csr", "k_coarse_scatter", "k_fine_sort", "k_tile_hist", "k_lsqr_post",
+                 "k_chol_inv_f32", "k_copy_f32",
+                 "k_gram_partial", "k_cholesky_f32", "k_qr_householder", "k_scan_tiles", "k_scan_bins",
+                 "k_scan_chunk_sums", "k_trsm_upper", "k_trsv_upper", "k_gram_reduce", "k_tri_inverse",
+                 "k_transpose64", "k_upper_matvec", "k_to_f32_transposed", "k_set_last")
 
 
 def parse():
@@ -359,6 +373,9 @@ def run_cw(args):
         if ab is not None:
             st["alg_GBps"] = ab / (st["avg_ms"] / 1000.0) / 1e9
             st["frac_of_peak"] = st["alg_GBps"] / peak
+        mb = _moved_bytes(kname, n, D, nnz, M)
+        if mb is not None:
+            st["moved_GBps"] = mb / (st["avg_ms"] / 1000.0) / 1e9
 
     # sketch alone (SA + Sb through cw_sketch_csr), for the SA nnz/s figure
     SA = torch.empty(M, D, device=device)

@@ -24,5 +24,9 @@ int gram_cholesky(const float* SA, int64_t m, int d, const float* Sb, double* R,
                   cudaStream_t stream);
 int trsv_upper(const double* R, int d, const double* rhs, double* x, cudaStream_t stream);
 int trsm_upper(const double* R, int d, const double* B, int k, double* X, cudaStream_t stream);
+int tri_inverse(const double* R, int d, double* M, cudaStream_t stream);
+// Gram + Cholesky + explicit inverse in shared memory (LSQR preconditioner).
+int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double* M, float* M32T, double* c,
+                      float* kappa_lb_host, cudaStream_t stream);
 
 }  // namespace cw

@@ -332,39 +332,204 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nchunk, int n
     Gm[(int64_t)cj * nc + ci] = s;
 }
 
-// In-place upper Cholesky G = R^T R of the leading d x d block (float64, one
-// CTA, right-looking).  Also forms c = R^-T g for g = G[0:d, d] when nc > d.
-// Flags a non-positive pivot in *bad.
-__global__ void __launch_bounds__(1024) k_cholesky_upper(double* __restrict__ Gm, int d, int nc, double* __restrict__ R,
-                                                        double* __restrict__ c, unsigned* bad) {
+// Upper Cholesky G = R^T R of the leading d x d block of the float64 Gram
+// matrix, computed in float32 by one CTA (right-looking, 32 x 32 thread grid
+// over the trailing block).  The carried column d becomes c = R^-T SA^T Sb.
+// float32 is enough here: this R only preconditions LSQR (any R with
+// SA R^-1 near-orthonormal works), and callers fall back to the float64
+// Householder R when the diagonal signals a large condition number.
+// W: float32 working copy (nc x nc, row-major).  Flags a non-positive pivot.
+__global__ void __launch_bounds__(1024) k_cholesky_f32(const double* __restrict__ Gm, float* __restrict__ W, int d,
+                                                      int nc, double* __restrict__ R, double* __restrict__ c,
+                                                      unsigned* bad) {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int64_t q = threadIdx.x; q < (int64_t)nc * nc; q += blockDim.x) W[q] = (float)Gm[q];
+    __syncthreads();
+    __shared__ float rowj[1025];
+    __shared__ int fail;
+    if (threadIdx.x == 0) fail = 0;
     for (int j = 0; j < d; ++j) {
         __syncthreads();
-        const double piv = Gm[(int64_t)j * nc + j];
-        if (!(piv > 0.0)) {
-            if (threadIdx.x == 0) atomicExch(bad, 1u);
-            return;
+        const float piv = W[(int64_t)j * nc + j];
+        if (!(piv > 0.f)) {
+            if (threadIdx.x == 0) {
+                fail = 1;
+                atomicExch(bad, 1u);
+            }
+            break;
         }
-        const double rjj = sqrt(piv);
+        const float rjj = sqrtf(piv);
+        const float inv = 1.0f / rjj;
+        for (int k = j + threadIdx.x; k < nc; k += blockDim.x) {
+            const float v = (k == j) ? rjj : W[(int64_t)j * nc + k] * inv;
+            W[(int64_t)j * nc + k] = v;
+            rowj[k] = v;
+        }
         __syncthreads();
-        // row j of R: G[j, k] / rjj for k >= j (including the carried column)
-        for (int k = j + threadIdx.x; k < nc; k += blockDim.x) Gm[(int64_t)j * nc + k] = (k == j) ? rjj : Gm[(int64_t)j * nc + k] / rjj;
-        __syncthreads();
-        // trailing update G[i, k] -= R[j, i] R[j, k] for j < i <= k
-        const int rem = d - j - 1;
-        const int64_t tot = (int64_t)rem * (nc - j - 1);
-        for (int64_t q = threadIdx.x; q < tot; q += blockDim.x) {
-            const int i = j + 1 + (int)(q / (nc - j - 1));
-            const int k = j + 1 + (int)(q % (nc - j - 1));
-            if (k >= i) Gm[(int64_t)i * nc + k] -= Gm[(int64_t)j * nc + i] * Gm[(int64_t)j * nc + k];
+        // W[i, k] -= R[j, i] * R[j, k] for j < i <= k
+        for (int i = j + 1 + ty; i < d; i += 32) {
+            const float rji = rowj[i];
+            float* wi = W + (int64_t)i * nc;
+            for (int k = i + tx; k < nc; k += 32) wi[k] -= rji * rowj[k];
         }
     }
     __syncthreads();
+    if (fail) return;
     for (int64_t q = threadIdx.x; q < (int64_t)d * d; q += blockDim.x) {
         const int i = (int)(q / d), k = (int)(q % d);
-        R[q] = (k < i) ? 0.0 : Gm[(int64_t)i * nc + k];
+        R[q] = (k < i) ? 0.0 : (double)W[(int64_t)i * nc + k];
     }
     if (c && nc > d)
-        for (int i = threadIdx.x; i < d; i += blockDim.x) c[i] = Gm[(int64_t)i * nc + d];
+        for (int i = threadIdx.x; i < d; i += blockDim.x) c[i] = (double)W[(int64_t)i * nc + d];
+}
+
+// Fast preconditioner in one CTA, all in shared memory (packed upper triangle,
+// float32): Cholesky G = R^T R of the Gram matrix (with the carried column
+// giving c = R^-T SA^T Sb), then M = R^-1 by Gauss-Jordan elimination on
+// [R | I] (right-looking, one barrier per step).  LSQR iterates on the operator
+// A M itself, so M only has to make A M well conditioned.  Outputs M (float64
+// row-major, upper), M32T (float32 column-major copy), c, and the diagonal
+// ratio max|R_jj| / min|R_jj| (a lower bound of kappa(SA)) in *kappa_lb.
+// Requires (nc + 1) * nc / 2 floats of shared memory.
+__device__ __forceinline__ int tri_off(int i, int nc) { return i * nc - (i * (i - 1)) / 2; }  // row i, col i
+
+__global__ void __launch_bounds__(1024) k_chol_inv_f32(const double* __restrict__ Gm, int d, int nc,
+                                                      double* __restrict__ M, float* __restrict__ M32T,
+                                                      double* __restrict__ c, float* __restrict__ kappa_lb,
+                                                      unsigned* bad) {
+    extern __shared__ float T[];  // packed upper triangle: T[tri_off(i) + (k - i)] = G[i][k], k >= i
+    __shared__ float rowk[1025];
+    __shared__ int fail;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = 0; i < nc; ++i)
+        for (int k = i + tid; k < nc; k += nt) T[tri_off(i, nc) + (k - i)] = (float)Gm[(int64_t)i * nc + k];
+    if (tid == 0) fail = 0;
+    __syncthreads();
+    // Cholesky, row j of R overwrites row j of T
+    for (int j = 0; j < d; ++j) {
+        const int oj = tri_off(j, nc);
+        const float piv = T[oj];
+        if (!(piv > 0.f)) {
+            if (tid == 0) {
+                fail = 1;
+                atomicExch(bad, 1u);
+            }
+            break;
+        }
+        const float inv = rsqrtf(piv);
+        __syncthreads();
+        for (int k = j + tid; k < nc; k += nt) {
+            const float v = (k == j) ? piv * inv : T[oj + (k - j)] * inv;
+            T[oj + (k - j)] = v;
+            rowk[k] = v;
+        }
+        __syncthreads();
+        // T[i][k] -= R[j][i] R[j][k] for j < i <= k < nc, i < d
+        const int rem = d - j - 1;
+        for (int i = j + 1 + tid / 32; i < d; i += nt / 32) {
+            const float rji = rowk[i];
+            float* Ti = T + tri_off(i, nc) - i;
+            for (int k = i + (tid & 31); k < nc; k += 32) Ti[k] -= rji * rowk[k];
+        }
+        (void)rem;
+        __syncthreads();
+    }
+    __syncthreads();
+    if (fail) return;
+    if (tid == 0) {
+        float mx = 0.f, mn = 3.4e38f;
+        for (int j = 0; j < d; ++j) {
+            const float v = fabsf(T[tri_off(j, nc)]);
+            mx = fmaxf(mx, v);
+            mn = fminf(mn, v);
+        }
+        *kappa_lb = mn > 0.f ? mx / mn : 3.4e38f;
+    }
+    if (c && nc > d)
+        for (int i = tid; i < d; i += nt) c[i] = (double)T[tri_off(i, nc) + (d - i)];
+    // Gauss-Jordan on [R | I] from the last row up: row k of M is
+    // e_k / R_kk - sum_{j>k} (R_kj / R_kk) M_j; rows are finished bottom-up.
+    // In place: entry (i, j), j > i, holds M_ij once row i is finished; the
+    // entries (i, j) with i < k <= j accumulate -sum R_ik M_kj as rows k finish.
+    // Implemented as: for k = d-1..0: M_k = (e_k - acc_k) / R_kk, where acc_k
+    // lives in row k; then acc_i += R_ik M_k for i < k.
+    __shared__ float colk[1025];
+    for (int k = d - 1; k >= 0; --k) {
+        __syncthreads();
+        const int ok = tri_off(k, nc);
+        const float rkk = T[ok];
+        // finish row k: M_kk = 1 / R_kk, M_kj = -acc_kj / R_kk for j > k
+        // (acc_kj for j > k was accumulated into T[k][j] after R_kj was saved)
+        for (int i = tid; i < k; i += nt) colk[i] = T[tri_off(i, nc) + (k - i)];  // R_ik, i < k
+        __syncthreads();
+        const float inv = 1.0f / rkk;
+        for (int j = k + tid; j < d; j += nt) {
+            const float v = (j == k) ? inv : -T[ok + (j - k)] * inv;
+            T[ok + (j - k)] = v;
+            rowk[j] = v;
+        }
+        __syncthreads();
+        // acc_ij += R_ik M_kj for i < k, j >= k  (entry (i, k) becomes acc_ik
+        // = R_ik M_kk, entries (i, j > k) accumulate)
+        for (int i = tid / 32; i < k; i += nt / 32) {
+            const float rik = colk[i];
+            float* Ti = T + tri_off(i, nc) - i;
+            for (int j = k + (tid & 31); j < d; j += 32) Ti[j] = (j == k ? 0.f : Ti[j]) + rik * rowk[j];
+        }
+    }
+    __syncthreads();
+    for (int64_t q = tid; q < (int64_t)d * d; q += nt) {
+        const int i = (int)(q / d), j = (int)(q % d);
+        const float v = (j < i) ? 0.f : T[tri_off(i, nc) + (j - i)];
+        M[q] = (double)v;
+        M32T[(int64_t)j * d + i] = v;
+    }
+}
+
+// M = R^-1 for upper-triangular row-major R (float64); one warp per column of
+// M, RT = R^T (column j of R contiguous) for coalesced reads.
+__global__ void k_tri_inverse(const double* __restrict__ RT, int d, double* __restrict__ M) {
+    const int lane = threadIdx.x & 31;
+    const int col = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (col >= d) return;
+    constexpr int kMaxPer = 32;  // d <= 1024
+    double s[kMaxPer];
+    const int per = (d + 31) / 32;
+#pragma unroll
+    for (int q = 0; q < kMaxPer; ++q) s[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < kMaxPer; ++q)
+        if (q < per && lane + 32 * q == col) s[q] = 1.0;
+    for (int j = col; j >= 0; --j) {
+        const int oj = j & 31, qj = j >> 5;
+        double sj = 0.0;
+#pragma unroll
+        for (int q = 0; q < kMaxPer; ++q)
+            if (q == qj) sj = s[q];
+        const double xj = __shfl_sync(0xFFFFFFFFu, sj, oj) / RT[(int64_t)j * d + j];
+#pragma unroll
+        for (int q = 0; q < kMaxPer; ++q) {
+            if (q < per) {
+                const int i = lane + 32 * q;
+                if (i == j)
+                    s[q] = xj;
+                else if (i < j)
+                    s[q] -= RT[(int64_t)j * d + i] * xj;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxPer; ++q) {
+        const int i = lane + 32 * q;
+        if (q < per && i < d) M[(int64_t)i * d + col] = (i <= col) ? s[q] : 0.0;
+    }
+}
+
+__global__ void k_transpose64(const double* __restrict__ A, int d, double* __restrict__ AT) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)d * d) return;
+    const int i = (int)(q / d), j = (int)(q % d);
+    AT[(int64_t)j * d + i] = A[q];
 }
 
 // ---------------------------------------------------------------- host drivers
@@ -452,6 +617,7 @@ int gram_cholesky(const float* SA, int64_t m, int d, const float* Sb, double* R,
     Scratch ws(stream);
     const size_t oP = ws.reserve(sizeof(double) * (size_t)nchunk * nc * nc);
     const size_t oG = ws.reserve(sizeof(double) * (size_t)nc * nc);
+    const size_t oW = ws.reserve(sizeof(float) * (size_t)nc * nc);
     const size_t oF = ws.reserve(sizeof(unsigned) * 2);
     CW_CUDA_TRY(ws.alloc());
     double* part = ws.at<double>(oP);
@@ -471,14 +637,60 @@ int gram_cholesky(const float* SA, int64_t m, int d, const float* Sb, double* R,
     }
     CW_LAUNCH_CHECK();
     {
-        CW_PROF("k_cholesky_upper", stream);
-        k_cholesky_upper<<<1, 1024, 0, stream>>>(Gm, d, nc, R, c, bad);
+        CW_PROF("k_cholesky_f32", stream);
+        k_cholesky_f32<<<1, 1024, 0, stream>>>(Gm, ws.at<float>(oW), d, nc, R, c, bad);
     }
     CW_LAUNCH_CHECK();
     unsigned h = 0;
     CW_CUDA_TRY(cudaMemcpyAsync(&h, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
     CW_CUDA_TRY(cudaStreamSynchronize(stream));
     return h ? CW_ERR_RANK : CW_OK;
+}
+
+// Gram + Cholesky + inverse for the LSQR preconditioner.  M (float64 d x d),
+// M32T (float32, column-major) and c = R^-T SA^T Sb; *kappa_lb receives the
+// diagonal ratio of R.  Returns CW_ERR_RANK on a non-positive pivot and
+// CW_ERR_SHAPE when the packed triangle does not fit in shared memory.
+int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double* M, float* M32T, double* c,
+                      float* kappa_lb_host, cudaStream_t stream) {
+    const int nc = d + (Sb ? 1 : 0);
+    const size_t tsmem = sizeof(float) * ((size_t)nc * (nc + 1) / 2);
+    if (tsmem > 220 * 1024) return CW_ERR_SHAPE;
+    const int ntile = (nc + kGramTile - 1) / kGramTile;
+    const int nchunk = (int)((m + kGramRowsPerChunk - 1) / kGramRowsPerChunk);
+    Scratch ws(stream);
+    const size_t oP = ws.reserve(sizeof(double) * (size_t)nchunk * nc * nc);
+    const size_t oG = ws.reserve(sizeof(double) * (size_t)nc * nc);
+    const size_t oF = ws.reserve(sizeof(unsigned) * 2 + sizeof(float) * 2);
+    CW_CUDA_TRY(ws.alloc());
+    double* part = ws.at<double>(oP);
+    double* Gm = ws.at<double>(oG);
+    unsigned* bad = ws.at<unsigned>(oF);
+    float* klb = reinterpret_cast<float*>(bad + 2);
+    CW_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned) * 2 + sizeof(float) * 2, stream));
+    dim3 gg((unsigned)(ntile * (ntile + 1) / 2), (unsigned)nchunk);
+    {
+        CW_PROF("k_gram_partial", stream);
+        k_gram_partial<<<gg, 256, 0, stream>>>(SA, Sb, m, d, nc, ntile, part);
+    }
+    const int64_t tot = (int64_t)nc * nc;
+    {
+        CW_PROF("k_gram_reduce", stream);
+        k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(part, nchunk, nc, Gm);
+    }
+    CW_CUDA_TRY(cudaFuncSetAttribute(k_chol_inv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
+    {
+        CW_PROF("k_chol_inv_f32", stream);
+        k_chol_inv_f32<<<1, 1024, tsmem, stream>>>(Gm, d, nc, M, M32T, c, klb, bad);
+    }
+    CW_LAUNCH_CHECK();
+    unsigned h[2] = {0, 0};
+    float kl[2] = {0.f, 0.f};
+    CW_CUDA_TRY(cudaMemcpyAsync(h, bad, sizeof(unsigned) * 2, cudaMemcpyDeviceToHost, stream));
+    CW_CUDA_TRY(cudaMemcpyAsync(kl, klb, sizeof(float) * 2, cudaMemcpyDeviceToHost, stream));
+    CW_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (kappa_lb_host) *kappa_lb_host = kl[0];
+    return h[0] ? CW_ERR_RANK : CW_OK;
 }
 
 int trsv_upper(const double* R, int d, const double* rhs, double* x, cudaStream_t stream) {
@@ -488,6 +700,25 @@ int trsv_upper(const double* R, int d, const double* rhs, double* x, cudaStream_
     }
     CW_LAUNCH_CHECK();
     return CW_OK;
+}
+
+// M = R^-1 (upper triangular, float64), one warp per column.
+int tri_inverse(const double* R, int d, double* M, cudaStream_t stream) {
+    if (d > 1024) return CW_ERR_SHAPE;
+    double* RT = nullptr;
+    CW_CUDA_TRY(cudaMallocAsync(&RT, sizeof(double) * (size_t)d * d, stream));
+    const int64_t dd = (int64_t)d * d;
+    {
+        CW_PROF("k_transpose64", stream);
+        k_transpose64<<<(unsigned)((dd + 255) / 256), 256, 0, stream>>>(R, d, RT);
+    }
+    {
+        CW_PROF("k_tri_inverse", stream);
+        k_tri_inverse<<<(unsigned)((d + 7) / 8), 256, 0, stream>>>(RT, d, M);
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(RT, stream);
+    return e == cudaSuccess ? CW_OK : CW_ERR_CUDA;
 }
 
 // X = R^-1 B (B d x k row-major; B == NULL gives the inverse, k == d).

@@ -47,108 +47,223 @@ struct PassArgs {
     float coef_first;      // used when st == nullptr
 };
 
-template <int LPR, int U>
-__global__ void __launch_bounds__(512, 2) k_lsqr_pass(PassArgs a) {
-    constexpr int COPIES = 32 / LPR;
+// ---- cp.async helpers (global -> shared without passing through registers)
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+constexpr int kPassBatch = 32;     // rows per warp batch (one per lane for row_ptr / z)
+constexpr int kPassCap = 640;      // staged nnz per batch (multiple of 4)
+constexpr int kPassStages = 2;
+
+// Copies col/val[s, e) into the stage buffers (element base = s & ~3 at offset
+// 0).  16-byte copies for whole aligned chunks inside [0, nnz), 4-byte copies
+// for the rest.  Every lane of the warp calls this.
+// vec16: col and val are 16-byte aligned (scol / sval always are).
+__device__ __forceinline__ void stage_nnz(const int32_t* __restrict__ col, const float* __restrict__ val,
+                                          int64_t nnz, int64_t s, int64_t e, int32_t* scol, float* sval,
+                                          int lane, bool vec16) {
+    const int64_t base = s & ~3ll;
+    const int64_t end4 = (e + 3) & ~3ll;
+    const int64_t nchunk = (end4 - base) >> 2;
+    for (int64_t q = lane; q < nchunk; q += 32) {
+        const int64_t g = base + 4 * q;
+        if (vec16 && g + 4 <= nnz) {
+            cp_async16(scol + 4 * q, col + g);
+            cp_async16(sval + 4 * q, val + g);
+        } else {
+            for (int t = 0; t < 4; ++t)
+                if (g + t < nnz) {
+                    cp_async4(scol + 4 * q + t, col + g + t);
+                    cp_async4(sval + 4 * q + t, val + g + t);
+                }
+        }
+    }
+}
+
+template <int LPR, int kPassWarps>
+__global__ void __launch_bounds__(kPassWarps * 32, 1) k_lsqr_pass(PassArgs a) {
     extern __shared__ __align__(16) float sm[];
     if (a.st && a.st->done) return;
+    constexpr int HALVES = 32 / LPR;          // rows processed side by side
+    constexpr int RPH = kPassBatch / HALVES;  // rows per sub-warp per batch
     const float coef = a.st ? (float)a.st->coef : a.coef_first;
-    const int nwarps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sub = lane / LPR, sl = lane % LPR;
-    const int NS = nwarps * COPIES;
-    const int sw = warp * COPIES + sub;
-    float* vh = sm;
-    float* acc = sm + a.dpad;
+    float* vh = sm;                                         // [dpad]
+    float* acc = vh + a.dpad;                               // [warps][HALVES][dpad]
+    // stage buffers start on a 128-byte boundary (16-byte cp.async targets)
+    const size_t stage_off = (((size_t)(1 + kPassWarps * HALVES) * a.dpad * sizeof(float)) + 127) & ~size_t(127);
+    int32_t* stage = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(sm) + stage_off);
+    const bool vec16 = ((reinterpret_cast<uintptr_t>(a.col) | reinterpret_cast<uintptr_t>(a.val)) & 15) == 0;
+    int32_t* wst = stage + (size_t)warp * kPassStages * 2 * (kPassCap + 8);
     for (int j = threadIdx.x; j < a.d; j += blockDim.x) vh[j] = a.vhat[j];
-    for (int q = threadIdx.x; q < NS * a.dpad; q += blockDim.x) acc[q] = 0.f;
+    for (int q = threadIdx.x; q < kPassWarps * HALVES * a.dpad; q += blockDim.x) acc[q] = 0.f;
     __syncthreads();
-    float* myacc = acc + (size_t)sw * a.dpad;
+    float* myacc = acc + (size_t)(warp * HALVES + sub) * a.dpad;
 
-    const int64_t per = (a.n + gridDim.x - 1) / gridDim.x;
-    const int64_t r0 = (per * blockIdx.x < a.n) ? per * blockIdx.x : a.n;
-    const int64_t r1 = (r0 + per < a.n) ? r0 + per : a.n;
+    // this warp's contiguous rows
+    const int64_t nw = (int64_t)gridDim.x * kPassWarps;
+    const int64_t gw = (int64_t)blockIdx.x * kPassWarps + warp;
+    const int64_t per = (((a.n + nw - 1) / nw) + kPassBatch - 1) / kPassBatch * kPassBatch;
+    const int64_t w0 = gw * per < a.n ? gw * per : a.n;
+    const int64_t w1 = w0 + per < a.n ? w0 + per : a.n;
+    const int64_t nbatch = (w1 - w0 + kPassBatch - 1) / kPassBatch;
+    const int64_t nnz = a.row_ptr[a.n];
+
+    // batch registers: lane l holds row_ptr[r0 + l], the batch end, z_in[r0 + l]
+    auto load_meta = [&](int64_t k, int32_t& rp, int32_t& rend, float& zo) {
+        rp = 0;
+        rend = 0;
+        zo = 0.f;
+        if (k < nbatch) {
+            const int64_t r0 = w0 + k * kPassBatch;
+            const int64_t r = r0 + lane;
+            const int64_t rl = (r0 + kPassBatch < w1) ? r0 + kPassBatch : w1;
+            if (r < rl) {
+                rp = __ldg(a.row_ptr + r);
+                zo = __ldg(a.zin + r);
+            }
+            rend = __ldg(a.row_ptr + rl);
+        }
+    };
+    auto issue = [&](int64_t k, int32_t rp, int32_t rend) {
+        if (k < nbatch) {
+            const int32_t s0 = __shfl_sync(0xFFFFFFFFu, rp, 0);
+            int32_t* scol = wst + (size_t)(k % kPassStages) * 2 * (kPassCap + 8);
+            float* sval = reinterpret_cast<float*>(scol + kPassCap + 8);
+            if (rend - s0 <= kPassCap) stage_nnz(a.col, a.val, nnz, s0, rend, scol, sval, lane, vec16);
+        }
+        cp_async_commit();
+    };
+
+    int32_t rpA, reA, rpB, reB, rpC, reC;
+    float zoA, zoB, zoC;
+    load_meta(0, rpA, reA, zoA);
+    load_meta(1, rpB, reB, zoB);
+    issue(0, rpA, reA);
     float zz = 0.f, bb = 0.f;
-    for (int64_t base = r0; base < r1; base += (int64_t)NS * U) {
-        int st[U], ln[U];
-        float zo[U];
-        int cc[U];
-        float vv[U];
+    for (int64_t k = 0; k < nbatch; ++k) {
+        load_meta(k + 2, rpC, reC, zoC);
+        issue(k + 1, rpB, reB);
+        cp_async_wait<1>();
+        __syncwarp();
+        const int64_t r0 = w0 + k * kPassBatch;
+        const int nrows = (int)((r0 + kPassBatch < w1 ? r0 + kPassBatch : w1) - r0);
+        const int32_t s0 = __shfl_sync(0xFFFFFFFFu, rpA, 0);
+        const bool staged = reA - s0 <= kPassCap;
+        const int32_t base = s0 & ~3;
+        const int32_t* scol = wst + (size_t)(k % kPassStages) * 2 * (kPassCap + 8);
+        const float* sval = reinterpret_cast<const float*>(scol + kPassCap + 8);
+        float zreg = 0.f;
+        // RI rows of this sub-warp at a time: independent dot products and
+        // reductions interleave; the A^T z updates then go row by row in order
+        constexpr int RI = 4;
+#pragma unroll 1
+        for (int t0 = 0; t0 < RPH; t0 += RI) {
+            int32_t rs[RI];
+            int len[RI];
+            float zold[RI], p[RI];
+            int c0[RI];
+            float v0[RI];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t r = base + sw + (int64_t)NS * u;
-            st[u] = 0;
-            ln[u] = 0;
-            zo[u] = 0.f;
-            if (r < r1) {
-                st[u] = __ldg(a.row_ptr + r);
-                ln[u] = __ldg(a.row_ptr + r + 1) - st[u];
-                zo[u] = __ldg(a.zin + r);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            cc[u] = 0;
-            vv[u] = 0.f;
-            if (sl < ln[u]) {
-                cc[u] = __ldg(a.col + st[u] + sl);
-                vv[u] = __ldg(a.val + st[u] + sl);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t r = base + sw + (int64_t)NS * u;
-            // w_r = sum_k val_k * vhat[col_k]
-            float p = 0.f;
-            for (int t = sl; t < ln[u]; t += LPR) {
-                int c;
-                float v;
-                if (t == sl) {
-                    c = cc[u];
-                    v = vv[u];
-                } else {
-                    c = __ldg(a.col + st[u] + t);
-                    v = __ldg(a.val + st[u] + t);
+            for (int u = 0; u < RI; ++u) {
+                const int row = sub * RPH + t0 + u;
+                rs[u] = __shfl_sync(0xFFFFFFFFu, rpA, row & 31);
+                const int32_t rn = __shfl_sync(0xFFFFFFFFu, rpA, (row + 1) & 31);
+                zold[u] = __shfl_sync(0xFFFFFFFFu, zoA, row & 31);
+                const int32_t re = (row + 1 < nrows) ? rn : reA;
+                len[u] = row < nrows ? re - rs[u] : 0;
+                c0[u] = 0;
+                v0[u] = 0.f;
+                if (sl < len[u]) {
+                    if (staged) {
+                        c0[u] = scol[rs[u] - base + sl];
+                        v0[u] = sval[rs[u] - base + sl];
+                    } else {
+                        c0[u] = __ldg(a.col + rs[u] + sl);
+                        v0[u] = __ldg(a.val + rs[u] + sl);
+                    }
                 }
-                if ((unsigned)c < (unsigned)a.d)
-                    p = fmaf(v, vh[c], p);
-                else
-                    flag_error(a.status, kDevBadColumn);
             }
 #pragma unroll
-            for (int o = LPR / 2; o > 0; o >>= 1) p += __shfl_xor_sync(0xFFFFFFFFu, p, o);
-            const float z = p - coef * zo[u];
-            if (r < r1) {
-                if (sl == 0) {
-                    a.zout[r] = z;
-                    zz = fmaf(z, z, zz);
-                    bb = fmaf(zo[u], zo[u], bb);
+            for (int u = 0; u < RI; ++u) {
+                p[u] = 0.f;
+                if (sl < len[u]) {
+                    if ((unsigned)c0[u] < (unsigned)a.d)
+                        p[u] = v0[u] * vh[c0[u]];
+                    else
+                        flag_error(a.status, kDevBadColumn);
                 }
-                // A^T z: this sub-warp's accumulator (distinct columns within a row)
-                for (int t = sl; t < ln[u]; t += LPR) {
+                for (int q = sl + LPR; q < len[u]; q += LPR) {  // rows longer than LPR
                     int c;
                     float v;
-                    if (t == sl) {
-                        c = cc[u];
-                        v = vv[u];
+                    if (staged) {
+                        c = scol[rs[u] - base + q];
+                        v = sval[rs[u] - base + q];
                     } else {
-                        c = __ldg(a.col + st[u] + t);
-                        v = __ldg(a.val + st[u] + t);
+                        c = __ldg(a.col + rs[u] + q);
+                        v = __ldg(a.val + rs[u] + q);
+                    }
+                    if ((unsigned)c < (unsigned)a.d)
+                        p[u] = fmaf(v, vh[c], p[u]);
+                    else
+                        flag_error(a.status, kDevBadColumn);
+                }
+            }
+#pragma unroll
+            for (int o = LPR / 2; o > 0; o >>= 1)
+#pragma unroll
+                for (int u = 0; u < RI; ++u) p[u] += __shfl_xor_sync(0xFFFFFFFFu, p[u], o);
+#pragma unroll
+            for (int u = 0; u < RI; ++u) {
+                const float z = p[u] - coef * zold[u];
+                if (sl == t0 + u) zreg = z;
+                if (sl < len[u] && (unsigned)c0[u] < (unsigned)a.d) myacc[c0[u]] = fmaf(v0[u], z, myacc[c0[u]]);
+                for (int q = sl + LPR; q < len[u]; q += LPR) {
+                    int c;
+                    float v;
+                    if (staged) {
+                        c = scol[rs[u] - base + q];
+                        v = sval[rs[u] - base + q];
+                    } else {
+                        c = __ldg(a.col + rs[u] + q);
+                        v = __ldg(a.val + rs[u] + q);
                     }
                     if ((unsigned)c < (unsigned)a.d) myacc[c] = fmaf(v, z, myacc[c]);
                 }
+                __syncwarp();
             }
-            __syncwarp();
         }
+        // lane l of sub-warp h holds z of row h*RPH + l (l < RPH)
+        const int myrow = sub * RPH + sl;
+        if (sl < RPH && myrow < nrows) {
+            a.zout[r0 + myrow] = zreg;
+            zz = fmaf(zreg, zreg, zz);
+        }
+        if (lane < nrows) bb = fmaf(zoA, zoA, bb);
+        __syncwarp();
+        rpA = rpB; reA = reB; zoA = zoB;
+        rpB = rpC; reB = reC; zoB = zoC;
     }
+    cp_async_wait<0>();
     __syncthreads();
-    // per-CTA partials in float64, sub-warps summed in a fixed order
+    // per-CTA partials in float64, sub-warp accumulators summed in a fixed order
+    const int NS = kPassWarps * HALVES;
     for (int j = threadIdx.x; j < a.d; j += blockDim.x) {
-        double s = 0.0;
-        for (int q = 0; q < NS; ++q) s += (double)acc[(size_t)q * a.dpad + j];
-        a.gpart[(size_t)blockIdx.x * a.d + j] = s;
+        double sacc = 0.0;
+        for (int q = 0; q < NS; ++q) sacc += (double)acc[(size_t)q * a.dpad + j];
+        a.gpart[(size_t)blockIdx.x * a.d + j] = sacc;
     }
-    __shared__ double rz[32], rb[32];
+    __shared__ double rz[kPassWarps], rb[kPassWarps];
     double zd = (double)zz, bd = (double)bb;
     for (int o = 16; o > 0; o >>= 1) {
         zd += __shfl_xor_sync(0xFFFFFFFFu, zd, o);
@@ -161,7 +276,7 @@ __global__ void __launch_bounds__(512, 2) k_lsqr_pass(PassArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0, tb = 0.0;
-        for (int w = 0; w < nwarps; ++w) {
+        for (int w = 0; w < kPassWarps; ++w) {
             t += rz[w];
             tb += rb[w];
         }
@@ -208,11 +323,31 @@ __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
     LsqrState* st = a.st;
     if (st->done) return;
     const int d = a.d;
-    // reduce the pass partials (fixed order)
-    for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < a.nblk; ++b) s += a.gpart[(size_t)b * d + j];
-        sg[j] = s;
+    // reduce the pass partials: G threads per column, each a fixed stripe of
+    // blocks, combined in stripe order (deterministic)
+    {
+        const int gper = blockDim.x / d >= 4 ? 4 : (blockDim.x / d >= 2 ? 2 : 1);
+        __shared__ double part4[1024];  // gper * d <= 1024
+        for (int t = threadIdx.x; t < d * gper; t += blockDim.x) {
+            const int j = t % d, g = t / d;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int b = g;
+            for (; b + 3 * gper < a.nblk; b += 4 * gper) {
+                s0 += a.gpart[(size_t)b * d + j];
+                s1 += a.gpart[(size_t)(b + gper) * d + j];
+                s2 += a.gpart[(size_t)(b + 2 * gper) * d + j];
+                s3 += a.gpart[(size_t)(b + 3 * gper) * d + j];
+            }
+            for (; b < a.nblk; b += gper) s0 += a.gpart[(size_t)b * d + j];
+            part4[g * d + j] = (s0 + s1) + (s2 + s3);
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+            double t = 0.0;
+            for (int g = 0; g < gper; ++g) t += part4[g * d + j];
+            sg[j] = t;
+        }
+        __syncthreads();
     }
     double zz = 0.0, bb = 0.0;
     for (int b = threadIdx.x; b < a.nblk; b += blockDim.x) {
@@ -225,12 +360,36 @@ __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
     const double beta = sqrt(zz);
     // scale of u = z * s_new: z = A x0 - b = -r0 on the first step
     const double s_new = beta > 0.0 ? (a.first ? -1.0 / beta : 1.0 / beta) : 0.0;
-    // t = M^T (A^T z); gvec = s_new * t - beta * v
+    // t = M^T (A^T z) with `gper` threads per column (fixed slices, fixed combine
+    // order); gvec = s_new * t - beta * v
+    __shared__ double tpart[1024];
+    {
+        const int gper = blockDim.x / d >= 4 ? 4 : (blockDim.x / d >= 2 ? 2 : 1);
+        for (int tq = threadIdx.x; tq < d * gper; tq += blockDim.x) {
+            const int j = tq % d, g = tq / d;
+            const int len = j + 1, lo = (int)((int64_t)len * g / gper), hi = (int)((int64_t)len * (g + 1) / gper);
+            double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+            int i = lo;
+            for (; i + 3 < hi; i += 4) {
+                t0 += a.M[(size_t)i * d + j] * sg[i];
+                t1 += a.M[(size_t)(i + 1) * d + j] * sg[i + 1];
+                t2 += a.M[(size_t)(i + 2) * d + j] * sg[i + 2];
+                t3 += a.M[(size_t)(i + 3) * d + j] * sg[i + 3];
+            }
+            for (; i < hi; ++i) t0 += a.M[(size_t)i * d + j] * sg[i];
+            tpart[g * d + j] = (t0 + t1) + (t2 + t3);
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+            double t = 0.0;
+            for (int g = 0; g < gper; ++g) t += tpart[g * d + j];
+            sv[j] = t;
+        }
+        __syncthreads();
+    }
     double loc = 0.0;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        double t = 0.0;
-        for (int i = 0; i <= j; ++i) t += a.M[(size_t)i * d + j] * sg[i];
-        double gv = s_new * t;
+        double gv = s_new * sv[j];
         if (!a.first) gv -= beta * a.v[j];
         sv[j] = gv;
         loc += gv * gv;
@@ -313,21 +472,45 @@ __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
     }
     __syncthreads();
     // next vhat = M v (float32; it feeds the float32 pass)
-    for (int i = threadIdx.x; i < d; i += blockDim.x) {
-        float s = 0.f;
-        for (int j = i; j < d; ++j) s = fmaf(a.M32T[(size_t)j * d + i], (float)sv[j], s);
-        a.vhat[i] = s;
+    {
+        // vhat = M v with `gper` threads per row (fixed slices, fixed combine order)
+        const int gper = blockDim.x / d >= 4 ? 4 : (blockDim.x / d >= 2 ? 2 : 1);
+        float* vpart = reinterpret_cast<float*>(sg);  // sg no longer needed
+        for (int tq = threadIdx.x; tq < d * gper; tq += blockDim.x) {
+            const int i = tq % d, g = tq / d;
+            const int len = d - i, lo = i + (int)((int64_t)len * g / gper), hi = i + (int)((int64_t)len * (g + 1) / gper);
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            int j = lo;
+            for (; j + 3 < hi; j += 4) {
+                s0 = fmaf(a.M32T[(size_t)j * d + i], (float)sv[j], s0);
+                s1 = fmaf(a.M32T[(size_t)(j + 1) * d + i], (float)sv[j + 1], s1);
+                s2 = fmaf(a.M32T[(size_t)(j + 2) * d + i], (float)sv[j + 2], s2);
+                s3 = fmaf(a.M32T[(size_t)(j + 3) * d + i], (float)sv[j + 3], s3);
+            }
+            for (; j < hi; ++j) s0 = fmaf(a.M32T[(size_t)j * d + i], (float)sv[j], s0);
+            vpart[g * d + i] = (s0 + s1) + (s2 + s3);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            float t = 0.f;
+            for (int g = 0; g < gper; ++g) t += vpart[g * d + i];
+            a.vhat[i] = t;
+        }
     }
 }
 
-__global__ void k_to_f32_transposed(const double* __restrict__ M, int d, float* __restrict__ MT,
-                                    float* __restrict__ x32, const double* __restrict__ x) {
+__global__ void k_to_f32_transposed(const double* __restrict__ M, int d, float* __restrict__ MT) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q < (int64_t)d * d) {
         const int i = (int)(q / d), j = (int)(q % d);
         MT[(size_t)j * d + i] = (float)M[q];
     }
-    if (q < d && x32) x32[q] = (float)x[q];
+}
+
+// y = float32 copy of x (n entries).
+__global__ void k_copy_f32(const double* __restrict__ x, int n, float* __restrict__ y) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) y[q] = (float)x[q];
 }
 
 // y = R x (upper triangular, float64, one thread per row)
@@ -358,11 +541,12 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     const int d = (int)A->d;
     const int64_t n = A->n;
     const int nsm = num_sms();
-    const int grid = 2 * nsm;
-    const int threads = 512;
+    const int grid = nsm;
+    const int pass_warps = d <= 256 ? 16 : (d <= 512 ? 8 : 4);
+    const int threads = pass_warps * 32;
     const int lpr = 16;
     const int dpad = ((d + 31) & ~31) + 1;
-    const int nsub = (threads / 32) * (32 / lpr);
+    const int nsub = pass_warps * (32 / lpr);
 
     Scratch ws(stream);
     const size_t oSA = ws.reserve(sizeof(float) * (size_t)m * d);
@@ -400,47 +584,43 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     st = sketch_impl(kSketchCSR, n, d, 0, 0, A->row_ptr, A->col, A->val, nullptr, b, m, seed, SA, Sb, nullptr,
                      stream);
     if (st != CW_OK) return st;
-    // preconditioner R: Cholesky of the Gram matrix, float64 Householder when that is not safe
-    bool use_qr = false;
-    st = gram_cholesky(SA, m, d, Sb, R, c, stream);
-    if (st == CW_ERR_RANK) {
-        use_qr = true;
-    } else if (st != CW_OK) {
-        return st;
-    } else {
-        std::vector<double> Rh((size_t)d * d);
-        CW_CUDA_TRY(cudaMemcpy(Rh.data(), R, sizeof(double) * (size_t)d * d, cudaMemcpyDeviceToHost));
-        double mx = 0.0, mn = INFINITY;
-        for (int j = 0; j < d; ++j) {
-            const double v = fabs(Rh[(size_t)j * d + j]);
-            mx = v > mx ? v : mx;
-            mn = v < mn ? v : mn;
-        }
-        // kappa(SA) >= max/min |R_jj|; the Gram route loses kappa^2 * 2^-24
-        if (!(mn > 0.0) || mx / mn > 300.0) use_qr = true;
-    }
-    if (use_qr) {
+    // preconditioner M = R^-1: R from the Cholesky factor of the Gram matrix of
+    // SA (one shared-memory kernel), or from the float64 Householder QR of SA
+    // when the Cholesky route is not safe (large diagonal ratio, a failed
+    // pivot, or d too large for the shared-memory kernel).  c = Q^T Sb.
+    float klb = 0.f;
+    st = gram_chol_inverse(SA, m, d, Sb, M, M32T, c, &klb, stream);
+    const bool fast_ok = (st == CW_OK) && klb <= 300.f;
+    if (st != CW_OK && st != CW_ERR_RANK && st != CW_ERR_SHAPE) return st;
+    if (!fast_ok) {
         st = qr64(SA, m, d, Sb, R, c, stream);
         if (st != CW_OK) return st;
+        st = tri_inverse(R, d, M, stream);
+        if (st != CW_OK) return st;
+        const int64_t dd0 = (int64_t)d * d;
+        {
+            CW_PROF("k_to_f32_transposed", stream);
+            k_to_f32_transposed<<<(unsigned)((dd0 + 255) / 256), 256, 0, stream>>>(M, d, M32T);
+        }
+        CW_LAUNCH_CHECK();
     }
-    st = trsv_upper(R, d, c, x0, stream);  // x0 = R^-1 c: sketch-and-solve start
-    if (st != CW_OK) return st;
-    st = trsm_upper(R, d, nullptr, d, M, stream);  // M = R^-1
-    if (st != CW_OK) return st;
-    const int64_t dd = (int64_t)d * d;
     {
-        CW_PROF("k_to_f32_transposed", stream);
-        k_to_f32_transposed<<<(unsigned)((dd + 255) / 256), 256, 0, stream>>>(M, d, M32T, vhat, x0);
+        CW_PROF("k_upper_matvec", stream);  // x0 = M c: the sketch-and-solve start
+        k_upper_matvec<<<(d + 127) / 128, 128, 0, stream>>>(M, d, c, x0, nullptr);
     }
     CW_LAUNCH_CHECK();
+    // first pass input: vhat = x0 (float32); y0 = R x0 = c
     {
-        CW_PROF("k_upper_matvec", stream);
-        k_upper_matvec<<<(d + 127) / 128, 128, 0, stream>>>(R, d, x0, y0, nullptr);
+        CW_PROF("k_copy_f32", stream);
+        k_copy_f32<<<(d + 255) / 256, 256, 0, stream>>>(x0, d, vhat);
     }
+    CW_CUDA_TRY(cudaMemcpyAsync(y0, c, sizeof(double) * d, cudaMemcpyDeviceToDevice, stream));
     CW_LAUNCH_CHECK();
 
-    const size_t pass_smem = sizeof(float) * (size_t)dpad * (1 + nsub);
-    auto pk = k_lsqr_pass<16, 4>;
+    const size_t pass_smem = ((sizeof(float) * (size_t)dpad * (1 + nsub) + 127) & ~size_t(127)) +
+                             sizeof(int32_t) * (size_t)pass_warps * kPassStages * 2 * (kPassCap + 8);
+    if (pass_smem > 227 * 1024) return CW_ERR_SHAPE;
+    auto pk = pass_warps == 16 ? k_lsqr_pass<16, 16> : (pass_warps == 8 ? k_lsqr_pass<16, 8> : k_lsqr_pass<16, 4>);
     CW_CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem));
     PassArgs pa{A->row_ptr, A->col, A->val, vhat, b, z, ws.at<double>(ogp), ws.at<double>(ozp), ws.at<double>(obp),
                 nullptr, status, n, d, dpad, 1.0f};

@@ -161,34 +161,35 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return r;
 }
 
+// Per row one 16-byte record {key, a, len, sigma*b}: a = row start (CSR) or
+// the row index (dense); written in coarse-bin order, stable within a bin.
 template <int MODE, bool HAS_B>
 __global__ void __launch_bounds__(256) k_coarse_scatter(HashParams hp, int64_t i0, int64_t n, int gshift,
                                                         int nbins, const uint32_t* __restrict__ O,
                                                         const int32_t* __restrict__ row_ptr,
-                                                        const float* __restrict__ b,
-                                                        uint32_t* __restrict__ rkey, int32_t* __restrict__ ra,
-                                                        int32_t* __restrict__ rlen, float* __restrict__ rb,
+                                                        const float* __restrict__ b, int4* __restrict__ rec,
                                                         unsigned* status) {
-    extern __shared__ uint32_t cnt[];  // [kTileWarps][nbins]
+    extern __shared__ uint32_t sm3[];
+    uint32_t* cnt = sm3;                                // [kTileWarps][nbins]
+    uint32_t* skeys = sm3 + kTileWarps * nbins;         // [kTileWarps][kTileRowsPerWarp]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int q = threadIdx.x; q < kTileWarps * nbins; q += blockDim.x) cnt[q] = 0;
     __syncthreads();
-
     const int64_t r0 = (int64_t)blockIdx.x * kTileRows + warp * kTileRowsPerWarp + lane;
-    uint32_t keys[kTileRowsPerLane];
-    {
+    uint32_t* wk = skeys + warp * kTileRowsPerWarp;
+    uint32_t* wc = cnt + warp * nbins;
+    if (r0 < n) {
         KeyWalk kw;
-        kw.init(hp, (uint64_t)(i0 + (r0 < n ? r0 : 0)), 32);
-#pragma unroll
+        kw.init(hp, (uint64_t)(i0 + r0), 32);
+#pragma unroll 4
         for (int j = 0; j < kTileRowsPerLane; ++j) {
-            keys[j] = kw.key(hp);
+            if (r0 + 32 * j >= n) break;
+            const uint32_t key = kw.key(hp);
+            wk[lane + 32 * j] = key;
+            atomicAdd(&wc[(key & 0x7FFFFFFFu) >> gshift], 1u);
             kw.step();
         }
     }
-    uint32_t* wc = cnt + warp * nbins;
-#pragma unroll
-    for (int j = 0; j < kTileRowsPerLane; ++j)
-        if (r0 + 32 * j < n) atomicAdd(&wc[(keys[j] & 0x7FFFFFFFu) >> gshift], 1u);
     __syncthreads();
     for (int bin = threadIdx.x; bin < nbins; bin += blockDim.x) {
         uint32_t run = O[(size_t)blockIdx.x * nbins + bin];
@@ -200,10 +201,10 @@ __global__ void __launch_bounds__(256) k_coarse_scatter(HashParams hp, int64_t i
         }
     }
     __syncthreads();
-
     const unsigned lt = lanemask_lt();
-#pragma unroll
+#pragma unroll 1
     for (int j0 = 0; j0 < kTileRowsPerLane; j0 += 4) {
+        if (r0 - lane + 32 * j0 >= n) break;
         int32_t st[4], ln[4];
         float bv[4];
 #pragma unroll
@@ -216,6 +217,8 @@ __global__ void __launch_bounds__(256) k_coarse_scatter(HashParams hp, int64_t i
                 if (MODE == kModeCSR) {
                     st[u] = __ldg(row_ptr + r);
                     ln[u] = __ldg(row_ptr + r + 1) - st[u];
+                } else if (MODE == kModeDense) {
+                    st[u] = (int32_t)r;
                 }
                 if (HAS_B) bv[u] = __ldg(b + r);
             }
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(256) k_coarse_scatter(HashParams hp, int64_t i
             const bool valid = r < n;
             const unsigned am = __ballot_sync(0xFFFFFFFFu, valid);
             if (am == 0) break;
-            const uint32_t key = keys[j];
+            const uint32_t key = valid ? wk[lane + 32 * j] : 0u;
             const uint32_t bin = (key & 0x7FFFFFFFu) >> gshift;
             unsigned peers = 0;
             uint32_t pos = 0;
@@ -239,217 +242,182 @@ __global__ void __launch_bounds__(256) k_coarse_scatter(HashParams hp, int64_t i
             if (valid && (__ffs(peers) - 1) == lane) wc[bin] += __popc(peers);
             __syncwarp();
             if (valid) {
-                rkey[pos] = key;
-                if (MODE == kModeCSR) {
-                    int32_t L = ln[u];
-                    if (L < 0) {
-                        flag_error(status, kDevBadRowPtr);
-                        L = 0;
-                    }
-                    ra[pos] = st[u];
-                    rlen[pos] = L;
-                } else if (MODE == kModeDense) {
-                    ra[pos] = (int32_t)r;
+                int32_t L = ln[u];
+                if (MODE == kModeCSR && L < 0) {
+                    flag_error(status, kDevBadRowPtr);
+                    L = 0;
                 }
-                if (HAS_B) rb[pos] = (key >> 31) ? -bv[u] : bv[u];
+                const float sb = HAS_B ? ((key >> 31) ? -bv[u] : bv[u]) : 0.f;
+                rec[pos] = make_int4((int)key, st[u], L, __float_as_int(sb));
             }
         }
     }
 }
 
-// ---------------------------------------------------------------- K4 common: in-CTA stable sort
+// ---------------------------------------------------------------- K4a: fine stable sort per group
 
-struct GroupSort {
-    uint32_t* cnt;     // [warps][G]
-    uint32_t* bstart;  // [G + 1]
-};
-
-// Counts the chunk's records [c0, c1) per fine bucket for each warp's
-// contiguous segment, scans, and leaves in cnt[w][fb] the first output slot of
-// warp w's records of bucket fb, and in bstart[] the bucket starts (relative
-// to c0).
-__device__ __forceinline__ void group_count_scan(const uint32_t* __restrict__ rkey, uint32_t c0, uint32_t c1,
-                                                 int G, int nwarps, GroupSort gsrt) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int q = threadIdx.x; q < nwarps * G; q += blockDim.x) gsrt.cnt[q] = 0;
-    __syncthreads();
-    const uint32_t len = c1 - c0;
-    const uint32_t seg = ((len + nwarps - 1) / nwarps + 31) & ~31u;
-    const uint32_t s0 = c0 + min(len, seg * warp), s1 = c0 + min(len, seg * (warp + 1));
-    uint32_t* wc = gsrt.cnt + warp * G;
-    for (uint32_t k = s0 + lane; k < s1; k += 32) atomicAdd(&wc[__ldg(rkey + k) & (G - 1)], 1u);
-    __syncthreads();
-    // bucket totals -> exclusive scan over buckets (G <= 256 <= blockDim)
+// One CTA per coarse bin (G = 2^gshift consecutive buckets): counting sort of
+// the bin's records by bucket, stable, written to the same region in bucket
+// order as {a | sign << 31 (dense) or a, len | sign << 31 (CSR)} and sigma*b;
+// bucket_ptr for the bin's buckets.  This is the permutation P of Section 5.2.
+template <int MODE, bool HAS_B>
+__global__ void __launch_bounds__(512) k_fine_sort(const int4* __restrict__ rec, const uint32_t* __restrict__ coarse_ptr,
+                                                   int64_t m, int gshift, int2* __restrict__ out2,
+                                                   float* __restrict__ outb, int32_t* __restrict__ bucket_ptr) {
+    __shared__ uint32_t cnt[16 * kMaxGroupBuckets];
+    __shared__ uint32_t bstart[kMaxGroupBuckets + 1];
     __shared__ uint32_t wsum[32];
+    const int nwarps = blockDim.x >> 5;
+    const int G = 1 << gshift;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x;
+    const uint32_t r0 = coarse_ptr[g], r1 = coarse_ptr[g + 1];
+    const int64_t b0 = (int64_t)g << gshift;
+    const int nb = (int)((m - b0) < (int64_t)G ? (m - b0) : (int64_t)G);
+    for (int q = threadIdx.x; q < nwarps * G; q += blockDim.x) cnt[q] = 0;
+    __syncthreads();
+    const uint32_t len = r1 - r0;
+    const uint32_t seg = ((len + nwarps - 1) / nwarps + 31) & ~31u;
+    const uint32_t s0 = r0 + min(len, seg * warp), s1 = r0 + min(len, seg * (warp + 1));
+    uint32_t* wc = cnt + warp * G;
+    for (uint32_t k = s0 + lane; k < s1; k += 32) atomicAdd(&wc[(uint32_t)__ldg(&rec[k].x) & (G - 1)], 1u);
+    __syncthreads();
+    // bucket totals -> exclusive scan (G <= blockDim)
     uint32_t tot = 0;
-    const int b = threadIdx.x;
-    if (b < G)
-        for (int w = 0; w < nwarps; ++w) tot += gsrt.cnt[w * G + b];
+    const int bq = threadIdx.x;
+    if (bq < G)
+        for (int w = 0; w < nwarps; ++w) tot += cnt[w * G + bq];
     uint32_t incl = tot;
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
         if (lane >= o) incl += v;
     }
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        uint32_t v = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
+        uint32_t v = (lane < nwarps) ? wsum[lane] : 0;
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+            const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
             if (lane >= o) v += u;
         }
         wsum[lane] = v;
     }
     __syncthreads();
-    if (b < G) {
+    if (bq < G) {
         uint32_t off = incl - tot + (warp ? wsum[warp - 1] : 0);
-        gsrt.bstart[b] = off;
+        bstart[bq] = off;
+        if (bq < nb) bucket_ptr[b0 + bq] = (int32_t)(r0 + off);
         for (int w = 0; w < nwarps; ++w) {
-            const uint32_t t = gsrt.cnt[w * G + b];
-            gsrt.cnt[w * G + b] = off;
+            const uint32_t t = cnt[w * G + bq];
+            cnt[w * G + bq] = off;
             off += t;
         }
     }
-    if (threadIdx.x == 0) gsrt.bstart[G] = len;
     __syncthreads();
+    const unsigned lt = lanemask_lt();
+    for (uint32_t kb = s0; kb < s1; kb += 32) {
+        const uint32_t k = kb + lane;
+        const bool valid = k < s1;
+        const unsigned am = __ballot_sync(0xFFFFFFFFu, valid);
+        int4 r = make_int4(0, 0, 0, 0);
+        if (valid) r = __ldg(&rec[k]);
+        const uint32_t key = (uint32_t)r.x;
+        const uint32_t fb = key & (G - 1);
+        unsigned peers = 0;
+        uint32_t pos = 0;
+        if (valid) {
+            peers = __match_any_sync(am, fb);
+            pos = wc[fb] + __popc(peers & lt);
+        }
+        __syncwarp();
+        if (valid && (__ffs(peers) - 1) == lane) wc[fb] += __popc(peers);
+        __syncwarp();
+        if (valid) {
+            const uint32_t sgn = key & 0x80000000u;
+            if (MODE == kModeCSR)
+                out2[r0 + pos] = make_int2(r.y, (int)((uint32_t)r.z | sgn));
+            else if (MODE == kModeDense)
+                out2[r0 + pos] = make_int2((int)((uint32_t)r.y | sgn), 0);
+            if (HAS_B) outb[r0 + pos] = __int_as_float(r.w);
+        }
+    }
 }
 
-// ---------------------------------------------------------------- K4: CSR apply
+// ---------------------------------------------------------------- K4b: CSR apply
 
 struct CsrApplyArgs {
-    const uint32_t* rkey;
-    const int32_t* ra;
-    const int32_t* rlen;
-    const float* rb;
-    const uint32_t* coarse_ptr;
+    const int2* rs;          // bucket-ordered {row start, len | sign << 31}
+    const float* rb;         // bucket-ordered sigma * b
+    const int32_t* bucket_ptr;
     const int32_t* col;
     const float* val;
     float* SA;
     float* Sb;
-    int32_t* bucket_ptr;
+    unsigned* counter;       // next bucket (zeroed before launch)
     unsigned* status;
     int64_t m;
     int d;
-    int dpad;      // accumulator row stride (floats)
-    int gshift;
-    int cap;       // records per chunk held in shared memory
-    int acc_global;  // 1: accumulate directly in SA (large d)
+    int dpad;
+    int acc_global;          // accumulate in the SA row itself (very wide rows)
+    int vec4;                // SA rows 16-byte aligned and d % 4 == 0
 };
 
+// Persistent warps take whole buckets from a counter; sub-warp `sub` of
+// COPIES = 32 / LPR adds the bucket's rows sub, sub + COPIES, ... (in order)
+// into its own shared-memory copy of the SA row; the copies are summed in a
+// fixed order.  No block barriers, no floating-point atomics.
 template <int LPR, int U, bool HAS_B>
-__global__ void __launch_bounds__(512) k_apply_csr(CsrApplyArgs a) {
+__global__ void __launch_bounds__(256) k_apply_csr(CsrApplyArgs a) {
     constexpr int COPIES = 32 / LPR;
-    extern __shared__ __align__(16) uint8_t smem[];
-    const int nwarps = blockDim.x >> 5;
-    const int G = 1 << a.gshift;
+    extern __shared__ __align__(16) float smacc[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sub = lane / LPR, sl = lane % LPR;
-
-    int32_t* s_start = reinterpret_cast<int32_t*>(smem);
-    uint32_t* s_len = reinterpret_cast<uint32_t*>(s_start + a.cap);
-    float* s_b = reinterpret_cast<float*>(s_len + a.cap);
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(s_b + (HAS_B ? a.cap : 0));
-    uint32_t* bstart = cnt + nwarps * G;
-    int* s_next = reinterpret_cast<int*>(bstart + G + 1);
-    float* acc_base = reinterpret_cast<float*>(s_next + 4);
-    const GroupSort gsrt{cnt, bstart};
-
-    const int g = blockIdx.x;
-    const uint32_t r0 = a.coarse_ptr[g], r1 = a.coarse_ptr[g + 1];
-    const int64_t b0 = (int64_t)g << a.gshift;
-    const int nb = (int)((a.m - b0) < (int64_t)G ? (a.m - b0) : (int64_t)G);
-    const bool multi = (r1 - r0) > (uint32_t)a.cap;
-
-    if (multi) {
-        // bucket_ptr over the whole group first (counts only)
-        group_count_scan(a.rkey, r0, r1, G, nwarps, gsrt);
-        for (int q = threadIdx.x; q < nb; q += blockDim.x) a.bucket_ptr[b0 + q] = (int32_t)(r0 + bstart[q]);
-        __syncthreads();
-    }
-
-    for (uint32_t c0 = r0, first = 1; first || c0 < r1; c0 += a.cap, first = 0) {
-        const uint32_t c1 = min(r1, c0 + (uint32_t)a.cap);
-        group_count_scan(a.rkey, c0, c1, G, nwarps, gsrt);
-        if (!multi)
-            for (int q = threadIdx.x; q < nb; q += blockDim.x) a.bucket_ptr[b0 + q] = (int32_t)(r0 + bstart[q]);
-        // place the chunk's records, stably sorted by bucket
-        {
-            const uint32_t len = c1 - c0;
-            const uint32_t seg = ((len + nwarps - 1) / nwarps + 31) & ~31u;
-            const uint32_t s0 = c0 + min(len, seg * warp), s1 = c0 + min(len, seg * (warp + 1));
-            uint32_t* wc = cnt + warp * G;
-            const unsigned lt = lanemask_lt();
-            for (uint32_t kb = s0; kb < s1; kb += 32) {
-                const uint32_t k = kb + lane;
-                const bool valid = k < s1;
-                const unsigned am = __ballot_sync(0xFFFFFFFFu, valid);
-                uint32_t key = 0, L = 0;
-                int32_t st = 0;
-                float bv = 0.f;
-                if (valid) {
-                    key = __ldg(a.rkey + k);
-                    st = __ldg(a.ra + k);
-                    L = (uint32_t)__ldg(a.rlen + k);
-                    if (HAS_B) bv = __ldg(a.rb + k);
-                }
-                const uint32_t fb = key & (G - 1);
-                unsigned peers = 0;
-                uint32_t pos = 0;
-                if (valid) {
-                    peers = __match_any_sync(am, fb);
-                    pos = wc[fb] + __popc(peers & lt);
-                }
-                __syncwarp();
-                if (valid && (__ffs(peers) - 1) == lane) wc[fb] += __popc(peers);
-                __syncwarp();
-                if (valid) {
-                    s_start[pos] = st;
-                    s_len[pos] = L | (key & 0x80000000u);
-                    if (HAS_B) s_b[pos] = bv;
-                }
-            }
+    float* accw = a.acc_global ? nullptr : smacc + (size_t)warp * COPIES * a.dpad;
+    for (;;) {
+        unsigned bk = 0;
+        if (lane == 0) bk = atomicAdd(a.counter, 1u);
+        bk = __shfl_sync(0xFFFFFFFFu, bk, 0);
+        if ((int64_t)bk >= a.m) break;
+        const int s = a.bucket_ptr[bk], e = a.bucket_ptr[bk + 1];
+        float* SArow = a.SA + (size_t)bk * a.d;
+        float* myacc;
+        if (a.acc_global) {
+            for (int c = lane; c < a.d; c += 32) SArow[c] = 0.f;
+            myacc = SArow;
+        } else {
+            for (int c = lane; c < COPIES * a.dpad; c += 32) accw[c] = 0.f;
+            myacc = accw + sub * a.dpad;
         }
-        if (threadIdx.x == 0) *s_next = 0;
-        __syncthreads();
-
-        // warps take whole buckets; sub-warp `sub` adds rows s+sub, s+sub+COPIES, ...
-        float* accw = a.acc_global ? nullptr : acc_base + (size_t)warp * COPIES * a.dpad;
-        for (;;) {
-            int bk = 0;
-            if (lane == 0) bk = atomicAdd(s_next, 1);
-            bk = __shfl_sync(0xFFFFFFFFu, bk, 0);
-            if (bk >= nb) break;
-            const int s = (int)bstart[bk], e = (int)bstart[bk + 1];
-            if (!first && s == e) continue;
-            float* SArow = a.SA + (size_t)(b0 + bk) * a.d;
-            float* myacc;
-            if (a.acc_global) {
-                // large d: this warp owns the SA row; COPIES == 1 (LPR == 32)
-                myacc = SArow;
-                if (first)
-                    for (int c = lane; c < a.d; c += 32) SArow[c] = 0.f;
-                __syncwarp();
-            } else {
-                for (int c = lane; c < COPIES * a.dpad; c += 32) accw[c] = 0.f;
-                __syncwarp();
-                myacc = accw + sub * a.dpad;
+        __syncwarp();
+        float sbacc = 0.f;
+        for (int k0 = s; k0 < e; k0 += 32) {
+            // records of up to 32 rows: lane l holds row k0 + l
+            int2 rr = make_int2(0, 0);
+            float rbv = 0.f;
+            if (k0 + lane < e) {
+                rr = __ldg(&a.rs[k0 + lane]);
+                if (HAS_B) rbv = __ldg(&a.rb[k0 + lane]);
             }
-            float sbacc = 0.f;
-            for (int k0 = s; k0 < e; k0 += COPIES * U) {
+            if (HAS_B) {
+                float t = rbv;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+                sbacc += t;
+            }
+            const int nrow = min(32, e - k0);
+#pragma unroll 1
+            for (int t0 = 0; t0 < 32; t0 += COPIES * U) {
+                if (t0 >= nrow) break;
                 int st[U];
                 uint32_t ln[U];
                 int cc[U];
                 float vv[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int kk = k0 + u * COPIES + sub;
-                    st[u] = 0;
-                    ln[u] = 0;
-                    if (kk < e) {
-                        st[u] = s_start[kk];
-                        ln[u] = s_len[kk];
-                        if (HAS_B && sl == 0) sbacc += s_b[kk];
-                    }
+                    const int t = t0 + u * COPIES + sub;  // row within the 32-row chunk
+                    st[u] = __shfl_sync(0xFFFFFFFFu, rr.x, t & 31);
+                    ln[u] = (uint32_t)__shfl_sync(0xFFFFFFFFu, rr.y, t & 31);
+                    if (t >= nrow) ln[u] = 0;
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -464,16 +432,17 @@ __global__ void __launch_bounds__(512) k_apply_csr(CsrApplyArgs a) {
                 for (int u = 0; u < U; ++u) {
                     const uint32_t L = ln[u] & 0x7FFFFFFFu;
                     const bool neg = (ln[u] >> 31) != 0;
-                    for (uint32_t t = sl; t < L; t += LPR) {
-                        int c;
-                        float v;
-                        if (t == (uint32_t)sl) {
-                            c = cc[u];
-                            v = vv[u];
-                        } else {
-                            c = __ldg(a.col + st[u] + t);
-                            v = __ldg(a.val + st[u] + t);
-                        }
+                    if ((uint32_t)sl < L) {
+                        const int c = cc[u];
+                        const float v = neg ? -vv[u] : vv[u];
+                        if ((unsigned)c < (unsigned)a.d)
+                            myacc[c] += v;
+                        else
+                            flag_error(a.status, kDevBadColumn);
+                    }
+                    for (uint32_t t = sl + LPR; t < L; t += LPR) {  // rows longer than LPR
+                        const int c = __ldg(a.col + st[u] + t);
+                        const float v = __ldg(a.val + st[u] + t);
                         if ((unsigned)c < (unsigned)a.d)
                             myacc[c] += neg ? -v : v;
                         else
@@ -482,52 +451,49 @@ __global__ void __launch_bounds__(512) k_apply_csr(CsrApplyArgs a) {
                     __syncwarp();
                 }
             }
-            __syncwarp();
-            if (!a.acc_global) {
+        }
+        if (!a.acc_global) {
+            if (a.vec4) {
+                for (int c = lane * 4; c < a.d; c += 128) {
+                    float4 v = make_float4(accw[c], accw[c + 1], accw[c + 2], accw[c + 3]);
+#pragma unroll
+                    for (int cp = 1; cp < COPIES; ++cp) {
+                        const float* o = accw + cp * a.dpad + c;
+                        v.x += o[0]; v.y += o[1]; v.z += o[2]; v.w += o[3];
+                    }
+                    *reinterpret_cast<float4*>(SArow + c) = v;
+                }
+            } else {
                 for (int c = lane; c < a.d; c += 32) {
                     float v = accw[c];
 #pragma unroll
                     for (int cp = 1; cp < COPIES; ++cp) v += accw[cp * a.dpad + c];
-                    if (first)
-                        SArow[c] = v;
-                    else
-                        SArow[c] += v;
+                    SArow[c] = v;
                 }
             }
-            if (HAS_B && a.Sb) {
-                float v = __shfl_sync(0xFFFFFFFFu, sbacc, 0);
-#pragma unroll
-                for (int cp = 1; cp < COPIES; ++cp) v += __shfl_sync(0xFFFFFFFFu, sbacc, cp * LPR);
-                if (lane == 0) a.Sb[b0 + bk] = first ? v : a.Sb[b0 + bk] + v;
-            }
-            __syncwarp();
         }
-        __syncthreads();
+        if (HAS_B && a.Sb && lane == 0) a.Sb[bk] = sbacc;
+        __syncwarp();
     }
 }
 
-// ---------------------------------------------------------------- K4: dense apply
+// ---------------------------------------------------------------- K4b: dense apply
 
 struct DenseApplyArgs {
-    const uint32_t* rkey;
-    const int32_t* ra;
+    const int2* rs;   // bucket-ordered {row | sign << 31, 0}
     const float* rb;
-    const uint32_t* coarse_ptr;
+    const int32_t* bucket_ptr;
     const float* A;
     int64_t lda;
     float* SA;
     float* Sb;
-    int32_t* bucket_ptr;
+    unsigned* counter;
     int64_t m;
     int d;
-    int gshift;
-    int cap;
     int vec4;      // 1 when A rows and d allow 16-byte loads
     double* SA64;  // PRECISE: float64 output of the two-word sums
 };
 
-// Each warp owns a bucket; lane l holds columns {4l + 128 v .. +3} (vec4) or
-// {l + 32 v} in registers; rows are added in ascending order.
 // PRECISE: each accumulator is a float32 pair (hi, lo) updated by an exact
 // two-sum, so SA is exact to ~2^-48 relative and is written in float64.
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
@@ -537,248 +503,130 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
     hi = t;
 }
 
+// Each warp owns a bucket at a time; lane l holds columns {4l + 128 v .. +3}
+// (vec4) or {l + 32 q + 128 v} in registers; rows are added in ascending order.
 template <int NV, int U, bool HAS_B, bool PRECISE>
-__global__ void __launch_bounds__(512) k_apply_dense(DenseApplyArgs a) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    const int nwarps = blockDim.x >> 5;
-    const int G = 1 << a.gshift;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t* s_row = reinterpret_cast<uint32_t*>(smem);
-    float* s_b = reinterpret_cast<float*>(s_row + a.cap);
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(s_b + (HAS_B ? a.cap : 0));
-    uint32_t* bstart = cnt + nwarps * G;
-    int* s_next = reinterpret_cast<int*>(bstart + G + 1);
-    const GroupSort gsrt{cnt, bstart};
-
-    const int g = blockIdx.x;
-    const uint32_t r0 = a.coarse_ptr[g], r1 = a.coarse_ptr[g + 1];
-    const int64_t b0 = (int64_t)g << a.gshift;
-    const int nb = (int)((a.m - b0) < (int64_t)G ? (a.m - b0) : (int64_t)G);
-    const bool multi = (r1 - r0) > (uint32_t)a.cap;
-    constexpr int COLS_PER_PASS = NV * 128;  // vec4 layout covers 128 columns per v
-
-    if (multi) {
-        group_count_scan(a.rkey, r0, r1, G, nwarps, gsrt);
-        for (int q = threadIdx.x; q < nb; q += blockDim.x) a.bucket_ptr[b0 + q] = (int32_t)(r0 + bstart[q]);
-        __syncthreads();
-    }
-    for (uint32_t c0 = r0, first = 1; first || c0 < r1; c0 += a.cap, first = 0) {
-        const uint32_t c1 = min(r1, c0 + (uint32_t)a.cap);
-        group_count_scan(a.rkey, c0, c1, G, nwarps, gsrt);
-        if (!multi)
-            for (int q = threadIdx.x; q < nb; q += blockDim.x) a.bucket_ptr[b0 + q] = (int32_t)(r0 + bstart[q]);
-        {
-            const uint32_t len = c1 - c0;
-            const uint32_t seg = ((len + nwarps - 1) / nwarps + 31) & ~31u;
-            const uint32_t s0 = c0 + min(len, seg * warp), s1 = c0 + min(len, seg * (warp + 1));
-            uint32_t* wc = cnt + warp * G;
-            const unsigned lt = lanemask_lt();
-            for (uint32_t kb = s0; kb < s1; kb += 32) {
-                const uint32_t k = kb + lane;
-                const bool valid = k < s1;
-                const unsigned am = __ballot_sync(0xFFFFFFFFu, valid);
-                uint32_t key = 0;
-                int32_t row = 0;
-                float bv = 0.f;
-                if (valid) {
-                    key = __ldg(a.rkey + k);
-                    row = __ldg(a.ra + k);
-                    if (HAS_B) bv = __ldg(a.rb + k);
-                }
-                const uint32_t fb = key & (G - 1);
-                unsigned peers = 0;
-                uint32_t pos = 0;
-                if (valid) {
-                    peers = __match_any_sync(am, fb);
-                    pos = wc[fb] + __popc(peers & lt);
-                }
-                __syncwarp();
-                if (valid && (__ffs(peers) - 1) == lane) wc[fb] += __popc(peers);
-                __syncwarp();
-                if (valid) {
-                    s_row[pos] = (uint32_t)row | (key & 0x80000000u);
-                    if (HAS_B) s_b[pos] = bv;
-                }
+__global__ void __launch_bounds__(256) k_apply_dense(DenseApplyArgs a) {
+    const int lane = threadIdx.x & 31;
+    constexpr int COLS_PER_PASS = NV * 128;
+    for (;;) {
+        unsigned bk = 0;
+        if (lane == 0) bk = atomicAdd(a.counter, 1u);
+        bk = __shfl_sync(0xFFFFFFFFu, bk, 0);
+        if ((int64_t)bk >= a.m) break;
+        const int s = a.bucket_ptr[bk], e = a.bucket_ptr[bk + 1];
+        float* SArow = a.SA ? a.SA + (size_t)bk * a.d : nullptr;
+        float sbacc = 0.f;
+        if (HAS_B) {
+            for (int k0 = s; k0 < e; k0 += 32) {
+                float t = (k0 + lane < e) ? __ldg(&a.rb[k0 + lane]) : 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+                sbacc += t;
             }
         }
-        if (threadIdx.x == 0) *s_next = 0;
-        __syncthreads();
-
-        for (;;) {
-            int bk = 0;
-            if (lane == 0) bk = atomicAdd(s_next, 1);
-            bk = __shfl_sync(0xFFFFFFFFu, bk, 0);
-            if (bk >= nb) break;
-            const int s = (int)bstart[bk], e = (int)bstart[bk + 1];
-            if (!first && s == e) continue;
-            float* SArow = a.SA + (size_t)(b0 + bk) * a.d;
-            float sbacc = 0.f;
-            if (HAS_B && lane == 0)
-                for (int k = s; k < e; ++k) sbacc += s_b[k];
-            for (int cbase = 0; cbase < a.d; cbase += COLS_PER_PASS) {
-                float4 acc[NV];
-                float4 accl[PRECISE ? NV : 1];
+        for (int cbase = 0; cbase < a.d; cbase += COLS_PER_PASS) {
+            float4 acc[NV];
+            float4 accl[PRECISE ? NV : 1];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int v = 0; v < NV; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                for (int v = 0; v < (PRECISE ? NV : 1); ++v) accl[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int k0 = s; k0 < e; k0 += U) {
-                    float4 x[U][NV];
-                    uint32_t rr[U];
+            for (int v = 0; v < (PRECISE ? NV : 1); ++v) accl[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int k0 = s; k0 < e; k0 += U) {
+                float4 x[U][NV];
+                uint32_t rr[U];
 #pragma unroll
-                    for (int u = 0; u < U; ++u) rr[u] = (k0 + u < e) ? s_row[k0 + u] : 0xFFFFFFFFu;
+                for (int u = 0; u < U; ++u) rr[u] = (k0 + u < e) ? (uint32_t)__ldg(&a.rs[k0 + u].x) : 0xFFFFFFFFu;
 #pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const bool ok = rr[u] != 0xFFFFFFFFu;
-                        const float* rowp = a.A + (int64_t)(rr[u] & 0x7FFFFFFFu) * a.lda;
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) {
-                            x[u][v] = make_float4(0.f, 0.f, 0.f, 0.f);
-                            if (ok) {
-                                if (a.vec4) {
-                                    const int c = cbase + v * 128 + lane * 4;
-                                    if (c < a.d) x[u][v] = __ldg(reinterpret_cast<const float4*>(rowp + c));
-                                } else {
-                                    const int c = cbase + v * 128 + lane;
-                                    if (c < a.d) x[u][v].x = __ldg(rowp + c);
-                                    if (c + 32 < a.d) x[u][v].y = __ldg(rowp + c + 32);
-                                    if (c + 64 < a.d) x[u][v].z = __ldg(rowp + c + 64);
-                                    if (c + 96 < a.d) x[u][v].w = __ldg(rowp + c + 96);
-                                }
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        if (rr[u] == 0xFFFFFFFFu) continue;
-                        const bool neg = (rr[u] >> 31) != 0;
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) {
-                            if (PRECISE) {
-                                const float sg = neg ? -1.f : 1.f;
-                                two_sum_acc(acc[v].x, accl[v].x, sg * x[u][v].x);
-                                two_sum_acc(acc[v].y, accl[v].y, sg * x[u][v].y);
-                                two_sum_acc(acc[v].z, accl[v].z, sg * x[u][v].z);
-                                two_sum_acc(acc[v].w, accl[v].w, sg * x[u][v].w);
-                            } else if (neg) {
-                                acc[v].x -= x[u][v].x; acc[v].y -= x[u][v].y;
-                                acc[v].z -= x[u][v].z; acc[v].w -= x[u][v].w;
-                            } else {
-                                acc[v].x += x[u][v].x; acc[v].y += x[u][v].y;
-                                acc[v].z += x[u][v].z; acc[v].w += x[u][v].w;
-                            }
-                        }
-                    }
-                }
-                if (PRECISE) {
-                    double* row64 = a.SA64 + (size_t)(b0 + bk) * a.d;
+                for (int u = 0; u < U; ++u) {
+                    const bool ok = rr[u] != 0xFFFFFFFFu;
+                    const float* rowp = a.A + (int64_t)(rr[u] & 0x7FFFFFFFu) * a.lda;
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        const float hv[4] = {acc[v].x, acc[v].y, acc[v].z, acc[v].w};
-                        const float lv[4] = {accl[v].x, accl[v].y, accl[v].z, accl[v].w};
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int cq = a.vec4 ? cbase + v * 128 + lane * 4 + q : cbase + v * 128 + lane + 32 * q;
-                            if (cq < a.d) {
-                                const double val = (double)hv[q] + (double)lv[q];
-                                row64[cq] = first ? val : row64[cq] + val;
+                        x[u][v] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (ok) {
+                            if (a.vec4) {
+                                const int c = cbase + v * 128 + lane * 4;
+                                if (c < a.d) x[u][v] = __ldg(reinterpret_cast<const float4*>(rowp + c));
+                            } else {
+                                const int c = cbase + v * 128 + lane;
+                                if (c < a.d) x[u][v].x = __ldg(rowp + c);
+                                if (c + 32 < a.d) x[u][v].y = __ldg(rowp + c + 32);
+                                if (c + 64 < a.d) x[u][v].z = __ldg(rowp + c + 64);
+                                if (c + 96 < a.d) x[u][v].w = __ldg(rowp + c + 96);
                             }
                         }
                     }
-                    continue;
                 }
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    if (a.vec4) {
-                        const int c = cbase + v * 128 + lane * 4;
-                        if (c < a.d) {
-                            float4* p = reinterpret_cast<float4*>(SArow + c);
-                            if (first) {
-                                *p = acc[v];
-                            } else {
-                                float4 o = *p;
-                                o.x += acc[v].x; o.y += acc[v].y; o.z += acc[v].z; o.w += acc[v].w;
-                                *p = o;
-                            }
-                        }
-                    } else {
-                        const int c = cbase + v * 128 + lane;
-                        const float vals[4] = {acc[v].x, acc[v].y, acc[v].z, acc[v].w};
+                for (int u = 0; u < U; ++u) {
+                    if (rr[u] == 0xFFFFFFFFu) continue;
+                    const bool neg = (rr[u] >> 31) != 0;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int cq = c + 32 * q;
-                            if (cq < a.d) SArow[cq] = first ? vals[q] : SArow[cq] + vals[q];
+                    for (int v = 0; v < NV; ++v) {
+                        if (PRECISE) {
+                            const float sg = neg ? -1.f : 1.f;
+                            two_sum_acc(acc[v].x, accl[v].x, sg * x[u][v].x);
+                            two_sum_acc(acc[v].y, accl[v].y, sg * x[u][v].y);
+                            two_sum_acc(acc[v].z, accl[v].z, sg * x[u][v].z);
+                            two_sum_acc(acc[v].w, accl[v].w, sg * x[u][v].w);
+                        } else if (neg) {
+                            acc[v].x -= x[u][v].x; acc[v].y -= x[u][v].y;
+                            acc[v].z -= x[u][v].z; acc[v].w -= x[u][v].w;
+                        } else {
+                            acc[v].x += x[u][v].x; acc[v].y += x[u][v].y;
+                            acc[v].z += x[u][v].z; acc[v].w += x[u][v].w;
                         }
                     }
                 }
             }
-            if (HAS_B && a.Sb && lane == 0) a.Sb[b0 + bk] = first ? sbacc : a.Sb[b0 + bk] + sbacc;
-            __syncwarp();
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const float hv[4] = {acc[v].x, acc[v].y, acc[v].z, acc[v].w};
+                const float lv[4] = {PRECISE ? accl[v].x : 0.f, PRECISE ? accl[v].y : 0.f,
+                                     PRECISE ? accl[v].z : 0.f, PRECISE ? accl[v].w : 0.f};
+                if (PRECISE) {
+                    double* row64 = a.SA64 + (size_t)bk * a.d;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int cq = a.vec4 ? cbase + v * 128 + lane * 4 + q : cbase + v * 128 + lane + 32 * q;
+                        if (cq < a.d) row64[cq] = (double)hv[q] + (double)lv[q];
+                    }
+                } else if (a.vec4) {
+                    const int c = cbase + v * 128 + lane * 4;
+                    if (c < a.d) *reinterpret_cast<float4*>(SArow + c) = acc[v];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int cq = cbase + v * 128 + lane + 32 * q;
+                        if (cq < a.d) SArow[cq] = hv[q];
+                    }
+                }
+            }
         }
-        __syncthreads();
+        if (HAS_B && a.Sb && lane == 0) a.Sb[bk] = sbacc;
     }
 }
 
-// ---------------------------------------------------------------- K4: vector only (Sx)
+// ---------------------------------------------------------------- K4b: vector only (Sx)
 
-__global__ void __launch_bounds__(256) k_apply_vec(const uint32_t* __restrict__ rkey, const float* __restrict__ rb,
-                                                  const uint32_t* __restrict__ coarse_ptr, int64_t m, int gshift,
-                                                  int cap, float* __restrict__ Sx, int32_t* __restrict__ bucket_ptr) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    const int nwarps = blockDim.x >> 5;
-    const int G = 1 << gshift;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* s_b = reinterpret_cast<float*>(smem);
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(s_b + cap);
-    uint32_t* bstart = cnt + nwarps * G;
-    const GroupSort gsrt{cnt, bstart};
-    const int g = blockIdx.x;
-    const uint32_t r0 = coarse_ptr[g], r1 = coarse_ptr[g + 1];
-    const int64_t b0 = (int64_t)g << gshift;
-    const int nb = (int)((m - b0) < (int64_t)G ? (m - b0) : (int64_t)G);
-    const bool multi = (r1 - r0) > (uint32_t)cap;
-    if (multi) {
-        group_count_scan(rkey, r0, r1, G, nwarps, gsrt);
-        for (int q = threadIdx.x; q < nb; q += blockDim.x) bucket_ptr[b0 + q] = (int32_t)(r0 + bstart[q]);
-        __syncthreads();
-    }
-    for (uint32_t c0 = r0, first = 1; first || c0 < r1; c0 += cap, first = 0) {
-        const uint32_t c1 = min(r1, c0 + (uint32_t)cap);
-        group_count_scan(rkey, c0, c1, G, nwarps, gsrt);
-        if (!multi)
-            for (int q = threadIdx.x; q < nb; q += blockDim.x) bucket_ptr[b0 + q] = (int32_t)(r0 + bstart[q]);
-        const uint32_t len = c1 - c0;
-        const uint32_t seg = ((len + nwarps - 1) / nwarps + 31) & ~31u;
-        const uint32_t s0 = c0 + min(len, seg * warp), s1 = c0 + min(len, seg * (warp + 1));
-        uint32_t* wc = cnt + warp * G;
-        const unsigned lt = lanemask_lt();
-        for (uint32_t kb = s0; kb < s1; kb += 32) {
-            const uint32_t k = kb + lane;
-            const bool valid = k < s1;
-            const unsigned am = __ballot_sync(0xFFFFFFFFu, valid);
-            uint32_t key = valid ? __ldg(rkey + k) : 0;
-            const float bv = valid ? __ldg(rb + k) : 0.f;
-            const uint32_t fb = key & (G - 1);
-            unsigned peers = 0;
-            uint32_t pos = 0;
-            if (valid) {
-                peers = __match_any_sync(am, fb);
-                pos = wc[fb] + __popc(peers & lt);
-            }
-            __syncwarp();
-            if (valid && (__ffs(peers) - 1) == lane) wc[fb] += __popc(peers);
-            __syncwarp();
-            if (valid) s_b[pos] = bv;
+__global__ void __launch_bounds__(256) k_apply_vec(const float* __restrict__ rb, const int32_t* __restrict__ bucket_ptr,
+                                                  int64_t m, float* __restrict__ Sx, unsigned* counter) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned bk = 0;
+        if (lane == 0) bk = atomicAdd(counter, 1u);
+        bk = __shfl_sync(0xFFFFFFFFu, bk, 0);
+        if ((int64_t)bk >= m) break;
+        const int s = bucket_ptr[bk], e = bucket_ptr[bk + 1];
+        float acc = 0.f;
+        for (int k0 = s; k0 < e; k0 += 32) {
+            float t = (k0 + lane < e) ? __ldg(&rb[k0 + lane]) : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+            acc += t;
         }
-        __syncthreads();
-        for (int q = threadIdx.x; q < nb; q += blockDim.x) {
-            const int s = (int)bstart[q], e = (int)bstart[q + 1];
-            if (!first && s == e) continue;
-            float acc = 0.f;
-            for (int k = s; k < e; ++k) acc += s_b[k];
-            Sx[b0 + q] = first ? acc : Sx[b0 + q] + acc;
-        }
-        __syncthreads();
+        if (lane == 0) Sx[bk] = acc;
     }
 }
 
@@ -788,12 +636,10 @@ __global__ void k_set_last(int32_t* bucket_ptr, int64_t m, int32_t n) { bucket_p
 
 struct SketchPlan {
     int gshift, nbins, ntiles, nchunks;
-    int cap;
-    int warps;
-    int lpr;
-    int dpad;
-    int acc_global;
-    size_t smem;
+    int lpr;        // CSR: lanes per row (16: two rows per warp step)
+    int dpad;       // CSR accumulator row stride (floats)
+    int acc_global; // CSR: accumulate in SA rows (very wide rows)
+    size_t acc_smem;
 };
 
 namespace {
@@ -804,74 +650,39 @@ int ilog2_ceil(uint64_t v) {
     return s;
 }
 
-int ilog2_floor(double v) {
-    int s = 0;
-    while ((double)(1ull << (s + 1)) <= v && s < 62) ++s;
-    return s;
-}
-
 }  // namespace
 
-// Chooses the group size G = 2^gshift (buckets per K4 CTA) so that at most
-// kMaxBins coarse bins exist, at most kMaxGroupBuckets buckets share a CTA, and
-// the expected group (n G / m rows) fills about 60% of the shared-memory record
-// capacity.  Larger groups are still correct: K4 then walks them in chunks.
-int plan_sketch(int mode, int64_t n, int64_t d, int64_t m, bool has_b, SketchPlan* p) {
-    const size_t smem_budget = 200 * 1024;
-    const int nsm = num_sms();
-    p->warps = 16;
-    p->acc_global = 0;
-    p->lpr = 32;
-    p->dpad = 0;
-    size_t acc_bytes = 0;
-    size_t rec_bytes = 4 + (has_b ? 4 : 0);
-    if (mode == kModeCSR) {
-        rec_bytes = 8 + (has_b ? 4 : 0);
-        p->lpr = 16;  // two rows per warp step (two accumulator copies)
-        p->dpad = (int)((d + 31) & ~31ll) + 1;  // odd stride: copies start on different banks
-        acc_bytes = (size_t)p->warps * 2 * p->dpad * sizeof(float);
-        if (acc_bytes > 96 * 1024) {
-            p->lpr = 32;
-            acc_bytes = (size_t)p->warps * p->dpad * sizeof(float);
-            while (acc_bytes > 96 * 1024 && p->warps > 8) {
-                p->warps /= 2;
-                acc_bytes = (size_t)p->warps * p->dpad * sizeof(float);
-            }
-            if (acc_bytes > 96 * 1024) {  // very wide rows: accumulate in the SA row itself
-                p->acc_global = 1;
-                acc_bytes = 0;
-                p->warps = 16;
-            }
-        }
-    } else if (mode == kModeVec) {
-        p->warps = 8;
-    }
-    const int threads = p->warps * 32;
-    const int gmax = std::min(ilog2_floor((double)std::min(threads, kMaxGroupBuckets)), ilog2_ceil((uint64_t)m));
+// Coarse bins: about 1024 (long runs of each bin per 8192-row tile keep the
+// coarse scatter's writes coalesced), at most kMaxBins, at most
+// kMaxGroupBuckets buckets per bin.
+int plan_sketch(int mode, int64_t n, int64_t d, int64_t m, SketchPlan* p) {
     const int gmin = ilog2_ceil(((uint64_t)m + kMaxBins - 1) / kMaxBins);
-    if (gmin > gmax && gmin > ilog2_floor((double)std::min(threads, kMaxGroupBuckets))) return CW_ERR_SHAPE;
-    const size_t fixed = acc_bytes + (size_t)p->warps * kMaxGroupBuckets * 4 + (kMaxGroupBuckets + 1) * 4 + 64;
-    size_t cap_budget = (smem_budget - fixed) / rec_bytes;
-    cap_budget = std::min<size_t>(cap_budget, 1u << 16) & ~size_t(31);
-    const double rows_per_bucket = (double)n / (double)m;
-    // largest group that fits ~60% of the record budget
-    const double tgt = 0.6 * (double)cap_budget / std::max(rows_per_bucket, 1e-9);
-    const int g_fit = tgt >= 1.0 ? ilog2_floor(tgt) : 0;
-    // enough groups to fill the GPU several times over
-    const double par = (double)m / (8.0 * nsm);
-    const int g_par = par >= 1.0 ? ilog2_floor(par) : 0;
-    int gs = std::min(std::min(g_fit, g_par), gmax);
+    const int gmax = ilog2_ceil((uint64_t)kMaxGroupBuckets);
+    if (gmin > gmax) return CW_ERR_SHAPE;
+    int gs = ilog2_ceil(((uint64_t)m + 1023) / 1024);
     gs = std::max(gs, gmin);
+    gs = std::min(gs, gmax);
+    gs = std::min(gs, ilog2_ceil((uint64_t)m));
     p->gshift = gs;
     p->nbins = (int)(((uint64_t)m + (1ull << gs) - 1) >> gs);
     p->ntiles = (int)((n + kTileRows - 1) / kTileRows);
     p->nchunks = (p->ntiles + kScanChunk - 1) / kScanChunk;
-    const int G = 1 << gs;
-    const double mean = rows_per_bucket * G;
-    size_t cap = (size_t)(1.25 * mean + 8.0 * sqrt(mean) + 64.0);
-    cap = (cap + 31) & ~size_t(31);
-    p->cap = (int)std::min(cap, cap_budget);
-    p->smem = (size_t)p->cap * rec_bytes + (size_t)p->warps * G * 4 + (size_t)(G + 1) * 4 + 16 + acc_bytes;
+    p->lpr = 16;
+    p->dpad = 0;
+    p->acc_global = 0;
+    p->acc_smem = 0;
+    if (mode == kModeCSR) {
+        p->dpad = (int)((d + 31) & ~31ll) + 4;  // copies start on different banks, rows stay 16-byte aligned
+        p->acc_smem = (size_t)8 * 2 * p->dpad * sizeof(float);
+        if (p->acc_smem > 96 * 1024) {
+            p->lpr = 32;
+            p->acc_smem = (size_t)8 * p->dpad * sizeof(float);
+            if (p->acc_smem > 96 * 1024) {
+                p->acc_global = 1;
+                p->acc_smem = 0;
+            }
+        }
+    }
     return CW_OK;
 }
 
@@ -880,9 +691,20 @@ static cudaError_t set_smem(F* f, size_t bytes) {
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <class F>
+static int persistent_grid(F* f, int threads, size_t smem) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, threads, smem) != cudaSuccess || per < 1) {
+        (void)cudaGetLastError();
+        per = 1;
+    }
+    return per * num_sms();
+}
+
 // mode: kModeCSR (row_ptr/col/val), kModeDense (A, lda), kModeVec (x in b).
 // bucket_ptr_out: optional device array of m + 1 ints (bucket starts of the
-// stable permutation); NULL uses internal scratch.
+// stable permutation); NULL uses internal scratch.  SA64 (dense only): write a
+// float64 SA from two-word sums instead of the float32 SA.
 int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const int32_t* row_ptr,
                 const int32_t* col, const float* val, const float* A, const float* b, int64_t m,
                 uint64_t seed, float* SA, float* Sb, int32_t* bucket_ptr_out, cudaStream_t stream,
@@ -896,7 +718,7 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
         return CW_OK;
     }
     SketchPlan p;
-    int st = plan_sketch(mode, n, d, m, has_b, &p);
+    int st = plan_sketch(mode, n, d, m, &p);
     if (st != CW_OK) return st;
     unsigned* status = device_status_word();
     if (!status) return CW_ERR_CUDA;
@@ -906,20 +728,21 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     const size_t oH = ws.reserve(sizeof(uint32_t) * (size_t)p.ntiles * p.nbins);
     const size_t oP = ws.reserve(sizeof(uint32_t) * (size_t)p.nchunks * p.nbins);
     const size_t oCP = ws.reserve(sizeof(uint32_t) * (size_t)(p.nbins + 1));
-    const size_t oKey = ws.reserve(sizeof(uint32_t) * (size_t)n);
-    const size_t oA = (mode != kModeVec) ? ws.reserve(sizeof(int32_t) * (size_t)n) : 0;
-    const size_t oLen = (mode == kModeCSR) ? ws.reserve(sizeof(int32_t) * (size_t)n) : 0;
-    const size_t oB = has_b ? ws.reserve(sizeof(float) * (size_t)n) : 0;
+    const size_t oRec = ws.reserve(sizeof(int4) * (size_t)n);
+    const size_t oR2 = (mode != kModeVec) ? ws.reserve(sizeof(int2) * (size_t)n) : 0;
+    const size_t oRB = has_b ? ws.reserve(sizeof(float) * (size_t)n) : 0;
     const size_t oBP = bucket_ptr_out ? 0 : ws.reserve(sizeof(int32_t) * (size_t)(m + 1));
+    const size_t oCnt = ws.reserve(sizeof(unsigned) * 4);
     CW_CUDA_TRY(ws.alloc());
     uint32_t* H = ws.at<uint32_t>(oH);
     uint32_t* P = ws.at<uint32_t>(oP);
     uint32_t* CP = ws.at<uint32_t>(oCP);
-    uint32_t* rkey = ws.at<uint32_t>(oKey);
-    int32_t* ra = (mode != kModeVec) ? ws.at<int32_t>(oA) : nullptr;
-    int32_t* rlen = (mode == kModeCSR) ? ws.at<int32_t>(oLen) : nullptr;
-    float* rb = has_b ? ws.at<float>(oB) : nullptr;
+    int4* rec = ws.at<int4>(oRec);
+    int2* r2 = (mode != kModeVec) ? ws.at<int2>(oR2) : nullptr;
+    float* rb = has_b ? ws.at<float>(oRB) : nullptr;
     int32_t* bptr = bucket_ptr_out ? bucket_ptr_out : ws.at<int32_t>(oBP);
+    unsigned* counter = ws.at<unsigned>(oCnt);
+    CW_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned) * 4, stream));
 
     {
         CW_PROF("k_tile_hist", stream);
@@ -931,47 +754,59 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
         CW_PROF("k_scan_chunk_sums", stream);
         k_scan_chunk_sums<<<sg, 256, 0, stream>>>(H, p.ntiles, p.nbins, P);
     }
-    CW_LAUNCH_CHECK();
     {
         CW_PROF("k_scan_bins", stream);
         k_scan_bins<<<1, 1024, 0, stream>>>(P, p.nchunks, p.nbins, CP, (uint32_t)n);
     }
-    CW_LAUNCH_CHECK();
     {
         CW_PROF("k_scan_tiles", stream);
         k_scan_tiles<<<sg, 256, 0, stream>>>(H, P, p.ntiles, p.nbins);
     }
     CW_LAUNCH_CHECK();
 
-    const size_t k3smem = sizeof(uint32_t) * kTileWarps * p.nbins;
-#define CW_K3(MODE, HB)                                                                             \
-    do {                                                                                            \
-        auto kf = k_coarse_scatter<MODE, HB>;                                                       \
-        CW_CUDA_TRY(set_smem(kf, k3smem));                                                          \
-        CW_PROF("k_coarse_scatter", stream);                                                        \
-        kf<<<p.ntiles, 256, k3smem, stream>>>(hp, i0, n, p.gshift, p.nbins, H, row_ptr, b, rkey, ra, \
-                                              rlen, rb, status);                                    \
+    const size_t k3smem = sizeof(uint32_t) * (size_t)kTileWarps * (p.nbins + kTileRowsPerWarp);
+#define CW_K3(MODE, HB)                                                                                    \
+    do {                                                                                                   \
+        auto kf = k_coarse_scatter<MODE, HB>;                                                              \
+        CW_CUDA_TRY(set_smem(kf, k3smem));                                                                 \
+        CW_PROF("k_coarse_scatter", stream);                                                               \
+        kf<<<p.ntiles, 256, k3smem, stream>>>(hp, i0, n, p.gshift, p.nbins, H, row_ptr, b, rec, status);   \
+    } while (0)
+#define CW_K4A(MODE, HB)                                                                      \
+    do {                                                                                      \
+        CW_PROF("k_fine_sort", stream);                                                       \
+        k_fine_sort<MODE, HB><<<p.nbins, 512, 0, stream>>>(rec, CP, m, p.gshift, r2, rb, bptr); \
     } while (0)
     if (mode == kModeCSR) {
-        if (has_b) CW_K3(kModeCSR, true); else CW_K3(kModeCSR, false);
+        if (has_b) { CW_K3(kModeCSR, true); CW_K4A(kModeCSR, true); }
+        else { CW_K3(kModeCSR, false); CW_K4A(kModeCSR, false); }
     } else if (mode == kModeDense) {
-        if (has_b) CW_K3(kModeDense, true); else CW_K3(kModeDense, false);
+        if (has_b) { CW_K3(kModeDense, true); CW_K4A(kModeDense, true); }
+        else { CW_K3(kModeDense, false); CW_K4A(kModeDense, false); }
     } else {
         CW_K3(kModeVec, true);
+        CW_K4A(kModeVec, true);
     }
 #undef CW_K3
+#undef CW_K4A
+    CW_LAUNCH_CHECK();
+    {
+        CW_PROF("k_set_last", stream);
+        k_set_last<<<1, 1, 0, stream>>>(bptr, m, (int32_t)n);
+    }
     CW_LAUNCH_CHECK();
 
     if (mode == kModeCSR) {
-        CsrApplyArgs a{rkey, ra, rlen, rb, CP, col, val, SA, Sb, bptr, status, m, (int)d, p.dpad,
-                       p.gshift, p.cap, p.acc_global};
-        const int threads = p.warps * 32;
+        const bool vec4 = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(SA) & 15) == 0);
+        CsrApplyArgs a{r2, rb, bptr, col, val, SA, Sb, counter, status, m, (int)d, p.dpad, p.acc_global,
+                       vec4 ? 1 : 0};
 #define CW_K4C(LPR, HB)                                                   \
     do {                                                                  \
         auto kf = k_apply_csr<LPR, 8, HB>;                                \
-        CW_CUDA_TRY(set_smem(kf, p.smem));                                \
+        CW_CUDA_TRY(set_smem(kf, p.acc_smem));                            \
+        const int grid = persistent_grid(kf, 256, p.acc_smem);            \
         CW_PROF("k_apply_csr", stream);                                   \
-        kf<<<p.nbins, threads, p.smem, stream>>>(a);                      \
+        kf<<<grid, 256, p.acc_smem, stream>>>(a);                         \
     } while (0)
         if (p.lpr == 16) {
             if (has_b) CW_K4C(16, true); else CW_K4C(16, false);
@@ -981,46 +816,37 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
 #undef CW_K4C
     } else if (mode == kModeDense) {
         const bool vec4 = (lda % 4 == 0) && (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
-                          ((reinterpret_cast<uintptr_t>(SA) & 15) == 0);
-        DenseApplyArgs a{rkey, ra, rb, CP, A, lda, SA, Sb, bptr, m, (int)d, p.gshift, p.cap, vec4 ? 1 : 0, SA64};
-        const int threads = p.warps * 32;
+                          (SA64 || (reinterpret_cast<uintptr_t>(SA) & 15) == 0);
+        DenseApplyArgs a{r2, rb, bptr, A, lda, SA, Sb, counter, m, (int)d, vec4 ? 1 : 0, SA64};
         const int nv = d <= 128 ? 1 : d <= 256 ? 2 : d <= 512 ? 4 : 8;
-#define CW_K4D(NV, U, HB)                                                 \
+#define CW_K4D(NV, U, HB, PR, NAME)                                       \
     do {                                                                  \
-        auto kf = k_apply_dense<NV, U, HB, false>;                        \
-        CW_CUDA_TRY(set_smem(kf, p.smem));                                \
-        CW_PROF("k_apply_dense", stream);                                 \
-        kf<<<p.nbins, threads, p.smem, stream>>>(a);                      \
-    } while (0)
-#define CW_K4P(NV, U)                                                     \
-    do {                                                                  \
-        auto kf = k_apply_dense<NV, U, false, true>;                      \
-        CW_CUDA_TRY(set_smem(kf, p.smem));                                \
-        CW_PROF("k_apply_dense_precise", stream);                         \
-        kf<<<p.nbins, threads, p.smem, stream>>>(a);                      \
+        auto kf = k_apply_dense<NV, U, HB, PR>;                           \
+        const int grid = persistent_grid(kf, 256, 0);                     \
+        CW_PROF(NAME, stream);                                            \
+        kf<<<grid, 256, 0, stream>>>(a);                                  \
     } while (0)
         if (SA64) {
-            if (nv == 1) CW_K4P(1, 8); else if (nv == 2) CW_K4P(2, 4);
-            else if (nv == 4) CW_K4P(4, 4); else CW_K4P(8, 2);
+            if (nv == 1) CW_K4D(1, 8, false, true, "k_apply_dense_precise");
+            else if (nv == 2) CW_K4D(2, 4, false, true, "k_apply_dense_precise");
+            else if (nv == 4) CW_K4D(4, 4, false, true, "k_apply_dense_precise");
+            else CW_K4D(8, 2, false, true, "k_apply_dense_precise");
         } else if (has_b) {
-            if (nv == 1) CW_K4D(1, 8, true); else if (nv == 2) CW_K4D(2, 4, true);
-            else if (nv == 4) CW_K4D(4, 4, true); else CW_K4D(8, 2, true);
+            if (nv == 1) CW_K4D(1, 8, true, false, "k_apply_dense");
+            else if (nv == 2) CW_K4D(2, 4, true, false, "k_apply_dense");
+            else if (nv == 4) CW_K4D(4, 4, true, false, "k_apply_dense");
+            else CW_K4D(8, 2, true, false, "k_apply_dense");
         } else {
-            if (nv == 1) CW_K4D(1, 8, false); else if (nv == 2) CW_K4D(2, 4, false);
-            else if (nv == 4) CW_K4D(4, 4, false); else CW_K4D(8, 2, false);
+            if (nv == 1) CW_K4D(1, 8, false, false, "k_apply_dense");
+            else if (nv == 2) CW_K4D(2, 4, false, false, "k_apply_dense");
+            else if (nv == 4) CW_K4D(4, 4, false, false, "k_apply_dense");
+            else CW_K4D(8, 2, false, false, "k_apply_dense");
         }
 #undef CW_K4D
-#undef CW_K4P
     } else {
-        auto kf = k_apply_vec;
-        CW_CUDA_TRY(set_smem(kf, p.smem));
+        const int grid = persistent_grid(k_apply_vec, 256, 0);
         CW_PROF("k_apply_vec", stream);
-        kf<<<p.nbins, p.warps * 32, p.smem, stream>>>(rkey, rb, CP, m, p.gshift, p.cap, Sb, bptr);
-    }
-    CW_LAUNCH_CHECK();
-    {
-        CW_PROF("k_set_last", stream);
-        k_set_last<<<1, 1, 0, stream>>>(bptr, m, (int32_t)n);
+        k_apply_vec<<<grid, 256, 0, stream>>>(rb, bptr, m, Sb, counter);
     }
     CW_LAUNCH_CHECK();
     return CW_OK;

@@ -152,12 +152,20 @@ def test_sketch_csr_flags_bad_column(cw):
     cw.device_status()  # flag is cleared
 
 
-def test_sketch_csr_flags_duplicate_column(cw):
-    A = W.csr_uniform(1000, 10, 3, seed=2)
-    A.col[1] = A.col[0]
-    cw.cw_sketch_csr(A.to("cuda"), None, 64, 1)
-    with pytest.raises(cw.CWError):
-        cw.device_status()
+def test_csr_check_finds_every_violation(cw):
+    good = W.csr_random_lengths(5000, 40, 0, 40, seed=2, empty_frac=0.1)
+    cw.cw_csr_check(good.to("cuda"))
+    dup = W.csr_uniform(1000, 10, 3, seed=2)
+    dup.col[1] = dup.col[0]
+    bad_col = W.csr_uniform(1000, 10, 3, seed=2)
+    bad_col.col[7] = -1
+    bad_ptr = W.csr_uniform(1000, 10, 3, seed=2)
+    bad_ptr.row_ptr[5] = bad_ptr.row_ptr[6] + 1
+    long_dup = W.csr_random_lengths(50, 100, 70, 80, seed=3)
+    long_dup.col[int(long_dup.row_ptr[3]) + 65] = long_dup.col[int(long_dup.row_ptr[3]) + 2]
+    for A in (dup, bad_col, bad_ptr, long_dup):
+        with pytest.raises(cw.CWError):
+            cw.cw_csr_check(A.to("cuda"))
 
 
 @pytest.mark.parametrize("n,d,lda,m,seed", [
