@@ -37,7 +37,7 @@ struct PassArgs {
     const float* vhat;     // d
     const float* zin;      // n (z of the previous step, or b for the first pass)
     float* zout;           // n
-    double* gpart;         // [grid][d]
+    float2* gpart;         // [grid][d] two-word (hi, lo) partial sums of A^T z
     double* zpart;         // [grid]
     double* bpart;         // [grid] (sum of zin^2; first pass only)
     const LsqrState* st;   // coef, done
@@ -93,22 +93,26 @@ template <int LPR, int kPassWarps>
 __global__ void __launch_bounds__(kPassWarps * 32, 1) k_lsqr_pass(PassArgs a) {
     extern __shared__ __align__(16) float sm[];
     if (a.st && a.st->done) return;
-    constexpr int HALVES = 32 / LPR;          // rows processed side by side
+    constexpr int HALVES = 32 / LPR;          // rows processed side by side (scalar path)
     constexpr int RPH = kPassBatch / HALVES;  // rows per sub-warp per batch
+    constexpr int COPIES = 8;                 // accumulator copies per warp (quad path: one per row slot)
+    static_assert(HALVES <= COPIES, "copies");
     const float coef = a.st ? (float)a.st->coef : a.coef_first;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sub = lane / LPR, sl = lane % LPR;
     float* vh = sm;                                         // [dpad]
-    float* acc = vh + a.dpad;                               // [warps][HALVES][dpad]
+    float* acc = vh + a.dpad;                               // [warps][COPIES][dpad]
     // stage buffers start on a 128-byte boundary (16-byte cp.async targets)
-    const size_t stage_off = (((size_t)(1 + kPassWarps * HALVES) * a.dpad * sizeof(float)) + 127) & ~size_t(127);
+    const size_t stage_off = (((size_t)(1 + kPassWarps * COPIES) * a.dpad * sizeof(float)) + 127) & ~size_t(127);
     int32_t* stage = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(sm) + stage_off);
     const bool vec16 = ((reinterpret_cast<uintptr_t>(a.col) | reinterpret_cast<uintptr_t>(a.val)) & 15) == 0;
     int32_t* wst = stage + (size_t)warp * kPassStages * 2 * (kPassCap + 8);
     for (int j = threadIdx.x; j < a.d; j += blockDim.x) vh[j] = a.vhat[j];
-    for (int q = threadIdx.x; q < kPassWarps * HALVES * a.dpad; q += blockDim.x) acc[q] = 0.f;
+    for (int q = threadIdx.x; q < kPassWarps * COPIES * a.dpad; q += blockDim.x) acc[q] = 0.f;
     __syncthreads();
-    float* myacc = acc + (size_t)(warp * HALVES + sub) * a.dpad;
+    float* myacc = acc + (size_t)(warp * COPIES + sub) * a.dpad;
+    const int qd = lane >> 2, ql = lane & 3;                // quad path: row slot, lane in quad
+    float* qacc = acc + (size_t)(warp * COPIES + qd) * a.dpad;
 
     // this warp's contiguous rows
     const int64_t nw = (int64_t)gridDim.x * kPassWarps;
@@ -164,11 +168,67 @@ __global__ void __launch_bounds__(kPassWarps * 32, 1) k_lsqr_pass(PassArgs a) {
         const int32_t* scol = wst + (size_t)(k % kPassStages) * 2 * (kPassCap + 8);
         const float* sval = reinterpret_cast<const float*>(scol + kPassCap + 8);
         float zreg = 0.f;
-        // RI rows of this sub-warp at a time: independent dot products and
-        // reductions interleave; the A^T z updates then go row by row in order
+        // quad path: every row of the batch starts on a 4-element boundary and
+        // has a multiple of 4 (at most 16) entries -> 4 lanes per row, 4 entries
+        // per lane from 16-byte shared loads, 8 rows per warp step, row slot q
+        // of each step accumulating into copy q (rows in ascending order).
+        bool quad = false;
+        {
+            // every lane takes part in the shuffle and the vote (full masks)
+            const int32_t nxt = __shfl_down_sync(0xFFFFFFFFu, rpA, 1);
+            const int32_t myl = (lane < nrows) ? ((lane + 1 < nrows) ? nxt : reA) - rpA : 0;
+            const bool ok = (lane >= nrows) || (((rpA & 3) == 0) && ((myl & 3) == 0) && myl <= 16);
+            quad = __all_sync(0xFFFFFFFFu, ok) && staged && vec16;
+        }
+        if (quad) {
+#pragma unroll 1
+            for (int step = 0; step < kPassBatch / 8; ++step) {
+                const int row = step * 8 + qd;
+                const int32_t rs = __shfl_sync(0xFFFFFFFFu, rpA, row);
+                const int32_t rn = __shfl_sync(0xFFFFFFFFu, rpA, (row + 1) & 31);
+                const float zold = __shfl_sync(0xFFFFFFFFu, zoA, row);
+                const int32_t re = (row + 1 < nrows) ? rn : reA;
+                const int len = row < nrows ? re - rs : 0;
+                const bool act = 4 * ql < len;
+                int4 c4 = make_int4(0, 0, 0, 0);
+                float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (act) {
+                    c4 = *reinterpret_cast<const int4*>(scol + (rs - base) + 4 * ql);
+                    v4 = *reinterpret_cast<const float4*>(sval + (rs - base) + 4 * ql);
+                    const unsigned cmax = max(max((unsigned)c4.x, (unsigned)c4.y), max((unsigned)c4.z, (unsigned)c4.w));
+                    if (cmax >= (unsigned)a.d) {
+                        flag_error(a.status, kDevBadColumn);
+                        c4 = make_int4(0, 0, 0, 0);
+                        v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+                float p = 0.f;
+                if (act) {
+                    p = v4.x * vh[c4.x];
+                    p = fmaf(v4.y, vh[c4.y], p);
+                    p = fmaf(v4.z, vh[c4.z], p);
+                    p = fmaf(v4.w, vh[c4.w], p);
+                }
+                p += __shfl_xor_sync(0xFFFFFFFFu, p, 1);
+                p += __shfl_xor_sync(0xFFFFFFFFu, p, 2);
+                const float z = p - coef * zold;
+                const float zt = __shfl_sync(0xFFFFFFFFu, z, (lane & 7) * 4);
+                if ((lane >> 3) == step) zreg = zt;
+                if (act) {
+                    qacc[c4.x] = fmaf(v4.x, z, qacc[c4.x]);
+                    qacc[c4.y] = fmaf(v4.y, z, qacc[c4.y]);
+                    qacc[c4.z] = fmaf(v4.z, z, qacc[c4.z]);
+                    qacc[c4.w] = fmaf(v4.w, z, qacc[c4.w]);
+                }
+                __syncwarp();
+            }
+        }
+        // scalar path: RI rows of this sub-warp at a time: independent dot
+        // products and reductions interleave; the A^T z updates then go row by
+        // row in order
         constexpr int RI = 4;
 #pragma unroll 1
-        for (int t0 = 0; t0 < RPH; t0 += RI) {
+        for (int t0 = 0; t0 < (quad ? 0 : RPH); t0 += RI) {
             int32_t rs[RI];
             int len[RI];
             float zold[RI], p[RI];
@@ -243,9 +303,10 @@ __global__ void __launch_bounds__(kPassWarps * 32, 1) k_lsqr_pass(PassArgs a) {
                 __syncwarp();
             }
         }
-        // lane l of sub-warp h holds z of row h*RPH + l (l < RPH)
-        const int myrow = sub * RPH + sl;
-        if (sl < RPH && myrow < nrows) {
+        // scalar path: lane l of sub-warp h holds z of row h*RPH + l (l < RPH);
+        // quad path: lane l holds z of row l
+        const int myrow = quad ? lane : sub * RPH + sl;
+        if ((quad || sl < RPH) && myrow < nrows) {
             a.zout[r0 + myrow] = zreg;
             zz = fmaf(zreg, zreg, zz);
         }
@@ -256,12 +317,19 @@ __global__ void __launch_bounds__(kPassWarps * 32, 1) k_lsqr_pass(PassArgs a) {
     }
     cp_async_wait<0>();
     __syncthreads();
-    // per-CTA partials in float64, sub-warp accumulators summed in a fixed order
-    const int NS = kPassWarps * HALVES;
+    // per-CTA partials: the accumulator copies summed in a fixed order with an
+    // exact two-sum (float32 hi + lo), so no float64 pipe work per CTA
+    const int NS = kPassWarps * COPIES;
     for (int j = threadIdx.x; j < a.d; j += blockDim.x) {
-        double sacc = 0.0;
-        for (int q = 0; q < NS; ++q) sacc += (double)acc[(size_t)q * a.dpad + j];
-        a.gpart[(size_t)blockIdx.x * a.d + j] = sacc;
+        float hi = 0.f, lo = 0.f;
+        for (int q = 0; q < NS; ++q) {
+            const float x = acc[(size_t)q * a.dpad + j];
+            const float t = hi + x;
+            const float bp = t - hi;
+            lo += (hi - (t - bp)) + (x - bp);
+            hi = t;
+        }
+        a.gpart[(size_t)blockIdx.x * a.d + j] = make_float2(hi, lo);
     }
     __shared__ double rz[kPassWarps], rb[kPassWarps];
     double zd = (double)zz, bd = (double)bb;
@@ -286,13 +354,12 @@ __global__ void __launch_bounds__(kPassWarps * 32, 1) k_lsqr_pass(PassArgs a) {
 }
 
 struct PostArgs {
-    const double* gpart;
+    const float2* gpart;
     const double* zpart;
     const double* bpart;  // first step only
     int nblk;
     int d;
-    const double* M;      // row-major d x d, upper triangular
-    const float* M32T;    // column-major float32 copy of M
+    const float* M32T;    // M = R^-1 (float32 values), column-major: M32T[j * d + i] = M_ij
     const double* y0;     // R x0
     double* v;
     double* w;
@@ -323,32 +390,22 @@ __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
     LsqrState* st = a.st;
     if (st->done) return;
     const int d = a.d;
-    // reduce the pass partials: G threads per column, each a fixed stripe of
-    // blocks, combined in stripe order (deterministic)
-    {
-        const int gper = blockDim.x / d >= 4 ? 4 : (blockDim.x / d >= 2 ? 2 : 1);
-        __shared__ double part4[1024];  // gper * d <= 1024
-        for (int t = threadIdx.x; t < d * gper; t += blockDim.x) {
-            const int j = t % d, g = t / d;
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            int b = g;
-            for (; b + 3 * gper < a.nblk; b += 4 * gper) {
-                s0 += a.gpart[(size_t)b * d + j];
-                s1 += a.gpart[(size_t)(b + gper) * d + j];
-                s2 += a.gpart[(size_t)(b + 2 * gper) * d + j];
-                s3 += a.gpart[(size_t)(b + 3 * gper) * d + j];
-            }
-            for (; b < a.nblk; b += gper) s0 += a.gpart[(size_t)b * d + j];
-            part4[g * d + j] = (s0 + s1) + (s2 + s3);
+    // reduce the pass partials (two-word sums, fixed order) -> g = A^T z as
+    // float32 (hi, lo) pairs in shared memory
+    __shared__ float ghi[1024], glo[1024];
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        float hi = 0.f, lo = 0.f;
+        for (int b = 0; b < a.nblk; ++b) {
+            const float2 x = a.gpart[(size_t)b * d + j];
+            const float t = hi + x.x;
+            const float bp = t - hi;
+            lo += (hi - (t - bp)) + (x.x - bp) + x.y;
+            hi = t;
         }
-        __syncthreads();
-        for (int j = threadIdx.x; j < d; j += blockDim.x) {
-            double t = 0.0;
-            for (int g = 0; g < gper; ++g) t += part4[g * d + j];
-            sg[j] = t;
-        }
-        __syncthreads();
+        ghi[j] = hi;
+        glo[j] = lo;
     }
+    __syncthreads();
     double zz = 0.0, bb = 0.0;
     for (int b = threadIdx.x; b < a.nblk; b += blockDim.x) {
         zz += a.zpart[b];
@@ -360,29 +417,32 @@ __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
     const double beta = sqrt(zz);
     // scale of u = z * s_new: z = A x0 - b = -r0 on the first step
     const double s_new = beta > 0.0 ? (a.first ? -1.0 / beta : 1.0 / beta) : 0.0;
-    // t = M^T (A^T z) with `gper` threads per column (fixed slices, fixed combine
-    // order); gvec = s_new * t - beta * v
-    __shared__ double tpart[1024];
+    // t = M^T (A^T z): exact float32 products (fma two-product) and two-word
+    // sums; `gper` threads per column over fixed slices, combined in order
+    __shared__ float2 tpart[1024];
     {
         const int gper = blockDim.x / d >= 4 ? 4 : (blockDim.x / d >= 2 ? 2 : 1);
         for (int tq = threadIdx.x; tq < d * gper; tq += blockDim.x) {
             const int j = tq % d, g = tq / d;
             const int len = j + 1, lo = (int)((int64_t)len * g / gper), hi = (int)((int64_t)len * (g + 1) / gper);
-            double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
-            int i = lo;
-            for (; i + 3 < hi; i += 4) {
-                t0 += a.M[(size_t)i * d + j] * sg[i];
-                t1 += a.M[(size_t)(i + 1) * d + j] * sg[i + 1];
-                t2 += a.M[(size_t)(i + 2) * d + j] * sg[i + 2];
-                t3 += a.M[(size_t)(i + 3) * d + j] * sg[i + 3];
+            const float* mcol = a.M32T + (size_t)j * d;
+            float sh = 0.f, sl2 = 0.f;
+            for (int i = lo; i < hi; ++i) {
+                const float mv = mcol[i];
+                const float p = mv * ghi[i];
+                float e = fmaf(mv, ghi[i], -p);
+                e = fmaf(mv, glo[i], e);
+                const float t = sh + p;
+                const float bp = t - sh;
+                sl2 += (sh - (t - bp)) + (p - bp) + e;
+                sh = t;
             }
-            for (; i < hi; ++i) t0 += a.M[(size_t)i * d + j] * sg[i];
-            tpart[g * d + j] = (t0 + t1) + (t2 + t3);
+            tpart[g * d + j] = make_float2(sh, sl2);
         }
         __syncthreads();
         for (int j = threadIdx.x; j < d; j += blockDim.x) {
             double t = 0.0;
-            for (int g = 0; g < gper; ++g) t += tpart[g * d + j];
+            for (int g = 0; g < gper; ++g) t += (double)tpart[g * d + j].x + (double)tpart[g * d + j].y;
             sv[j] = t;
         }
         __syncthreads();
@@ -473,7 +533,10 @@ __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
     __syncthreads();
     // next vhat = M v (float32; it feeds the float32 pass)
     {
-        // vhat = M v with `gper` threads per row (fixed slices, fixed combine order)
+        // vhat = M v in float32, `gper` threads per row (fixed slices, fixed combine order)
+        __shared__ float vf[1024];
+        for (int j = threadIdx.x; j < d; j += blockDim.x) vf[j] = (float)sv[j];
+        __syncthreads();
         const int gper = blockDim.x / d >= 4 ? 4 : (blockDim.x / d >= 2 ? 2 : 1);
         float* vpart = reinterpret_cast<float*>(sg);  // sg no longer needed
         for (int tq = threadIdx.x; tq < d * gper; tq += blockDim.x) {
@@ -482,12 +545,12 @@ __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
             float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
             int j = lo;
             for (; j + 3 < hi; j += 4) {
-                s0 = fmaf(a.M32T[(size_t)j * d + i], (float)sv[j], s0);
-                s1 = fmaf(a.M32T[(size_t)(j + 1) * d + i], (float)sv[j + 1], s1);
-                s2 = fmaf(a.M32T[(size_t)(j + 2) * d + i], (float)sv[j + 2], s2);
-                s3 = fmaf(a.M32T[(size_t)(j + 3) * d + i], (float)sv[j + 3], s3);
+                s0 = fmaf(a.M32T[(size_t)j * d + i], vf[j], s0);
+                s1 = fmaf(a.M32T[(size_t)(j + 1) * d + i], vf[j + 1], s1);
+                s2 = fmaf(a.M32T[(size_t)(j + 2) * d + i], vf[j + 2], s2);
+                s3 = fmaf(a.M32T[(size_t)(j + 3) * d + i], vf[j + 3], s3);
             }
-            for (; j < hi; ++j) s0 = fmaf(a.M32T[(size_t)j * d + i], (float)sv[j], s0);
+            for (; j < hi; ++j) s0 = fmaf(a.M32T[(size_t)j * d + i], vf[j], s0);
             vpart[g * d + i] = (s0 + s1) + (s2 + s3);
         }
         __syncthreads();
@@ -499,11 +562,15 @@ __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
     }
 }
 
-__global__ void k_to_f32_transposed(const double* __restrict__ M, int d, float* __restrict__ MT) {
+// MT = float32 transpose of M (column-major copy); M itself is rounded to the
+// same float32 values so that every use of the preconditioner agrees.
+__global__ void k_to_f32_transposed(double* __restrict__ M, int d, float* __restrict__ MT) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q < (int64_t)d * d) {
         const int i = (int)(q / d), j = (int)(q % d);
-        MT[(size_t)j * d + i] = (float)M[q];
+        const float v = (float)M[q];
+        MT[(size_t)j * d + i] = v;
+        M[q] = (double)v;
     }
 }
 
@@ -542,11 +609,16 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     const int64_t n = A->n;
     const int nsm = num_sms();
     const int grid = nsm;
-    const int pass_warps = d <= 256 ? 16 : (d <= 512 ? 8 : 4);
+    // warps per CTA: as many as the per-warp shared memory (8 accumulator
+    // copies of d floats + two cp.async stages) allows, from {12, 8, 4}
+    const size_t per_warp = sizeof(float) * 8 * (size_t)(((d + 31) & ~31) + 1) +
+                            sizeof(int32_t) * kPassStages * 2 * (kPassCap + 8);
+    const int fit = (int)((220 * 1024) / per_warp);
+    const int pass_warps = fit >= 12 ? 12 : (fit >= 8 ? 8 : 4);
     const int threads = pass_warps * 32;
     const int lpr = 16;
     const int dpad = ((d + 31) & ~31) + 1;
-    const int nsub = pass_warps * (32 / lpr);
+    const int nsub = pass_warps * 8;  // accumulator copies
 
     Scratch ws(stream);
     const size_t oSA = ws.reserve(sizeof(float) * (size_t)m * d);
@@ -563,7 +635,7 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     const size_t og = ws.reserve(sizeof(double) * (size_t)d);
     const size_t ovh = ws.reserve(sizeof(float) * (size_t)d);
     const size_t oz = ws.reserve(sizeof(float) * (size_t)(n > 0 ? n : 1));
-    const size_t ogp = ws.reserve(sizeof(double) * (size_t)grid * d);
+    const size_t ogp = ws.reserve(sizeof(float2) * (size_t)grid * d);
     const size_t ozp = ws.reserve(sizeof(double) * (size_t)grid);
     const size_t obp = ws.reserve(sizeof(double) * (size_t)grid);
     const size_t ost = ws.reserve(sizeof(LsqrState));
@@ -620,16 +692,16 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     const size_t pass_smem = ((sizeof(float) * (size_t)dpad * (1 + nsub) + 127) & ~size_t(127)) +
                              sizeof(int32_t) * (size_t)pass_warps * kPassStages * 2 * (kPassCap + 8);
     if (pass_smem > 227 * 1024) return CW_ERR_SHAPE;
-    auto pk = pass_warps == 16 ? k_lsqr_pass<16, 16> : (pass_warps == 8 ? k_lsqr_pass<16, 8> : k_lsqr_pass<16, 4>);
+    auto pk = pass_warps == 12 ? k_lsqr_pass<16, 12> : (pass_warps == 8 ? k_lsqr_pass<16, 8> : k_lsqr_pass<16, 4>);
     CW_CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem));
-    PassArgs pa{A->row_ptr, A->col, A->val, vhat, b, z, ws.at<double>(ogp), ws.at<double>(ozp), ws.at<double>(obp),
+    PassArgs pa{A->row_ptr, A->col, A->val, vhat, b, z, ws.at<float2>(ogp), ws.at<double>(ozp), ws.at<double>(obp),
                 nullptr, status, n, d, dpad, 1.0f};
     {
         CW_PROF("k_lsqr_pass", stream);
         pk<<<grid, threads, pass_smem, stream>>>(pa);  // z = A x0 - b
     }
     CW_LAUNCH_CHECK();
-    PostArgs qa{ws.at<double>(ogp), ws.at<double>(ozp), ws.at<double>(obp), grid, d, M, M32T, y0,
+    PostArgs qa{ws.at<float2>(ogp), ws.at<double>(ozp), ws.at<double>(obp), grid, d, M32T, y0,
                 ws.at<double>(ov), ws.at<double>(ow), ws.at<double>(ody), ws.at<double>(og), vhat, state, rtol,
                 max_iter, 1};
     {

@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(512) k_fine_sort(const int4* __restrict__ rec,
     const uint32_t seg = ((len + nwarps - 1) / nwarps + 31) & ~31u;
     const uint32_t s0 = r0 + min(len, seg * warp), s1 = r0 + min(len, seg * (warp + 1));
     uint32_t* wc = cnt + warp * G;
+#pragma unroll 4
     for (uint32_t k = s0 + lane; k < s1; k += 32) atomicAdd(&wc[(uint32_t)__ldg(&rec[k].x) & (G - 1)], 1u);
     __syncthreads();
     // bucket totals -> exclusive scan (G <= blockDim)
@@ -315,12 +316,22 @@ __global__ void __launch_bounds__(512) k_fine_sort(const int4* __restrict__ rec,
     }
     __syncthreads();
     const unsigned lt = lanemask_lt();
-    for (uint32_t kb = s0; kb < s1; kb += 32) {
+    constexpr int PF = 4;  // records loaded ahead per lane
+    for (uint32_t kb0 = s0; kb0 < s1; kb0 += 32 * PF) {
+      int4 rq[PF];
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+          const uint32_t k = kb0 + 32 * u + lane;
+          rq[u] = (k < s1) ? __ldg(&rec[k]) : make_int4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const uint32_t kb = kb0 + 32 * u;
+        if (kb >= s1) break;
         const uint32_t k = kb + lane;
         const bool valid = k < s1;
         const unsigned am = __ballot_sync(0xFFFFFFFFu, valid);
-        int4 r = make_int4(0, 0, 0, 0);
-        if (valid) r = __ldg(&rec[k]);
+        const int4 r = rq[u];
         const uint32_t key = (uint32_t)r.x;
         const uint32_t fb = key & (G - 1);
         unsigned peers = 0;
@@ -340,6 +351,7 @@ __global__ void __launch_bounds__(512) k_fine_sort(const int4* __restrict__ rec,
                 out2[r0 + pos] = make_int2((int)((uint32_t)r.y | sgn), 0);
             if (HAS_B) outb[r0 + pos] = __int_as_float(r.w);
         }
+      }
     }
 }
 
