@@ -390,22 +390,53 @@ __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
     LsqrState* st = a.st;
     if (st->done) return;
     const int d = a.d;
-    // reduce the pass partials (two-word sums, fixed order) -> g = A^T z as
-    // float32 (hi, lo) pairs in shared memory
+    // reduce the pass partials (two-word sums) -> g = A^T z as float32 (hi, lo)
+    // pairs in shared memory; `gp` threads per column take fixed stripes of
+    // blocks, four independent loads in flight, stripes combined in order
     __shared__ float ghi[1024], glo[1024];
-    for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        float hi = 0.f, lo = 0.f;
-        for (int b = 0; b < a.nblk; ++b) {
-            const float2 x = a.gpart[(size_t)b * d + j];
-            const float t = hi + x.x;
-            const float bp = t - hi;
-            lo += (hi - (t - bp)) + (x.x - bp) + x.y;
-            hi = t;
+    {
+        __shared__ float2 gstripe[1024];
+        const int gp = blockDim.x / d >= 4 ? 4 : (blockDim.x / d >= 2 ? 2 : 1);
+        for (int tq = threadIdx.x; tq < d * gp; tq += blockDim.x) {
+            const int j = tq % d, g = tq / d;
+            float hi = 0.f, lo = 0.f;
+            int b = g;
+            for (; b + 3 * gp < a.nblk; b += 4 * gp) {
+                float2 x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = a.gpart[(size_t)(b + u * gp) * d + j];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float t = hi + x[u].x;
+                    const float bp = t - hi;
+                    lo += (hi - (t - bp)) + (x[u].x - bp) + x[u].y;
+                    hi = t;
+                }
+            }
+            for (; b < a.nblk; b += gp) {
+                const float2 x = a.gpart[(size_t)b * d + j];
+                const float t = hi + x.x;
+                const float bp = t - hi;
+                lo += (hi - (t - bp)) + (x.x - bp) + x.y;
+                hi = t;
+            }
+            gstripe[g * d + j] = make_float2(hi, lo);
         }
-        ghi[j] = hi;
-        glo[j] = lo;
+        __syncthreads();
+        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+            float hi = 0.f, lo = 0.f;
+            for (int g = 0; g < gp; ++g) {
+                const float2 x = gstripe[g * d + j];
+                const float t = hi + x.x;
+                const float bp = t - hi;
+                lo += (hi - (t - bp)) + (x.x - bp) + x.y;
+                hi = t;
+            }
+            ghi[j] = hi;
+            glo[j] = lo;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     double zz = 0.0, bb = 0.0;
     for (int b = threadIdx.x; b < a.nblk; b += blockDim.x) {
         zz += a.zpart[b];
@@ -427,15 +458,22 @@ __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
             const int len = j + 1, lo = (int)((int64_t)len * g / gper), hi = (int)((int64_t)len * (g + 1) / gper);
             const float* mcol = a.M32T + (size_t)j * d;
             float sh = 0.f, sl2 = 0.f;
-            for (int i = lo; i < hi; ++i) {
-                const float mv = mcol[i];
-                const float p = mv * ghi[i];
-                float e = fmaf(mv, ghi[i], -p);
-                e = fmaf(mv, glo[i], e);
-                const float t = sh + p;
-                const float bp = t - sh;
-                sl2 += (sh - (t - bp)) + (p - bp) + e;
-                sh = t;
+            int i = lo;
+            for (; i < hi; i += 8) {
+                float mv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) mv[u] = (i + u < hi) ? mcol[i + u] : 0.f;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (i + u >= hi) break;
+                    const float p = mv[u] * ghi[i + u];
+                    float e = fmaf(mv[u], ghi[i + u], -p);
+                    e = fmaf(mv[u], glo[i + u], e);
+                    const float t = sh + p;
+                    const float bp = t - sh;
+                    sl2 += (sh - (t - bp)) + (p - bp) + e;
+                    sh = t;
+                }
             }
             tpart[g * d + j] = make_float2(sh, sl2);
         }
