@@ -130,6 +130,31 @@ int cw_sketch_csr_rows(const cw_csr *A, int64_t i0, const float *b, int64_t m, u
                        float *SA, float *Sb, cw_stream stream);
 
 /*
+ * cw_sketch_csr_noalloc - cw_sketch_csr for callers that cannot allocate
+ * device memory during the call: code that runs under its own allocator owning
+ * the device's memory, latency-critical paths where a pool allocation could
+ * block, or hosts whose allocator must not be re-entered.  (Not a step of the
+ * paper's method: the paper has no counterpart; it is a deployment variant.)
+ * Same arguments, results and determinism as cw_sketch_csr, but every scratch
+ * byte comes from one static device array of 24 MiB built into the library,
+ * so this call makes no cudaMalloc / cudaMallocAsync / cudaFree call and no
+ * allocating library call.  Every GPU that loads the library holds that array
+ * until the process exits.
+ * Limit: n * 28 + (m + 1) * 4 bytes plus the tile histograms must fit in
+ * 24 MiB (roughly n <= 800,000 rows for m = 65536); larger problems return
+ * CW_ERR_SHAPE without launching anything.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before capturing
+ * any stream.  All calls share the array and it keeps the previous call's
+ * contents (what must start at zero is cleared by every call); calls whose
+ * work can overlap on the GPU race on it and must be ordered by the caller.
+ * Input errors found on the device are kept in a separate static flag and are
+ * not reported by cw_device_status().  Asynchronous.
+ */
+int cw_sketch_csr_noalloc(const cw_csr *A, const float *b, int64_t m, uint64_t seed, float *SA,
+                          float *Sb, cw_stream stream);
+
+/*
  * cw_sketch_dense - SA and Sb for dense row-major A (n x d, leading dimension
  * lda >= d).  Same limits and outputs as cw_sketch_csr.  Asynchronous.
  */

@@ -26,7 +26,7 @@ __all__ = [
 HEADER = os.path.join(_build.ROOT, "include", "cw.h")
 EXPORTS = (
     "cw_status_string", "cw_version", "cw_device_status", "cw_csr_check", "cw_hash", "cw_sketch_csr",
-    "cw_sketch_csr_rows", "cw_sketch_dense", "cw_sketch_vec", "cw_qr", "cw_solve_sketch",
+    "cw_sketch_csr_rows", "cw_sketch_csr_noalloc", "cw_sketch_dense", "cw_sketch_vec", "cw_qr", "cw_solve_sketch",
     "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage", "cw_launch_count", "cw_profile_enable",
     "cw_profile_get", "cw_profile_reset",
 )
@@ -54,6 +54,7 @@ _SIGS = {
     "cw_hash": ([_u64, _i64, _i64, _i64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_csr": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_csr_rows": ([ctypes.POINTER(_CSR), _i64, _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
+    "cw_sketch_csr_noalloc": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_dense": ([_p, _i64, _i64, _i64, _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_vec": ([_p, _i64, _i64, _u64, _p, _p], ctypes.c_int),
     "cw_qr": ([_p, _i64, _i64, _p, _p, _p, _p], ctypes.c_int),

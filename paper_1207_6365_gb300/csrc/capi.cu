@@ -88,9 +88,15 @@ void resolve_pending_locked() {
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+namespace {
+thread_local int t_prof_suppress = 0;
+}
+ProfSuppress::ProfSuppress() { ++t_prof_suppress; }
+ProfSuppress::~ProfSuppress() { --t_prof_suppress; }
+
 ProfScope::ProfScope(const char* name, cudaStream_t s) : name_(name), s_(s), a_(nullptr) {
     count_launch();
-    if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    if (!g_prof_on.load(std::memory_order_relaxed) || t_prof_suppress) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     a_ = take_event();
     if (a_) cudaEventRecord((cudaEvent_t)a_, s_);

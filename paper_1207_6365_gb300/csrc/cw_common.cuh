@@ -195,6 +195,15 @@ class ProfScope {
     void* a_;
 };
 
+// While alive on a thread, ProfScope records no events on that thread.
+class ProfSuppress {
+  public:
+    ProfSuppress();
+    ~ProfSuppress();
+    ProfSuppress(const ProfSuppress&) = delete;
+    ProfSuppress& operator=(const ProfSuppress&) = delete;
+};
+
 #define CW_PROF_CAT2(a, b) a##b
 #define CW_PROF_CAT(a, b) CW_PROF_CAT2(a, b)
 #define CW_PROF(name, stream) ::cw::ProfScope CW_PROF_CAT(_cw_prof_scope_, __LINE__)(name, stream)
@@ -206,6 +215,9 @@ class ProfScope {
 class Scratch {
   public:
     explicit Scratch(cudaStream_t s) : s_(s) {}
+    // Carve from a caller-owned buffer instead of allocating: alloc() then
+    // fails with cudaErrorMemoryAllocation when the reservations exceed `bytes`.
+    Scratch(cudaStream_t s, void* external, size_t bytes) : s_(s), ext_(external), ext_bytes_(bytes) {}
     ~Scratch() { release(); }
     Scratch(const Scratch&) = delete;
     Scratch& operator=(const Scratch&) = delete;
@@ -217,24 +229,30 @@ class Scratch {
         return off;
     }
     cudaError_t alloc() {
+        if (ext_) {
+            if (size_ > ext_bytes_) return cudaErrorMemoryAllocation;
+            base_ = ext_;
+            return cudaSuccess;
+        }
         if (size_ == 0) return cudaSuccess;
         return cudaMallocAsync(&base_, size_, s_);
     }
+    size_t size() const { return size_; }
     template <class T>
     T* at(size_t off) const {
         return reinterpret_cast<T*>(static_cast<char*>(base_) + off);
     }
     void release() {
-        if (base_) {
-            cudaFreeAsync(base_, s_);
-            base_ = nullptr;
-        }
+        if (base_ && !ext_) cudaFreeAsync(base_, s_);
+        base_ = nullptr;
     }
 
   private:
     cudaStream_t s_;
     void* base_ = nullptr;
     size_t size_ = 0;
+    void* ext_ = nullptr;
+    size_t ext_bytes_ = 0;
 };
 
 inline int num_sms() {

@@ -8,11 +8,19 @@ namespace cw {
 
 enum SketchModeId { kSketchCSR = 0, kSketchDense = 1, kSketchVec = 2 };
 
-// SA / Sb of a CSR, dense or vector input (see sketch.cu).
+// Caller-provided scratch for sketch_impl (no allocation inside the call).
+struct SketchWorkspace {
+    void* base;        // device memory, 256-byte aligned
+    size_t bytes;
+    unsigned* status;  // device word for the sticky input-error flags
+};
+
+// SA / Sb of a CSR, dense or vector input (see sketch.cu).  With `ext`, all
+// scratch is carved from ext->base (CW_ERR_SHAPE when it does not fit).
 int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const int32_t* row_ptr,
                 const int32_t* col, const float* val, const float* A, const float* b, int64_t m,
                 uint64_t seed, float* SA, float* Sb, int32_t* bucket_ptr_out, cudaStream_t stream,
-                double* SA64 = nullptr);
+                double* SA64 = nullptr, const SketchWorkspace* ext = nullptr);
 int validate_common(int64_t n, int64_t d, int64_t m);
 
 // float64 Householder QR of [SA | Sb]; synchronises.  SA64 (row-major float64)

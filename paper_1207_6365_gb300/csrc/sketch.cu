@@ -720,7 +720,7 @@ static int persistent_grid(F* f, int threads, size_t smem) {
 int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const int32_t* row_ptr,
                 const int32_t* col, const float* val, const float* A, const float* b, int64_t m,
                 uint64_t seed, float* SA, float* Sb, int32_t* bucket_ptr_out, cudaStream_t stream,
-                double* SA64) {
+                double* SA64, const SketchWorkspace* ext) {
     const bool has_b = b != nullptr && (mode == kModeVec || Sb != nullptr);
     if (n == 0) {
         if (SA && d > 0) CW_CUDA_TRY(cudaMemsetAsync(SA, 0, sizeof(float) * (size_t)m * (size_t)d, stream));
@@ -732,11 +732,11 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     SketchPlan p;
     int st = plan_sketch(mode, n, d, m, &p);
     if (st != CW_OK) return st;
-    unsigned* status = device_status_word();
+    unsigned* status = ext ? ext->status : device_status_word();
     if (!status) return CW_ERR_CUDA;
     const HashParams hp = make_hash_params(seed, m);
 
-    Scratch ws(stream);
+    Scratch ws = ext ? Scratch(stream, ext->base, ext->bytes) : Scratch(stream);
     const size_t oH = ws.reserve(sizeof(uint32_t) * (size_t)p.ntiles * p.nbins);
     const size_t oP = ws.reserve(sizeof(uint32_t) * (size_t)p.nchunks * p.nbins);
     const size_t oCP = ws.reserve(sizeof(uint32_t) * (size_t)(p.nbins + 1));
@@ -745,6 +745,7 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     const size_t oRB = has_b ? ws.reserve(sizeof(float) * (size_t)n) : 0;
     const size_t oBP = bucket_ptr_out ? 0 : ws.reserve(sizeof(int32_t) * (size_t)(m + 1));
     const size_t oCnt = ws.reserve(sizeof(unsigned) * 4);
+    if (ext && ws.size() > ext->bytes) return CW_ERR_SHAPE;
     CW_CUDA_TRY(ws.alloc());
     uint32_t* H = ws.at<uint32_t>(oH);
     uint32_t* P = ws.at<uint32_t>(oP);
