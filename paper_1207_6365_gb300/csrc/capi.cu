@@ -37,6 +37,28 @@ unsigned* device_status_word() {
     return g_status[dev];
 }
 
+namespace {
+std::mutex g_pool_mu;
+bool g_pool_done[kMaxDevices] = {false};
+}  // namespace
+
+void keep_pool_cached() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        (void)cudaGetLastError();
+        return;
+    }
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (g_pool_done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    (void)cudaGetLastError();
+    g_pool_done[dev] = true;
+}
+
 // ---------------------------------------------------------------- measurement hooks
 
 namespace {

@@ -210,6 +210,12 @@ class ProfSuppress {
 
 // ---------------------------------------------------------------- stream-ordered scratch
 
+// Keeps the current device's default memory pool from returning freed memory
+// to the driver at every synchronisation (its default release threshold is 0,
+// which makes the next cudaMallocAsync map fresh pages).  Process-local: it
+// changes this process's pool attribute only, once per device.
+void keep_pool_cached();
+
 // Scratch arena: one cudaMallocAsync on the call's stream, carved into
 // 256-byte aligned pieces, released with cudaFreeAsync on the same stream.
 class Scratch {
@@ -235,6 +241,7 @@ class Scratch {
             return cudaSuccess;
         }
         if (size_ == 0) return cudaSuccess;
+        keep_pool_cached();
         return cudaMallocAsync(&base_, size_, s_);
     }
     size_t size() const { return size_; }

@@ -383,106 +383,182 @@ __global__ void __launch_bounds__(1024) k_cholesky_f32(const double* __restrict_
         for (int i = threadIdx.x; i < d; i += blockDim.x) c[i] = (double)W[(int64_t)i * nc + d];
 }
 
-// Fast preconditioner in one CTA, all in shared memory (packed upper triangle,
-// float32): Cholesky G = R^T R of the Gram matrix (with the carried column
-// giving c = R^-T SA^T Sb), then M = R^-1 by Gauss-Jordan elimination on
-// [R | I] (right-looking, one barrier per step).  LSQR iterates on the operator
-// A M itself, so M only has to make A M well conditioned.  Outputs M (float64
-// row-major, upper), M32T (float32 column-major copy), c, and the diagonal
-// ratio max|R_jj| / min|R_jj| (a lower bound of kappa(SA)) in *kappa_lb.
-// Requires (nc + 1) * nc / 2 floats of shared memory.
-__device__ __forceinline__ int tri_off(int i, int nc) { return i * nc - (i * (i - 1)) / 2; }  // row i, col i
+// ---- blocked Cholesky + inverse on many SMs (LSQR preconditioner) --------
+//
+// W (float32, nc x nc, row-major) starts as the Gram matrix; after the panel
+// loop its upper triangle holds R (G = R^T R) and its column d holds
+// c = R^-T SA^T Sb.  Panels of 32 columns: one CTA factors the diagonal block
+// and solves the panel's rows to the right, then one CTA per 32 x 32 tile of
+// the trailing upper triangle subtracts the rank-32 update.
 
-__global__ void __launch_bounds__(1024) k_chol_inv_f32(const double* __restrict__ Gm, int d, int nc,
-                                                      double* __restrict__ M, float* __restrict__ M32T,
-                                                      double* __restrict__ c, float* __restrict__ kappa_lb,
-                                                      unsigned* bad) {
-    extern __shared__ float T[];  // packed upper triangle: T[tri_off(i) + (k - i)] = G[i][k], k >= i
-    __shared__ float rowk[1025];
+constexpr int kCholB = 32;
+
+__global__ void k_gram_to_f32(const double* __restrict__ Gm, int64_t cnt, float* __restrict__ W) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < cnt) W[q] = (float)Gm[q];
+}
+
+__global__ void __launch_bounds__(512) k_chol_panel(float* __restrict__ W, int d, int nc, int p0,
+                                                    unsigned* bad) {
+    __shared__ float D[kCholB][kCholB + 1];
     __shared__ int fail;
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int i = 0; i < nc; ++i)
-        for (int k = i + tid; k < nc; k += nt) T[tri_off(i, nc) + (k - i)] = (float)Gm[(int64_t)i * nc + k];
+    const int pb = min(kCholB, d - p0);
+    for (int q = tid; q < kCholB * kCholB; q += nt) {
+        const int i = q / kCholB, j = q % kCholB;
+        D[i][j] = (i < pb && j < pb) ? W[(int64_t)(p0 + i) * nc + p0 + j] : 0.f;
+    }
     if (tid == 0) fail = 0;
     __syncthreads();
-    // Cholesky, row j of R overwrites row j of T
-    for (int j = 0; j < d; ++j) {
-        const int oj = tri_off(j, nc);
-        const float piv = T[oj];
-        if (!(piv > 0.f)) {
-            if (tid == 0) {
+    for (int j = 0; j < pb; ++j) {
+        if (tid == 0) {
+            const float piv = D[j][j];
+            if (!(piv > 0.f)) {
                 fail = 1;
                 atomicExch(bad, 1u);
+            } else {
+                D[j][j] = sqrtf(piv);
             }
-            break;
-        }
-        const float inv = rsqrtf(piv);
-        __syncthreads();
-        for (int k = j + tid; k < nc; k += nt) {
-            const float v = (k == j) ? piv * inv : T[oj + (k - j)] * inv;
-            T[oj + (k - j)] = v;
-            rowk[k] = v;
         }
         __syncthreads();
-        // T[i][k] -= R[j][i] R[j][k] for j < i <= k < nc, i < d
-        const int rem = d - j - 1;
-        for (int i = j + 1 + tid / 32; i < d; i += nt / 32) {
-            const float rji = rowk[i];
-            float* Ti = T + tri_off(i, nc) - i;
-            for (int k = i + (tid & 31); k < nc; k += 32) Ti[k] -= rji * rowk[k];
+        if (fail) return;
+        const float r = D[j][j];
+        if (tid > j && tid < pb) D[j][tid] /= r;
+        __syncthreads();
+        for (int q = tid; q < pb * pb; q += nt) {
+            const int i = q / pb, k = q % pb;
+            if (i > j && k >= i) D[i][k] -= D[j][i] * D[j][k];
         }
-        (void)rem;
         __syncthreads();
     }
-    __syncthreads();
-    if (fail) return;
-    if (tid == 0) {
-        float mx = 0.f, mn = 3.4e38f;
-        for (int j = 0; j < d; ++j) {
-            const float v = fabsf(T[tri_off(j, nc)]);
-            mx = fmaxf(mx, v);
-            mn = fminf(mn, v);
+    for (int q = tid; q < pb * pb; q += nt) {
+        const int i = q / pb, k = q % pb;
+        if (k >= i) W[(int64_t)(p0 + i) * nc + p0 + k] = D[i][k];
+    }
+    // rows p0..p0+pb-1 of R to the right of the block: R_pp^T X = W[p0.., k]
+    for (int k = p0 + pb + tid; k < nc; k += nt) {
+        float x[kCholB];
+#pragma unroll
+        for (int i = 0; i < kCholB; ++i) {
+            if (i < pb) {
+                float sacc = W[(int64_t)(p0 + i) * nc + k];
+#pragma unroll
+                for (int q = 0; q < kCholB; ++q)
+                    if (q < i) sacc -= D[q][i] * x[q];
+                x[i] = sacc / D[i][i];
+                W[(int64_t)(p0 + i) * nc + k] = x[i];
+            }
         }
+    }
+}
+
+// W[i][k] -= sum_q R[p0+q][i] R[p0+q][k] over the trailing block (i < d, k >= i).
+__global__ void __launch_bounds__(256) k_chol_update(float* __restrict__ W, int d, int nc, int p0) {
+    __shared__ float Ri[kCholB][kCholB + 1];
+    __shared__ float Rk[kCholB][kCholB + 1];
+    const int s0 = p0 + kCholB;
+    const int ntk = (nc - s0 + kCholB - 1) / kCholB;
+    int t = blockIdx.x, ti = 0;
+    while (t >= ntk - ti) {
+        t -= ntk - ti;
+        ++ti;
+    }
+    const int tk = ti + t;
+    const int i0 = s0 + kCholB * ti, k0 = s0 + kCholB * tk;
+    for (int q = threadIdx.x; q < kCholB * kCholB; q += blockDim.x) {
+        const int r = q / kCholB, c = q % kCholB;
+        const float* row = W + (int64_t)(p0 + r) * nc;
+        Ri[r][c] = (i0 + c < d) ? row[i0 + c] : 0.f;
+        Rk[r][c] = (k0 + c < nc) ? row[k0 + c] : 0.f;
+    }
+    __syncthreads();
+    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = ty * 4 + a;
+        const int i = i0 + r, k = k0 + tx;
+        if (i < d && k < nc && k >= i) {
+            float acc = 0.f;
+#pragma unroll 8
+            for (int q = 0; q < kCholB; ++q) acc = fmaf(Ri[q][r], Rk[q][tx], acc);
+            W[(int64_t)i * nc + k] -= acc;
+        }
+    }
+}
+
+// diagonal ratio (lower bound of kappa) and c = W[0:d, d] in float64
+__global__ void k_chol_finish(const float* __restrict__ W, int d, int nc, double* __restrict__ c,
+                              float* __restrict__ kappa_lb) {
+    __shared__ float smx[32], smn[32];
+    float mx = 0.f, mn = 3.4e38f;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const float v = fabsf(W[(int64_t)j * nc + j]);
+        mx = fmaxf(mx, v);
+        mn = fminf(mn, v);
+        if (c && nc > d) c[j] = (double)W[(int64_t)j * nc + d];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+        mn = fminf(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        smx[threadIdx.x >> 5] = mx;
+        smn[threadIdx.x >> 5] = mn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            mx = fmaxf(mx, smx[w]);
+            mn = fminf(mn, smn[w]);
+        }
+        mx = fmaxf(mx, smx[0]);
+        mn = fminf(mn, smn[0]);
         *kappa_lb = mn > 0.f ? mx / mn : 3.4e38f;
     }
-    if (c && nc > d)
-        for (int i = tid; i < d; i += nt) c[i] = (double)T[tri_off(i, nc) + (d - i)];
-    // Gauss-Jordan on [R | I] from the last row up: row k of M is
-    // e_k / R_kk - sum_{j>k} (R_kj / R_kk) M_j; rows are finished bottom-up.
-    // In place: entry (i, j), j > i, holds M_ij once row i is finished; the
-    // entries (i, j) with i < k <= j accumulate -sum R_ik M_kj as rows k finish.
-    // Implemented as: for k = d-1..0: M_k = (e_k - acc_k) / R_kk, where acc_k
-    // lives in row k; then acc_i += R_ik M_k for i < k.
-    __shared__ float colk[1025];
-    for (int k = d - 1; k >= 0; --k) {
+}
+
+// M = R^-1 (float32 arithmetic, R = upper triangle of W), one warp per column:
+// x_i = (delta_ij - sum_{i<k<=j} R_ik x_k) / R_ii for i = j .. 0, R rows read
+// from a shared-memory copy of the packed triangle when it fits (PACKED).
+template <bool PACKED>
+__global__ void __launch_bounds__(256) k_tri_inv_f32(const float* __restrict__ W, int d, int nc,
+                                                    double* __restrict__ M, float* __restrict__ M32T) {
+    extern __shared__ float sh[];
+    float* xs = sh;                                   // [8][1024]
+    float* T = sh + 8 * 1024;                         // packed triangle (PACKED)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (PACKED) {
+        for (int i = 0; i < d; ++i)
+            for (int k = i + threadIdx.x; k < d; k += blockDim.x)
+                T[i * d - (i * (i - 1)) / 2 + (k - i)] = W[(int64_t)i * nc + k];
         __syncthreads();
-        const int ok = tri_off(k, nc);
-        const float rkk = T[ok];
-        // finish row k: M_kk = 1 / R_kk, M_kj = -acc_kj / R_kk for j > k
-        // (acc_kj for j > k was accumulated into T[k][j] after R_kj was saved)
-        for (int i = tid; i < k; i += nt) colk[i] = T[tri_off(i, nc) + (k - i)];  // R_ik, i < k
-        __syncthreads();
-        const float inv = 1.0f / rkk;
-        for (int j = k + tid; j < d; j += nt) {
-            const float v = (j == k) ? inv : -T[ok + (j - k)] * inv;
-            T[ok + (j - k)] = v;
-            rowk[j] = v;
-        }
-        __syncthreads();
-        // acc_ij += R_ik M_kj for i < k, j >= k  (entry (i, k) becomes acc_ik
-        // = R_ik M_kk, entries (i, j > k) accumulate)
-        for (int i = tid / 32; i < k; i += nt / 32) {
-            const float rik = colk[i];
-            float* Ti = T + tri_off(i, nc) - i;
-            for (int j = k + (tid & 31); j < d; j += 32) Ti[j] = (j == k ? 0.f : Ti[j]) + rik * rowk[j];
-        }
     }
-    __syncthreads();
-    for (int64_t q = tid; q < (int64_t)d * d; q += nt) {
-        const int i = (int)(q / d), j = (int)(q % d);
-        const float v = (j < i) ? 0.f : T[tri_off(i, nc) + (j - i)];
-        M[q] = (double)v;
-        M32T[(int64_t)j * d + i] = v;
+    const int col = blockIdx.x * 8 + warp;
+    if (col >= d) return;
+    float* x = xs + warp * 1024;
+    for (int i = lane; i < d; i += 32) x[i] = 0.f;
+    __syncwarp();
+    for (int i = col; i >= 0; --i) {
+        float part = 0.f;
+        if (PACKED) {
+            const float* Ri = T + i * d - (i * (i - 1)) / 2 - i;
+            for (int k = i + 1 + lane; k <= col; k += 32) part = fmaf(Ri[k], x[k], part);
+        } else {
+            const float* Ri = W + (int64_t)i * nc;
+            for (int k = i + 1 + lane; k <= col; k += 32) part = fmaf(Ri[k], x[k], part);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+        if (lane == 0) {
+            const float rii = PACKED ? T[i * d - (i * (i - 1)) / 2] : W[(int64_t)i * nc + i];
+            x[i] = ((i == col ? 1.f : 0.f) - part) / rii;
+        }
+        __syncwarp();
+    }
+    for (int i = lane; i < d; i += 32) {
+        const float v = (i <= col) ? x[i] : 0.f;
+        M[(int64_t)i * d + col] = (double)v;
+        M32T[(int64_t)col * d + i] = v;
     }
 }
 
@@ -654,17 +730,18 @@ int gram_cholesky(const float* SA, int64_t m, int d, const float* Sb, double* R,
 int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double* M, float* M32T, double* c,
                       float* kappa_lb_host, cudaStream_t stream) {
     const int nc = d + (Sb ? 1 : 0);
-    const size_t tsmem = sizeof(float) * ((size_t)nc * (nc + 1) / 2);
-    if (tsmem > 220 * 1024) return CW_ERR_SHAPE;
+    if (d > 1024) return CW_ERR_SHAPE;
     const int ntile = (nc + kGramTile - 1) / kGramTile;
     const int nchunk = (int)((m + kGramRowsPerChunk - 1) / kGramRowsPerChunk);
     Scratch ws(stream);
     const size_t oP = ws.reserve(sizeof(double) * (size_t)nchunk * nc * nc);
     const size_t oG = ws.reserve(sizeof(double) * (size_t)nc * nc);
+    const size_t oW = ws.reserve(sizeof(float) * (size_t)nc * nc);
     const size_t oF = ws.reserve(sizeof(unsigned) * 2 + sizeof(float) * 2);
     CW_CUDA_TRY(ws.alloc());
     double* part = ws.at<double>(oP);
     double* Gm = ws.at<double>(oG);
+    float* W = ws.at<float>(oW);
     unsigned* bad = ws.at<unsigned>(oF);
     float* klb = reinterpret_cast<float*>(bad + 2);
     CW_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned) * 2 + sizeof(float) * 2, stream));
@@ -678,10 +755,38 @@ int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double
         CW_PROF("k_gram_reduce", stream);
         k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(part, nchunk, nc, Gm);
     }
-    CW_CUDA_TRY(cudaFuncSetAttribute(k_chol_inv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
     {
-        CW_PROF("k_chol_inv_f32", stream);
-        k_chol_inv_f32<<<1, 1024, tsmem, stream>>>(Gm, d, nc, M, M32T, c, klb, bad);
+        CW_PROF("k_gram_to_f32", stream);
+        k_gram_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(Gm, tot, W);
+    }
+    for (int p0 = 0; p0 < d; p0 += kCholB) {
+        {
+            CW_PROF("k_chol_panel", stream);
+            k_chol_panel<<<1, 512, 0, stream>>>(W, d, nc, p0, bad);
+        }
+        const int s0 = p0 + kCholB;
+        if (s0 < d) {
+            const int nti = (d - s0 + kCholB - 1) / kCholB, ntk = (nc - s0 + kCholB - 1) / kCholB;
+            int tiles = 0;
+            for (int ti = 0; ti < nti; ++ti) tiles += ntk - ti;
+            CW_PROF("k_chol_update", stream);
+            k_chol_update<<<tiles, 256, 0, stream>>>(W, d, nc, p0);
+        }
+    }
+    {
+        CW_PROF("k_chol_finish", stream);
+        k_chol_finish<<<1, 1024, 0, stream>>>(W, d, nc, c, klb);
+    }
+    const size_t packed = sizeof(float) * ((size_t)d * (d + 1) / 2);
+    const size_t xs = sizeof(float) * 8 * 1024;
+    if (xs + packed <= 200 * 1024) {
+        CW_CUDA_TRY(cudaFuncSetAttribute(k_tri_inv_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(xs + packed)));
+        CW_PROF("k_tri_inv_f32", stream);
+        k_tri_inv_f32<true><<<(d + 7) / 8, 256, xs + packed, stream>>>(W, d, nc, M, M32T);
+    } else {
+        CW_PROF("k_tri_inv_f32", stream);
+        k_tri_inv_f32<false><<<(d + 7) / 8, 256, xs, stream>>>(W, d, nc, M, M32T);
     }
     CW_LAUNCH_CHECK();
     unsigned h[2] = {0, 0};
