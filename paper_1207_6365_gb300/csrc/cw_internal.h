@@ -27,9 +27,6 @@ int validate_common(int64_t n, int64_t d, int64_t m);
 // replaces SA when given.
 int qr64(const float* SA, int64_t m, int d, const float* Sb, double* R, double* c, cudaStream_t stream,
          const double* SA64 = nullptr);
-// Cholesky factor of the Gram matrix of SA (fast preconditioner); synchronises.
-int gram_cholesky(const float* SA, int64_t m, int d, const float* Sb, double* R, double* c,
-                  cudaStream_t stream);
 int trsv_upper(const double* R, int d, const double* rhs, double* x, cudaStream_t stream);
 int trsm_upper(const double* R, int d, const double* B, int k, double* X, cudaStream_t stream);
 int tri_inverse(const double* R, int d, double* M, cudaStream_t stream);

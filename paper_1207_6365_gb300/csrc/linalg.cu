@@ -257,130 +257,131 @@ __global__ void k_trsm_upper(const double* __restrict__ R, int d, const double* 
     for (int i = threadIdx.x; i < d; i += blockDim.x) X[(int64_t)i * k + col] = sx[i];
 }
 
-// ---------------------------------------------------------------- Gram matrix (fast R)
+// ---- Gram matrix SA^T SA: 128 x 128 output tiles, 8 x 8 per thread ----------
+//
+// CTA (ti <= tj, chunk) accumulates sum over its rows of SA[r, ti*128 + a] *
+// SA[r, tj*128 + b] in float32 and writes a float64 partial tile; partials are
+// added over chunks in a fixed order.  The diagonal tiles also accumulate
+// SA^T Sb for their columns, tile (0, 0) also Sb^T Sb.
 
-constexpr int kGramTile = 64;
-constexpr int kGramRowsPerChunk = 2048;
+constexpr int kGT = 128;         // tile edge
+constexpr int kGK = 16;          // rows per shared-memory stage
 
-// Partial Gram of the columns [ti*64, ti*64+64) x [tj*64, tj*64+64) of
-// X = [SA | Sb] over one chunk of rows; float32 products and sums within the
-// chunk, stored as float64 partials [chunk][nc][nc].
-__global__ void __launch_bounds__(256) k_gram_partial(const float* __restrict__ SA, const float* __restrict__ Sb,
-                                                     int64_t m, int d, int nc, int ntile,
-                                                     double* __restrict__ part) {
-    __shared__ float Xi[32][kGramTile + 1];
-    __shared__ float Xj[32][kGramTile + 1];
-    // upper-triangular tile index -> (ti, tj)
+__global__ void __launch_bounds__(256) k_gram_tile(const float* __restrict__ SA, const float* __restrict__ Sb,
+                                                   int64_t m, int d, int ntile, int rows, double* __restrict__ part,
+                                                   double* __restrict__ vpart) {
+    __shared__ __align__(16) float As[kGK][kGT + 4];
+    __shared__ __align__(16) float Bs[kGK][kGT + 4];
+    __shared__ float Ss[kGK];
     int t = blockIdx.x, ti = 0;
     while (t >= ntile - ti) {
         t -= ntile - ti;
         ++ti;
     }
     const int tj = ti + t;
-    const int chunk = blockIdx.y;
-    const int64_t rb = (int64_t)chunk * kGramRowsPerChunk;
-    const int64_t re = (rb + kGramRowsPerChunk < m) ? rb + kGramRowsPerChunk : m;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 4 x 4 outputs each
-    float acc[4][4] = {};
-    for (int64_t r = rb; r < re; r += 32) {
-        for (int q = threadIdx.x; q < 32 * kGramTile; q += blockDim.x) {
-            const int rr = q / kGramTile, cc = q % kGramTile;
-            const int64_t row = r + rr;
-            const int ci = ti * kGramTile + cc, cj = tj * kGramTile + cc;
-            float vi = 0.f, vj = 0.f;
-            if (row < re) {
-                vi = ci < d ? SA[row * d + ci] : (ci == d && Sb ? Sb[row] : 0.f);
-                vj = cj < d ? SA[row * d + cj] : (cj == d && Sb ? Sb[row] : 0.f);
+    const int64_t r0 = (int64_t)blockIdx.y * rows;
+    const int64_t r1 = (r0 + rows < m) ? r0 + rows : m;
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(SA) & 15) == 0);
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    // diagonal tiles also form SA^T Sb for their columns (lanes with tx == 0)
+    // and tile (0, 0) forms Sb^T Sb (thread 0)
+    const bool vrow = Sb && ti == tj && tx == 0;
+    float vacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float sbb = 0.f;
+    const int ci0 = ti * kGT, cj0 = tj * kGT;
+    for (int64_t rb = r0; rb < r1; rb += kGK) {
+        if (Sb && ti == tj && threadIdx.x < kGK) Ss[threadIdx.x] = (rb + threadIdx.x < r1) ? Sb[rb + threadIdx.x] : 0.f;
+        // stage: 16 rows x 128 columns of each operand; thread loads 2 x 4 floats per operand
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = threadIdx.x + 256 * h;   // 0..511 -> (row kk, column quad cq)
+            const int kk = q >> 5, cq = (q & 31) * 4;
+            const int64_t r = rb + kk;
+            float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < r1) {
+                const float* row = SA + r * d;
+                if (vec && ci0 + cq + 3 < d) {
+                    va = *reinterpret_cast<const float4*>(row + ci0 + cq);
+                } else {
+                    va.x = ci0 + cq < d ? row[ci0 + cq] : 0.f;
+                    va.y = ci0 + cq + 1 < d ? row[ci0 + cq + 1] : 0.f;
+                    va.z = ci0 + cq + 2 < d ? row[ci0 + cq + 2] : 0.f;
+                    va.w = ci0 + cq + 3 < d ? row[ci0 + cq + 3] : 0.f;
+                }
+                if (vec && cj0 + cq + 3 < d) {
+                    vb = *reinterpret_cast<const float4*>(row + cj0 + cq);
+                } else {
+                    vb.x = cj0 + cq < d ? row[cj0 + cq] : 0.f;
+                    vb.y = cj0 + cq + 1 < d ? row[cj0 + cq + 1] : 0.f;
+                    vb.z = cj0 + cq + 2 < d ? row[cj0 + cq + 2] : 0.f;
+                    vb.w = cj0 + cq + 3 < d ? row[cj0 + cq + 3] : 0.f;
+                }
             }
-            Xi[rr][cc] = vi;
-            Xj[rr][cc] = vj;
+            *reinterpret_cast<float4*>(&As[kk][cq]) = va;
+            *reinterpret_cast<float4*>(&Bs[kk][cq]) = vb;
         }
         __syncthreads();
-#pragma unroll 4
-        for (int rr = 0; rr < 32; ++rr) {
-            float a[4], b[4];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                a[p] = Xi[rr][ty * 4 + p];
-                b[p] = Xj[rr][tx * 4 + p];
+        for (int kk = 0; kk < kGK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+            if (vrow) {
+                const float sb = Ss[kk];
+#pragma unroll
+                for (int a = 0; a < 8; ++a) vacc[a] = fmaf(av[a], sb, vacc[a]);
+                sbb = fmaf(sb, sb, sbb);
             }
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
         }
         __syncthreads();
     }
-    double* out = part + (size_t)chunk * nc * nc;
+    double* out = part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kGT * kGT;
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int ci = ti * kGramTile + ty * 4 + p, cj = tj * kGramTile + tx * 4 + q;
-            if (ci < nc && cj < nc && ci <= cj) out[(size_t)ci * nc + cj] = (double)acc[p][q];
-        }
+        for (int b = 0; b < 8; ++b) out[(ty * 8 + a) * kGT + tx * 8 + b] = (double)acc[a][b];
+    if (vrow) {
+        double* vo = vpart + (size_t)blockIdx.y * (d + 1);
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+            if (ci0 + ty * 8 + a < d) vo[ci0 + ty * 8 + a] = (double)vacc[a];
+        if (ti == 0 && ty == 0) vo[d] = (double)sbb;
+    }
 }
 
-__global__ void k_gram_reduce(const double* __restrict__ part, int nchunk, int nc, double* __restrict__ Gm) {
+// Gm (nc x nc, full, float64) from the tile and vector partials, fixed order.
+__global__ void k_gram_reduce2(const double* __restrict__ tpart, const double* __restrict__ vpart, int nchunk,
+                               int ntile, int d, int nc, double* __restrict__ Gm) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)nc * nc) return;
     const int ci = (int)(idx / nc), cj = (int)(idx % nc);
     if (ci > cj) return;
     double s = 0.0;
-    for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * nc * nc + idx];
+    if (cj < d) {
+        const int ti = ci / kGT, tj = cj / kGT;
+        int tl = 0;
+        for (int q = 0; q < ti; ++q) tl += ntile - q;
+        tl += tj - ti;
+        const int ntl = ntile * (ntile + 1) / 2;
+        const int off = (ci % kGT) * kGT + (cj % kGT);
+        for (int c = 0; c < nchunk; ++c) s += tpart[((size_t)c * ntl + tl) * kGT * kGT + off];
+    } else {
+        for (int c = 0; c < nchunk; ++c) s += vpart[(size_t)c * (d + 1) + ci];
+    }
     Gm[(int64_t)ci * nc + cj] = s;
     Gm[(int64_t)cj * nc + ci] = s;
-}
-
-// Upper Cholesky G = R^T R of the leading d x d block of the float64 Gram
-// matrix, computed in float32 by one CTA (right-looking, 32 x 32 thread grid
-// over the trailing block).  The carried column d becomes c = R^-T SA^T Sb.
-// float32 is enough here: this R only preconditions LSQR (any R with
-// SA R^-1 near-orthonormal works), and callers fall back to the float64
-// Householder R when the diagonal signals a large condition number.
-// W: float32 working copy (nc x nc, row-major).  Flags a non-positive pivot.
-__global__ void __launch_bounds__(1024) k_cholesky_f32(const double* __restrict__ Gm, float* __restrict__ W, int d,
-                                                      int nc, double* __restrict__ R, double* __restrict__ c,
-                                                      unsigned* bad) {
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int64_t q = threadIdx.x; q < (int64_t)nc * nc; q += blockDim.x) W[q] = (float)Gm[q];
-    __syncthreads();
-    __shared__ float rowj[1025];
-    __shared__ int fail;
-    if (threadIdx.x == 0) fail = 0;
-    for (int j = 0; j < d; ++j) {
-        __syncthreads();
-        const float piv = W[(int64_t)j * nc + j];
-        if (!(piv > 0.f)) {
-            if (threadIdx.x == 0) {
-                fail = 1;
-                atomicExch(bad, 1u);
-            }
-            break;
-        }
-        const float rjj = sqrtf(piv);
-        const float inv = 1.0f / rjj;
-        for (int k = j + threadIdx.x; k < nc; k += blockDim.x) {
-            const float v = (k == j) ? rjj : W[(int64_t)j * nc + k] * inv;
-            W[(int64_t)j * nc + k] = v;
-            rowj[k] = v;
-        }
-        __syncthreads();
-        // W[i, k] -= R[j, i] * R[j, k] for j < i <= k
-        for (int i = j + 1 + ty; i < d; i += 32) {
-            const float rji = rowj[i];
-            float* wi = W + (int64_t)i * nc;
-            for (int k = i + tx; k < nc; k += 32) wi[k] -= rji * rowj[k];
-        }
-    }
-    __syncthreads();
-    if (fail) return;
-    for (int64_t q = threadIdx.x; q < (int64_t)d * d; q += blockDim.x) {
-        const int i = (int)(q / d), k = (int)(q % d);
-        R[q] = (k < i) ? 0.0 : (double)W[(int64_t)i * nc + k];
-    }
-    if (c && nc > d)
-        for (int i = threadIdx.x; i < d; i += blockDim.x) c[i] = (double)W[(int64_t)i * nc + d];
 }
 
 // ---- blocked Cholesky + inverse on many SMs (LSQR preconditioner) --------
@@ -398,8 +399,36 @@ __global__ void k_gram_to_f32(const double* __restrict__ Gm, int64_t cnt, float*
     if (q < cnt) W[q] = (float)Gm[q];
 }
 
+// Cholesky of a pb x pb (pb <= 32) diagonal block held by one warp, lane k
+// holding column k in registers (entries 0..k): right-looking, the pivot and
+// row j of R reach the other lanes by shuffles.  Returns false, the same on
+// every lane, when a pivot is not positive.
+__device__ __forceinline__ bool chol_block32(float (&col)[kCholB], int pb) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < kCholB; ++j) {
+        const float piv = __shfl_sync(0xFFFFFFFFu, col[j], j);
+        if (j < pb) {
+            if (!(piv > 0.f)) ok = false;
+            const float r = sqrtf(piv);
+            if (lane == j) col[j] = r;
+            else if (lane > j) col[j] = col[j] / r;
+        }
+        const float rjk = col[j];
+#pragma unroll
+        for (int i = 0; i < kCholB; ++i) {   // constant trip count keeps col[] in registers
+            if (i > j) {
+                const float rji = __shfl_sync(0xFFFFFFFFu, col[j], i);
+                if (j < pb && lane >= i) col[i] = fmaf(-rji, rjk, col[i]);
+            }
+        }
+    }
+    return ok;
+}
+
 __global__ void __launch_bounds__(512) k_chol_panel(float* __restrict__ W, int d, int nc, int p0,
-                                                    unsigned* bad) {
+                                                   unsigned* bad) {
     __shared__ float D[kCholB][kCholB + 1];
     __shared__ int fail;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -410,27 +439,21 @@ __global__ void __launch_bounds__(512) k_chol_panel(float* __restrict__ W, int d
     }
     if (tid == 0) fail = 0;
     __syncthreads();
-    for (int j = 0; j < pb; ++j) {
-        if (tid == 0) {
-            const float piv = D[j][j];
-            if (!(piv > 0.f)) {
-                fail = 1;
-                atomicExch(bad, 1u);
-            } else {
-                D[j][j] = sqrtf(piv);
-            }
+    if (tid < 32) {
+        float col[kCholB];
+#pragma unroll
+        for (int q = 0; q < kCholB; ++q) col[q] = D[q][tid];
+        const bool ok = chol_block32(col, pb);
+        if (!ok && tid == 0) {
+            fail = 1;
+            atomicExch(bad, 1u);
         }
-        __syncthreads();
-        if (fail) return;
-        const float r = D[j][j];
-        if (tid > j && tid < pb) D[j][tid] /= r;
-        __syncthreads();
-        for (int q = tid; q < pb * pb; q += nt) {
-            const int i = q / pb, k = q % pb;
-            if (i > j && k >= i) D[i][k] -= D[j][i] * D[j][k];
-        }
-        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kCholB; ++q)
+            if (q <= tid) D[q][tid] = col[q];
     }
+    __syncthreads();
+    if (fail) return;
     for (int q = tid; q < pb * pb; q += nt) {
         const int i = q / pb, k = q % pb;
         if (k >= i) W[(int64_t)(p0 + i) * nc + p0 + k] = D[i][k];
@@ -439,16 +462,20 @@ __global__ void __launch_bounds__(512) k_chol_panel(float* __restrict__ W, int d
     for (int k = p0 + pb + tid; k < nc; k += nt) {
         float x[kCholB];
 #pragma unroll
+        for (int i = 0; i < kCholB; ++i) x[i] = (i < pb) ? W[(int64_t)(p0 + i) * nc + k] : 0.f;
+#pragma unroll
         for (int i = 0; i < kCholB; ++i) {
             if (i < pb) {
-                float sacc = W[(int64_t)(p0 + i) * nc + k];
+                float sacc = x[i];
 #pragma unroll
                 for (int q = 0; q < kCholB; ++q)
                     if (q < i) sacc -= D[q][i] * x[q];
                 x[i] = sacc / D[i][i];
-                W[(int64_t)(p0 + i) * nc + k] = x[i];
             }
         }
+#pragma unroll
+        for (int i = 0; i < kCholB; ++i)
+            if (i < pb) W[(int64_t)(p0 + i) * nc + k] = x[i];
     }
 }
 
@@ -483,6 +510,155 @@ __global__ void __launch_bounds__(256) k_chol_update(float* __restrict__ W, int 
             for (int q = 0; q < kCholB; ++q) acc = fmaf(Ri[q][r], Rk[q][tx], acc);
             W[(int64_t)i * nc + k] -= acc;
         }
+    }
+}
+
+// The whole factorization in one CTA when the packed upper triangle of W fits
+// in shared memory: for each panel of 32 columns, warp 0 factors the diagonal
+// block, one thread per column to the right solves the panel's rows, and all
+// warps subtract the rank-32 update from the trailing triangle (warp = 4 rows
+// x 128 columns, lane = 4 columns 32 apart).  W is read once and written once.
+// Packed row i holds columns i..nc-1 at P[i*nc - i*(i+1)/2 + k].  The three
+// phases are separate non-inlined functions so that each one's unrolled
+// register arrays get the whole register budget.
+__device__ __forceinline__ int chol_off(int i, int nc) { return i * nc - (i * (i + 1)) / 2; }
+
+// warp 0: diagonal block of panel p0 (pb columns) into Dg and back into P;
+// returns false on a non-positive pivot (the same on every lane)
+__device__ __noinline__ bool chol_small_factor(float* P, float (*Dg)[kCholB + 1], int nc, int p0, int pb) {
+    const int lane = threadIdx.x & 31;
+    float col[kCholB];
+#pragma unroll
+    for (int q = 0; q < kCholB; ++q) col[q] = (q <= lane && lane < pb) ? P[chol_off(p0 + q, nc) + p0 + lane] : 0.f;
+    const bool ok = chol_block32(col, pb);
+#pragma unroll
+    for (int q = 0; q < kCholB; ++q) {
+        if (q <= lane && lane < pb) P[chol_off(p0 + q, nc) + p0 + lane] = col[q];
+        Dg[q][lane] = col[q];
+    }
+    return ok;
+}
+
+// column k to the right of the block: R_pp^T x = P[p0.., k], rows in two halves of 16
+__device__ __noinline__ void chol_small_panel(float* P, const float (*Dg)[kCholB + 1], int nc, int p0, int pb,
+                                              int k) {
+    float x[16], y[16];
+    int o = chol_off(p0, nc) + k;   // P index of (p0 + i, k), advanced row by row
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        x[i] = (i < pb) ? P[o] : 0.f;
+        o += nc - (p0 + i) - 1;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        x[q] = (q < pb) ? x[q] / Dg[q][q] : 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (i > q) x[i] = fmaf(-Dg[q][i], x[q], x[i]);
+    }
+    const int o16 = o;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        y[i] = (16 + i < pb) ? P[o] : 0.f;
+        o += nc - (p0 + 16 + i) - 1;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) y[i] = fmaf(-Dg[q][16 + i], x[q], y[i]);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        y[q] = (16 + q < pb) ? y[q] / Dg[16 + q][16 + q] : 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (i > q) y[i] = fmaf(-Dg[16 + q][16 + i], y[q], y[i]);
+    }
+    o = chol_off(p0, nc) + k;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if (i < pb) P[o] = x[i];
+        o += nc - (p0 + i) - 1;
+    }
+    o = o16;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if (16 + i < pb) P[o] = y[i];
+        o += nc - (p0 + 16 + i) - 1;
+    }
+}
+
+// P[i][k] -= sum_q R[p0+q][i] R[p0+q][k] for i in [i0, i0 + 4) (< d), the lane's
+// four columns kb + lane + 32c (>= i, < nc)
+__device__ __noinline__ void chol_small_update(float* P, int d, int nc, int p0, int pb, int i0, int kb) {
+    const int lane = threadIdx.x & 31;
+    float acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+    int o = chol_off(p0, nc);
+    for (int q = 0; q < pb; ++q) {
+        const float* Rq = P + o;
+        float a[4], b[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = (i0 + r < d) ? Rq[i0 + r] : 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int k = kb + lane + 32 * c;
+            b[c] = (k < nc) ? Rq[k] : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+        o += nc - (p0 + q) - 1;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = i0 + r, k = kb + lane + 32 * c;
+            if (i < d && k < nc && k >= i) P[chol_off(i, nc) + k] -= acc[r][c];
+        }
+}
+
+__global__ void __launch_bounds__(512) k_chol_small(float* __restrict__ W, int d, int nc, unsigned* bad) {
+    extern __shared__ float P[];
+    __shared__ float Dg[kCholB][kCholB + 1];   // R of the current diagonal block
+    __shared__ int fail;
+    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, nw = nt >> 5;
+    for (int q = tid; q < nc * nc; q += nt) {
+        const int i = q / nc, k = q - i * nc;
+        if (k >= i) cp_async4(P + chol_off(i, nc) + k, W + q);
+    }
+    cp_async_wait_all();
+    if (tid == 0) fail = 0;
+    __syncthreads();
+    for (int p0 = 0; p0 < d; p0 += kCholB) {
+        const int pb = min(kCholB, d - p0);
+        if (warp == 0) {
+            const bool ok = chol_small_factor(P, Dg, nc, p0, pb);
+            if (!ok && tid == 0) {
+                fail = 1;
+                atomicExch(bad, 1u);
+            }
+        }
+        __syncthreads();
+        if (fail) return;
+        const int s0 = p0 + pb;
+        for (int k = s0 + tid; k < nc; k += nt) chol_small_panel(P, Dg, nc, p0, pb, k);
+        __syncthreads();
+        const int nbi = (d - s0 + 3) / 4, ng = (nc - s0 + 127) / 128;
+        for (int wt = warp; wt < nbi * ng; wt += nw) {
+            const int bi = wt / ng, g = wt - bi * ng;
+            const int i0 = s0 + 4 * bi, kb = s0 + 128 * g;
+            if (kb + 127 >= i0) chol_small_update(P, d, nc, p0, pb, i0, kb);   // else below the diagonal
+        }
+        __syncthreads();
+    }
+    for (int q = tid; q < nc * nc; q += nt) {
+        const int i = q / nc, k = q - i * nc;
+        if (k >= i) W[q] = P[chol_off(i, nc) + k];
     }
 }
 
@@ -528,9 +704,11 @@ __global__ void __launch_bounds__(256) k_tri_inv_f32(const float* __restrict__ W
     float* T = sh + 8 * 1024;                         // packed triangle (PACKED)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (PACKED) {
-        for (int i = 0; i < d; ++i)
-            for (int k = i + threadIdx.x; k < d; k += blockDim.x)
-                T[i * d - (i * (i - 1)) / 2 + (k - i)] = W[(int64_t)i * nc + k];
+        for (int q = threadIdx.x; q < d * d; q += blockDim.x) {
+            const int i = q / d, k = q - i * d;
+            if (k >= i) cp_async4(T + i * d - (i * (i - 1)) / 2 + (k - i), W + (int64_t)i * nc + k);
+        }
+        cp_async_wait_all();
         __syncthreads();
     }
     const int col = blockIdx.x * 8 + warp;
@@ -682,84 +860,57 @@ int qr64(const float* SA, int64_t m, int d, const float* Sb, double* R, double* 
     return CW_OK;
 }
 
-// Fast R: upper Cholesky factor of the Gram matrix of SA (float32 products,
-// float64 accumulation across row chunks), and c = R^-T SA^T Sb when Sb is
-// given.  Returns CW_ERR_RANK when a pivot is not positive.  Asynchronous
-// except for the final flag read (synchronises).
-int gram_cholesky(const float* SA, int64_t m, int d, const float* Sb, double* R, double* c, cudaStream_t stream) {
-    const int nc = d + (Sb ? 1 : 0);
-    const int ntile = (nc + kGramTile - 1) / kGramTile;
-    const int nchunk = (int)((m + kGramRowsPerChunk - 1) / kGramRowsPerChunk);
-    Scratch ws(stream);
-    const size_t oP = ws.reserve(sizeof(double) * (size_t)nchunk * nc * nc);
-    const size_t oG = ws.reserve(sizeof(double) * (size_t)nc * nc);
-    const size_t oW = ws.reserve(sizeof(float) * (size_t)nc * nc);
-    const size_t oF = ws.reserve(sizeof(unsigned) * 2);
-    CW_CUDA_TRY(ws.alloc());
-    double* part = ws.at<double>(oP);
-    double* Gm = ws.at<double>(oG);
-    unsigned* bad = ws.at<unsigned>(oF);
-    CW_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned) * 2, stream));
-    dim3 gg((unsigned)(ntile * (ntile + 1) / 2), (unsigned)nchunk);
-    {
-        CW_PROF("k_gram_partial", stream);
-        k_gram_partial<<<gg, 256, 0, stream>>>(SA, Sb, m, d, nc, ntile, part);
-    }
-    CW_LAUNCH_CHECK();
-    const int64_t tot = (int64_t)nc * nc;
-    {
-        CW_PROF("k_gram_reduce", stream);
-        k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(part, nchunk, nc, Gm);
-    }
-    CW_LAUNCH_CHECK();
-    {
-        CW_PROF("k_cholesky_f32", stream);
-        k_cholesky_f32<<<1, 1024, 0, stream>>>(Gm, ws.at<float>(oW), d, nc, R, c, bad);
-    }
-    CW_LAUNCH_CHECK();
-    unsigned h = 0;
-    CW_CUDA_TRY(cudaMemcpyAsync(&h, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
-    CW_CUDA_TRY(cudaStreamSynchronize(stream));
-    return h ? CW_ERR_RANK : CW_OK;
-}
-
-// Gram + Cholesky + inverse for the LSQR preconditioner.  M (float64 d x d),
-// M32T (float32, column-major) and c = R^-T SA^T Sb; *kappa_lb receives the
-// diagonal ratio of R.  Returns CW_ERR_RANK on a non-positive pivot and
-// CW_ERR_SHAPE when the packed triangle does not fit in shared memory.
+// Gram + Cholesky + inverse for the LSQR preconditioner.  M (float64 d x d,
+// float32 values), M32T (float32, column-major) and c = R^-T SA^T Sb; *kappa_lb
+// receives the diagonal ratio of R.  Returns CW_ERR_RANK on a non-positive
+// pivot.  Synchronises (the caller needs the ratio on the host).
 int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double* M, float* M32T, double* c,
                       float* kappa_lb_host, cudaStream_t stream) {
     const int nc = d + (Sb ? 1 : 0);
     if (d > 1024) return CW_ERR_SHAPE;
-    const int ntile = (nc + kGramTile - 1) / kGramTile;
-    const int nchunk = (int)((m + kGramRowsPerChunk - 1) / kGramRowsPerChunk);
+    const int ntile = (d + kGT - 1) / kGT;
+    const int ntl = ntile * (ntile + 1) / 2;
+    // rows per chunk: about one CTA per SM in one wave (146 registers a thread)
+    int64_t rows = (m * ntl + num_sms() - 1) / num_sms();
+    rows = ((rows + kGK - 1) / kGK) * kGK;
+    if (rows < 256) rows = 256;
+    const int nchunk = (int)((m + rows - 1) / rows);
     Scratch ws(stream);
-    const size_t oP = ws.reserve(sizeof(double) * (size_t)nchunk * nc * nc);
+    const size_t oP = ws.reserve(sizeof(double) * (size_t)nchunk * ntl * kGT * kGT);
+    const size_t oV = ws.reserve(sizeof(double) * (size_t)nchunk * (d + 1));
     const size_t oG = ws.reserve(sizeof(double) * (size_t)nc * nc);
     const size_t oW = ws.reserve(sizeof(float) * (size_t)nc * nc);
     const size_t oF = ws.reserve(sizeof(unsigned) * 2 + sizeof(float) * 2);
     CW_CUDA_TRY(ws.alloc());
     double* part = ws.at<double>(oP);
+    double* vpart = ws.at<double>(oV);
     double* Gm = ws.at<double>(oG);
     float* W = ws.at<float>(oW);
     unsigned* bad = ws.at<unsigned>(oF);
     float* klb = reinterpret_cast<float*>(bad + 2);
     CW_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned) * 2 + sizeof(float) * 2, stream));
-    dim3 gg((unsigned)(ntile * (ntile + 1) / 2), (unsigned)nchunk);
     {
-        CW_PROF("k_gram_partial", stream);
-        k_gram_partial<<<gg, 256, 0, stream>>>(SA, Sb, m, d, nc, ntile, part);
+        CW_PROF("k_gram_tile", stream);
+        k_gram_tile<<<dim3((unsigned)ntl, (unsigned)nchunk), 256, 0, stream>>>(SA, Sb, m, d, ntile, (int)rows, part,
+                                                                             vpart);
     }
     const int64_t tot = (int64_t)nc * nc;
     {
         CW_PROF("k_gram_reduce", stream);
-        k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(part, nchunk, nc, Gm);
+        k_gram_reduce2<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(part, vpart, nchunk, ntile, d, nc, Gm);
     }
     {
         CW_PROF("k_gram_to_f32", stream);
         k_gram_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(Gm, tot, W);
     }
-    for (int p0 = 0; p0 < d; p0 += kCholB) {
+    const size_t psm = sizeof(float) * ((size_t)nc * (nc + 1) / 2);
+    const bool small = psm + 1024 <= 227 * 1024;
+    if (small) {
+        CW_CUDA_TRY(cudaFuncSetAttribute(k_chol_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+        CW_PROF("k_chol_small", stream);
+        k_chol_small<<<1, 512, psm, stream>>>(W, d, nc, bad);
+    }
+    for (int p0 = 0; !small && p0 < d; p0 += kCholB) {
         {
             CW_PROF("k_chol_panel", stream);
             k_chol_panel<<<1, 512, 0, stream>>>(W, d, nc, p0, bad);

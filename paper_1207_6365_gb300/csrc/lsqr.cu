@@ -47,19 +47,6 @@ struct PassArgs {
     float coef_first;      // used when st == nullptr
 };
 
-// ---- cp.async helpers (global -> shared without passing through registers)
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
 constexpr int kPassBatch = 32;     // rows per warp batch (one per lane for row_ptr / z)
 constexpr int kPassCap = 640;      // staged nnz per batch (multiple of 4)
 constexpr int kPassStages = 2;

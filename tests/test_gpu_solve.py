@@ -126,6 +126,21 @@ def test_lsqr_ragged_rows(cw):
     assert abs(_rho(A, b, x, rn) - _rho(A, b, x_o, rn)) <= RHO_TOL
 
 
+@pytest.mark.parametrize("n,d,k,m,seed", [
+    (150000, 300, 8, 4096, 7),    # one-CTA Cholesky, last panel 12 columns wide
+    (80000, 400, 6, 8192, 8),     # packed triangle too large for one CTA: panel kernels
+    (30000, 1, 1, 64, 9),         # a single column
+    (50000, 33, 5, 512, 10)])     # two panels, the second one column wide
+def test_lsqr_shapes(cw, n, d, k, m, seed):
+    A = W.csr_uniform(n, d, k, seed=seed + 40)
+    b, _ = W.rhs(A, 0.1, seed=seed + 50)
+    x, it, test, x_o, it_o, test_o, conv_o = _lsqr_case(cw, A, b, m, seed)
+    assert conv_o and test <= 1e-6
+    assert abs(it - it_o) <= 1, (it, it_o)
+    _, rn = oracle.lstsq_exact_csr(A.row_ptr, A.col, A.val, A.d, b)
+    assert abs(_rho(A, b, x, rn) - _rho(A, b, x_o, rn)) <= RHO_TOL
+
+
 def test_lsqr_max_iter_reports_noconv(cw):
     A = W.csr_uniform(20000, 16, 4, seed=2)
     b, _ = W.rhs(A, 0.5, seed=3)
