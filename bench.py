@@ -20,6 +20,7 @@ float64 CPU oracle on a bounded row sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -78,10 +79,12 @@ TIMED_KERNELS = ("k_lsqr_pass", "k_apply_csr", "k_coarse_scatter", "k_fine_sort"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("cw", "reference"), default="cw")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rows", type=int, default=N_ROWS,
+                    help="rows of A (a smaller case of the same workload for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
@@ -137,9 +140,11 @@ def sum_over_ranks(x, world, device=None):
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples every 200 ms while running."""
+    """nvidia-smi clock / throttle samples every 100 ms while running; stop()
+    keeps the samples taken between mark_start() and mark_end() (all samples if
+    none fall inside)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -147,15 +152,27 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = os.path.join("/tmp", "cw_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader",
-                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.fh,
+                                          "-lms", "100", "-i", str(self.gpu)], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # wait (at most 5 s) for the first sample so the timed region is covered
+        t_end = time.time() + 5.0
+        while time.time() < t_end and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
+
+    def mark_start(self):
+        self.t0 = datetime.datetime.now()
+
+    def mark_end(self):
+        self.t1 = datetime.datetime.now()
 
     def stop(self):
         if self.proc is None:
@@ -166,25 +183,30 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, mx, reasons = [], [], set()
+        rows = []
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1].split()[0]))
-                mx.append(float(parts[2].split()[0]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                sm = float(parts[2].split()[0])
+                mx = float(parts[3].split()[0])
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
+            rs = {nm for nm, v in zip(names, parts[6:10]) if v.lower().startswith("active")}
+            rows.append((ts, sm, mx, rs))
         os.unlink(self.path)
-        if not sm:
+        inside = [r for r in rows if self.t0 and self.t1 and self.t0 <= r[0] <= self.t1]
+        use = inside or rows
+        if not use:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        reasons = set()
+        for r in use:
+            reasons |= r[3]
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+                "samples": len(use), "samples_in_timed_region": len(inside), "reasons": sorted(reasons)}
 
 
 # ---------------------------------------------------------------- peaks and profiles
@@ -315,7 +337,7 @@ def run_cw(args):
     dist_init(world, "nccl")
     cw.load()
 
-    A, b = make_problem("cuda", replica=rank)
+    A, b = make_problem("cuda", rows=args.rows, replica=rank)
     n, nnz = A.n, A.nnz
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -323,17 +345,18 @@ def run_cw(args):
     def step():
         return cw.cw_lsqr_precond(A, b, M, SEED, rtol=RTOL, max_iter=100)
 
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         x, it, test = step()
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(local)
     cw.profile_reset()
     cw.profile_enable(True)
     l0 = cw.launch_count()
     barrier(world, device)
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.mark_start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -343,6 +366,7 @@ def run_cw(args):
         iters.append(it)
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks.mark_end()
     barrier(world, device)
     clk = clocks.stop()
     cw.profile_enable(False)
@@ -447,7 +471,9 @@ def run_cw(args):
         line = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": n, "d": D, "nnz": nnz, "m": M, "rtol": RTOL,
+                "config": {"workload": WORKLOAD if n == N_ROWS else
+                           "smaller case for profiler captures (n = %d), otherwise as: %s" % (n, WORKLOAD),
+                           "n": n, "d": D, "nnz": nnz, "m": M, "rtol": RTOL,
                            "l2": "inputs (2.3 GB of CSR and b) larger than the 129 MB L2; no flush",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clk,
