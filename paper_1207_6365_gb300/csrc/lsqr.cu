@@ -47,266 +47,218 @@ struct PassArgs {
     float coef_first;      // used when st == nullptr
 };
 
-constexpr int kPassBatch = 32;     // rows per warp batch (one per lane for row_ptr / z)
-constexpr int kPassCap = 640;      // staged nnz per batch (multiple of 4)
-constexpr int kPassStages = 2;
+constexpr int kPassBatch = 32;     // rows per warp batch (lane l holds row_ptr / z of row l)
 
-// Copies col/val[s, e) into the stage buffers (element base = s & ~3 at offset
-// 0).  16-byte copies for whole aligned chunks inside [0, nnz), 4-byte copies
-// for the rest.  Every lane of the warp calls this.
-// vec16: col and val are 16-byte aligned (scol / sval always are).
-__device__ __forceinline__ void stage_nnz(const int32_t* __restrict__ col, const float* __restrict__ val,
-                                          int64_t nnz, int64_t s, int64_t e, int32_t* scol, float* sval,
-                                          int lane, bool vec16) {
-    const int64_t base = s & ~3ll;
-    const int64_t end4 = (e + 3) & ~3ll;
-    const int64_t nchunk = (end4 - base) >> 2;
-    for (int64_t q = lane; q < nchunk; q += 32) {
-        const int64_t g = base + 4 * q;
-        if (vec16 && g + 4 <= nnz) {
-            cp_async16(scol + 4 * q, col + g);
-            cp_async16(sval + 4 * q, val + g);
-        } else {
-            for (int t = 0; t < 4; ++t)
-                if (g + t < nnz) {
-                    cp_async4(scol + 4 * q + t, col + g + t);
-                    cp_async4(sval + 4 * q + t, val + g + t);
-                }
-        }
-    }
+// Streaming 16-byte loads that do not allocate in L1 (each nonzero is read
+// once per pass; L1 is left to the shared-memory accumulators).
+__device__ __forceinline__ int4 ld_stream_i4(const int32_t* p) {
+    int4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p));
+    return r;
+}
+__device__ __forceinline__ float4 ld_stream_f4(const float* p) {
+    float4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p));
+    return r;
 }
 
-template <int LPR, int kPassWarps>
-__global__ void __launch_bounds__(kPassWarps * 32, 1) k_lsqr_pass(PassArgs a) {
+// One CTA per SM, kW warps; warp w owns a contiguous block of rows and walks
+// it in batches of 32.  Shared memory holds only vhat and eight accumulator
+// copies of A^T z per warp, so many warps fit on the SM; nonzeros go straight
+// from global memory to registers.
+//
+// Quad batches (every row starts on a 4-element boundary and has a multiple
+// of 4, at most 16, entries): four lanes per row, four entries per lane,
+// eight rows per step; all four steps' 16-byte loads are issued before the
+// first is used.  Row slot q of a step accumulates into copy q, so no two
+// lanes ever update the same address in one instruction and every address is
+// updated in program order: the sums are the same in every run.
+// Other batches: a half-warp per row (16 lanes, longer rows loop), four rows
+// at a time, two accumulator copies.
+template <int kW>
+__global__ void __launch_bounds__(kW * 32, 1) k_lsqr_pass(PassArgs a) {
     extern __shared__ __align__(16) float sm[];
     if (a.st && a.st->done) return;
-    constexpr int HALVES = 32 / LPR;          // rows processed side by side (scalar path)
-    constexpr int RPH = kPassBatch / HALVES;  // rows per sub-warp per batch
-    constexpr int COPIES = 8;                 // accumulator copies per warp (quad path: one per row slot)
-    static_assert(HALVES <= COPIES, "copies");
+    constexpr int LPR = 16, HALVES = 32 / LPR, RPH = kPassBatch / HALVES, COPIES = 8;
     const float coef = a.st ? (float)a.st->coef : a.coef_first;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sub = lane / LPR, sl = lane % LPR;
-    float* vh = sm;                                         // [dpad]
-    float* acc = vh + a.dpad;                               // [warps][COPIES][dpad]
-    // stage buffers start on a 128-byte boundary (16-byte cp.async targets)
-    const size_t stage_off = (((size_t)(1 + kPassWarps * COPIES) * a.dpad * sizeof(float)) + 127) & ~size_t(127);
-    int32_t* stage = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(sm) + stage_off);
+    float* vh = sm;                      // [dpad], zero past d
+    float* acc = vh + a.dpad;            // [kW][COPIES][dpad]
     const bool vec16 = ((reinterpret_cast<uintptr_t>(a.col) | reinterpret_cast<uintptr_t>(a.val)) & 15) == 0;
-    int32_t* wst = stage + (size_t)warp * kPassStages * 2 * (kPassCap + 8);
-    for (int j = threadIdx.x; j < a.d; j += blockDim.x) vh[j] = a.vhat[j];
-    for (int q = threadIdx.x; q < kPassWarps * COPIES * a.dpad; q += blockDim.x) acc[q] = 0.f;
+    for (int j = threadIdx.x; j < a.dpad; j += blockDim.x) vh[j] = j < a.d ? a.vhat[j] : 0.f;
+    for (int q = threadIdx.x; q < kW * COPIES * a.dpad; q += blockDim.x) acc[q] = 0.f;
     __syncthreads();
     float* myacc = acc + (size_t)(warp * COPIES + sub) * a.dpad;
-    const int qd = lane >> 2, ql = lane & 3;                // quad path: row slot, lane in quad
+    const int qd = lane >> 2, ql = lane & 3;   // quad batches: row slot, lane in quad
     float* qacc = acc + (size_t)(warp * COPIES + qd) * a.dpad;
 
-    // this warp's contiguous rows
-    const int64_t nw = (int64_t)gridDim.x * kPassWarps;
-    const int64_t gw = (int64_t)blockIdx.x * kPassWarps + warp;
+    const int64_t nw = (int64_t)gridDim.x * kW;
+    const int64_t gw = (int64_t)blockIdx.x * kW + warp;
     const int64_t per = (((a.n + nw - 1) / nw) + kPassBatch - 1) / kPassBatch * kPassBatch;
     const int64_t w0 = gw * per < a.n ? gw * per : a.n;
     const int64_t w1 = w0 + per < a.n ? w0 + per : a.n;
-    const int64_t nbatch = (w1 - w0 + kPassBatch - 1) / kPassBatch;
-    const int64_t nnz = a.row_ptr[a.n];
+    const int nbatch = (int)((w1 - w0 + kPassBatch - 1) / kPassBatch);
 
-    // batch registers: lane l holds row_ptr[r0 + l], the batch end, z_in[r0 + l]
-    auto load_meta = [&](int64_t k, int32_t& rp, int32_t& rend, float& zo) {
+    auto load_meta = [&](int k, int32_t& rp, int32_t& rend, float& zo) {
         rp = 0;
         rend = 0;
         zo = 0.f;
         if (k < nbatch) {
-            const int64_t r0 = w0 + k * kPassBatch;
-            const int64_t r = r0 + lane;
+            const int64_t r0 = w0 + (int64_t)k * kPassBatch;
             const int64_t rl = (r0 + kPassBatch < w1) ? r0 + kPassBatch : w1;
-            if (r < rl) {
-                rp = __ldg(a.row_ptr + r);
-                zo = __ldg(a.zin + r);
+            if (r0 + lane < rl) {
+                rp = __ldg(a.row_ptr + r0 + lane);
+                zo = __ldg(a.zin + r0 + lane);
             }
             rend = __ldg(a.row_ptr + rl);
         }
     };
-    auto issue = [&](int64_t k, int32_t rp, int32_t rend) {
-        if (k < nbatch) {
-            const int32_t s0 = __shfl_sync(0xFFFFFFFFu, rp, 0);
-            int32_t* scol = wst + (size_t)(k % kPassStages) * 2 * (kPassCap + 8);
-            float* sval = reinterpret_cast<float*>(scol + kPassCap + 8);
-            if (rend - s0 <= kPassCap) stage_nnz(a.col, a.val, nnz, s0, rend, scol, sval, lane, vec16);
-        }
-        cp_async_commit();
-    };
-
-    int32_t rpA, reA, rpB, reB, rpC, reC;
-    float zoA, zoB, zoC;
+    int32_t rpA, reA, rpB, reB;
+    float zoA, zoB;
     load_meta(0, rpA, reA, zoA);
-    load_meta(1, rpB, reB, zoB);
-    issue(0, rpA, reA);
     float zz = 0.f, bb = 0.f;
-    for (int64_t k = 0; k < nbatch; ++k) {
-        load_meta(k + 2, rpC, reC, zoC);
-        issue(k + 1, rpB, reB);
-        cp_async_wait<1>();
-        __syncwarp();
-        const int64_t r0 = w0 + k * kPassBatch;
+    for (int k = 0; k < nbatch; ++k) {
+        load_meta(k + 1, rpB, reB, zoB);   // next batch's rows, in flight during this one
+        const int64_t r0 = w0 + (int64_t)k * kPassBatch;
         const int nrows = (int)((r0 + kPassBatch < w1 ? r0 + kPassBatch : w1) - r0);
-        const int32_t s0 = __shfl_sync(0xFFFFFFFFu, rpA, 0);
-        const bool staged = reA - s0 <= kPassCap;
-        const int32_t base = s0 & ~3;
-        const int32_t* scol = wst + (size_t)(k % kPassStages) * 2 * (kPassCap + 8);
-        const float* sval = reinterpret_cast<const float*>(scol + kPassCap + 8);
         float zreg = 0.f;
-        // quad path: every row of the batch starts on a 4-element boundary and
-        // has a multiple of 4 (at most 16) entries -> 4 lanes per row, 4 entries
-        // per lane from 16-byte shared loads, 8 rows per warp step, row slot q
-        // of each step accumulating into copy q (rows in ascending order).
-        bool quad = false;
-        {
-            // every lane takes part in the shuffle and the vote (full masks)
-            const int32_t nxt = __shfl_down_sync(0xFFFFFFFFu, rpA, 1);
-            const int32_t myl = (lane < nrows) ? ((lane + 1 < nrows) ? nxt : reA) - rpA : 0;
-            const bool ok = (lane >= nrows) || (((rpA & 3) == 0) && ((myl & 3) == 0) && myl <= 16);
-            quad = __all_sync(0xFFFFFFFFu, ok) && staged && vec16;
-        }
+        // every lane takes part in the shuffle and the vote (full masks)
+        const int32_t nxt = __shfl_down_sync(0xFFFFFFFFu, rpA, 1);
+        const int32_t myl = (lane < nrows) ? ((lane + 1 < nrows) ? nxt : reA) - rpA : 0;
+        const bool okq = (lane >= nrows) || (((rpA & 3) == 0) && ((myl & 3) == 0) && myl <= 16);
+        const bool quad = __all_sync(0xFFFFFFFFu, okq) && vec16;
         if (quad) {
-#pragma unroll 1
-            for (int step = 0; step < kPassBatch / 8; ++step) {
+            int4 c4[4];
+            float4 v4[4];
+            int lens[4];
+            float zolds[4];
+#pragma unroll
+            for (int step = 0; step < 4; ++step) {
                 const int row = step * 8 + qd;
                 const int32_t rs = __shfl_sync(0xFFFFFFFFu, rpA, row);
-                const int32_t rn = __shfl_sync(0xFFFFFFFFu, rpA, (row + 1) & 31);
-                const float zold = __shfl_sync(0xFFFFFFFFu, zoA, row);
-                const int32_t re = (row + 1 < nrows) ? rn : reA;
-                const int len = row < nrows ? re - rs : 0;
-                const bool act = 4 * ql < len;
-                int4 c4 = make_int4(0, 0, 0, 0);
-                float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                lens[step] = __shfl_sync(0xFFFFFFFFu, myl, row);
+                zolds[step] = __shfl_sync(0xFFFFFFFFu, zoA, row);
+                c4[step] = make_int4(0, 0, 0, 0);
+                v4[step] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (4 * ql < lens[step]) {
+                    c4[step] = ld_stream_i4(a.col + rs + 4 * ql);
+                    v4[step] = ld_stream_f4(a.val + rs + 4 * ql);
+                }
+            }
+#pragma unroll
+            for (int step = 0; step < 4; ++step) {
+                const bool act = 4 * ql < lens[step];
+                int4 c = c4[step];
+                float4 v = v4[step];
                 if (act) {
-                    c4 = *reinterpret_cast<const int4*>(scol + (rs - base) + 4 * ql);
-                    v4 = *reinterpret_cast<const float4*>(sval + (rs - base) + 4 * ql);
-                    const unsigned cmax = max(max((unsigned)c4.x, (unsigned)c4.y), max((unsigned)c4.z, (unsigned)c4.w));
+                    const unsigned cmax = max(max((unsigned)c.x, (unsigned)c.y), max((unsigned)c.z, (unsigned)c.w));
                     if (cmax >= (unsigned)a.d) {
                         flag_error(a.status, kDevBadColumn);
-                        c4 = make_int4(0, 0, 0, 0);
-                        v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        c = make_int4(0, 0, 0, 0);
+                        v = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 }
                 float p = 0.f;
                 if (act) {
-                    p = v4.x * vh[c4.x];
-                    p = fmaf(v4.y, vh[c4.y], p);
-                    p = fmaf(v4.z, vh[c4.z], p);
-                    p = fmaf(v4.w, vh[c4.w], p);
+                    p = v.x * vh[c.x];
+                    p = fmaf(v.y, vh[c.y], p);
+                    p = fmaf(v.z, vh[c.z], p);
+                    p = fmaf(v.w, vh[c.w], p);
                 }
                 p += __shfl_xor_sync(0xFFFFFFFFu, p, 1);
                 p += __shfl_xor_sync(0xFFFFFFFFu, p, 2);
-                const float z = p - coef * zold;
+                const float z = p - coef * zolds[step];
                 const float zt = __shfl_sync(0xFFFFFFFFu, z, (lane & 7) * 4);
                 if ((lane >> 3) == step) zreg = zt;
                 if (act) {
-                    qacc[c4.x] = fmaf(v4.x, z, qacc[c4.x]);
-                    qacc[c4.y] = fmaf(v4.y, z, qacc[c4.y]);
-                    qacc[c4.z] = fmaf(v4.z, z, qacc[c4.z]);
-                    qacc[c4.w] = fmaf(v4.w, z, qacc[c4.w]);
+                    qacc[c.x] = fmaf(v.x, z, qacc[c.x]);
+                    qacc[c.y] = fmaf(v.y, z, qacc[c.y]);
+                    qacc[c.z] = fmaf(v.z, z, qacc[c.z]);
+                    qacc[c.w] = fmaf(v.w, z, qacc[c.w]);
                 }
                 __syncwarp();
             }
-        }
-        // scalar path: RI rows of this sub-warp at a time: independent dot
-        // products and reductions interleave; the A^T z updates then go row by
-        // row in order
-        constexpr int RI = 4;
+        } else {
+            // RI rows of this half-warp at a time: independent dot products and
+            // reductions interleave; the A^T z updates then go row by row in order
+            constexpr int RI = 4;
 #pragma unroll 1
-        for (int t0 = 0; t0 < (quad ? 0 : RPH); t0 += RI) {
-            int32_t rs[RI];
-            int len[RI];
-            float zold[RI], p[RI];
-            int c0[RI];
-            float v0[RI];
+            for (int t0 = 0; t0 < RPH; t0 += RI) {
+                int32_t rs[RI];
+                int len[RI];
+                float zold[RI], p[RI];
+                int c0[RI];
+                float v0[RI];
 #pragma unroll
-            for (int u = 0; u < RI; ++u) {
-                const int row = sub * RPH + t0 + u;
-                rs[u] = __shfl_sync(0xFFFFFFFFu, rpA, row & 31);
-                const int32_t rn = __shfl_sync(0xFFFFFFFFu, rpA, (row + 1) & 31);
-                zold[u] = __shfl_sync(0xFFFFFFFFu, zoA, row & 31);
-                const int32_t re = (row + 1 < nrows) ? rn : reA;
-                len[u] = row < nrows ? re - rs[u] : 0;
-                c0[u] = 0;
-                v0[u] = 0.f;
-                if (sl < len[u]) {
-                    if (staged) {
-                        c0[u] = scol[rs[u] - base + sl];
-                        v0[u] = sval[rs[u] - base + sl];
-                    } else {
+                for (int u = 0; u < RI; ++u) {
+                    const int row = sub * RPH + t0 + u;
+                    rs[u] = __shfl_sync(0xFFFFFFFFu, rpA, row & 31);
+                    len[u] = __shfl_sync(0xFFFFFFFFu, myl, row & 31);
+                    zold[u] = __shfl_sync(0xFFFFFFFFu, zoA, row & 31);
+                    c0[u] = 0;
+                    v0[u] = 0.f;
+                    if (sl < len[u]) {
                         c0[u] = __ldg(a.col + rs[u] + sl);
                         v0[u] = __ldg(a.val + rs[u] + sl);
                     }
                 }
-            }
 #pragma unroll
-            for (int u = 0; u < RI; ++u) {
-                p[u] = 0.f;
-                if (sl < len[u]) {
-                    if ((unsigned)c0[u] < (unsigned)a.d)
-                        p[u] = v0[u] * vh[c0[u]];
-                    else
-                        flag_error(a.status, kDevBadColumn);
-                }
-                for (int q = sl + LPR; q < len[u]; q += LPR) {  // rows longer than LPR
-                    int c;
-                    float v;
-                    if (staged) {
-                        c = scol[rs[u] - base + q];
-                        v = sval[rs[u] - base + q];
-                    } else {
-                        c = __ldg(a.col + rs[u] + q);
-                        v = __ldg(a.val + rs[u] + q);
+                for (int u = 0; u < RI; ++u) {
+                    p[u] = 0.f;
+                    if (sl < len[u]) {
+                        if ((unsigned)c0[u] < (unsigned)a.d)
+                            p[u] = v0[u] * vh[c0[u]];
+                        else
+                            flag_error(a.status, kDevBadColumn);
                     }
-                    if ((unsigned)c < (unsigned)a.d)
-                        p[u] = fmaf(v, vh[c], p[u]);
-                    else
-                        flag_error(a.status, kDevBadColumn);
-                }
-            }
-#pragma unroll
-            for (int o = LPR / 2; o > 0; o >>= 1)
-#pragma unroll
-                for (int u = 0; u < RI; ++u) p[u] += __shfl_xor_sync(0xFFFFFFFFu, p[u], o);
-#pragma unroll
-            for (int u = 0; u < RI; ++u) {
-                const float z = p[u] - coef * zold[u];
-                if (sl == t0 + u) zreg = z;
-                if (sl < len[u] && (unsigned)c0[u] < (unsigned)a.d) myacc[c0[u]] = fmaf(v0[u], z, myacc[c0[u]]);
-                for (int q = sl + LPR; q < len[u]; q += LPR) {
-                    int c;
-                    float v;
-                    if (staged) {
-                        c = scol[rs[u] - base + q];
-                        v = sval[rs[u] - base + q];
-                    } else {
-                        c = __ldg(a.col + rs[u] + q);
-                        v = __ldg(a.val + rs[u] + q);
+                    for (int q = sl + LPR; q < len[u]; q += LPR) {  // rows longer than LPR
+                        const int c = __ldg(a.col + rs[u] + q);
+                        const float v = __ldg(a.val + rs[u] + q);
+                        if ((unsigned)c < (unsigned)a.d)
+                            p[u] = fmaf(v, vh[c], p[u]);
+                        else
+                            flag_error(a.status, kDevBadColumn);
                     }
-                    if ((unsigned)c < (unsigned)a.d) myacc[c] = fmaf(v, z, myacc[c]);
                 }
-                __syncwarp();
+#pragma unroll
+                for (int o = LPR / 2; o > 0; o >>= 1)
+#pragma unroll
+                    for (int u = 0; u < RI; ++u) p[u] += __shfl_xor_sync(0xFFFFFFFFu, p[u], o);
+#pragma unroll
+                for (int u = 0; u < RI; ++u) {
+                    const float z = p[u] - coef * zold[u];
+                    if (sl == t0 + u) zreg = z;
+                    if (sl < len[u] && (unsigned)c0[u] < (unsigned)a.d) myacc[c0[u]] = fmaf(v0[u], z, myacc[c0[u]]);
+                    for (int q = sl + LPR; q < len[u]; q += LPR) {
+                        const int c = __ldg(a.col + rs[u] + q);
+                        const float v = __ldg(a.val + rs[u] + q);
+                        if ((unsigned)c < (unsigned)a.d) myacc[c] = fmaf(v, z, myacc[c]);
+                    }
+                    __syncwarp();
+                }
             }
         }
-        // scalar path: lane l of sub-warp h holds z of row h*RPH + l (l < RPH);
-        // quad path: lane l holds z of row l
+        // quad batches: lane l holds z of row l; others: lane l of half h
+        // holds z of row h*RPH + l (l < RPH)
         const int myrow = quad ? lane : sub * RPH + sl;
         if ((quad || sl < RPH) && myrow < nrows) {
             a.zout[r0 + myrow] = zreg;
             zz = fmaf(zreg, zreg, zz);
         }
         if (lane < nrows) bb = fmaf(zoA, zoA, bb);
-        __syncwarp();
-        rpA = rpB; reA = reB; zoA = zoB;
-        rpB = rpC; reB = reC; zoB = zoC;
+        rpA = rpB;
+        reA = reB;
+        zoA = zoB;
     }
-    cp_async_wait<0>();
     __syncthreads();
     // per-CTA partials: the accumulator copies summed in a fixed order with an
     // exact two-sum (float32 hi + lo), so no float64 pipe work per CTA
-    const int NS = kPassWarps * COPIES;
+    const int NS = kW * COPIES;
     for (int j = threadIdx.x; j < a.d; j += blockDim.x) {
         float hi = 0.f, lo = 0.f;
         for (int q = 0; q < NS; ++q) {
@@ -318,7 +270,7 @@ __global__ void __launch_bounds__(kPassWarps * 32, 1) k_lsqr_pass(PassArgs a) {
         }
         a.gpart[(size_t)blockIdx.x * a.d + j] = make_float2(hi, lo);
     }
-    __shared__ double rz[kPassWarps], rb[kPassWarps];
+    __shared__ double rz[kW], rb[kW];
     double zd = (double)zz, bd = (double)bb;
     for (int o = 16; o > 0; o >>= 1) {
         zd += __shfl_xor_sync(0xFFFFFFFFu, zd, o);
@@ -331,7 +283,7 @@ __global__ void __launch_bounds__(kPassWarps * 32, 1) k_lsqr_pass(PassArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0, tb = 0.0;
-        for (int w = 0; w < kPassWarps; ++w) {
+        for (int w = 0; w < kW; ++w) {
             t += rz[w];
             tb += rb[w];
         }
@@ -634,16 +586,20 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     const int64_t n = A->n;
     const int nsm = num_sms();
     const int grid = nsm;
-    // warps per CTA: as many as the per-warp shared memory (8 accumulator
-    // copies of d floats + two cp.async stages) allows, from {12, 8, 4}
-    const size_t per_warp = sizeof(float) * 8 * (size_t)(((d + 31) & ~31) + 1) +
-                            sizeof(int32_t) * kPassStages * 2 * (kPassCap + 8);
-    const int fit = (int)((220 * 1024) / per_warp);
-    const int pass_warps = fit >= 12 ? 12 : (fit >= 8 ? 8 : 4);
-    const int threads = pass_warps * 32;
-    const int lpr = 16;
+    // warps per CTA: the most (from 24, 16, 12, 8, 4) whose vhat + eight
+    // accumulator copies of d floats per warp fit in shared memory; 24 warps
+    // measured fastest at d = 256 (more leave too little L1 for the loads in flight)
     const int dpad = ((d + 31) & ~31) + 1;
-    const int nsub = pass_warps * 8;  // accumulator copies
+    auto pass_bytes = [&](int w) { return sizeof(float) * (size_t)dpad * (1 + 8 * (size_t)w); };
+    int pass_warps = 4;
+    for (int w : {24, 16, 12, 8})
+        if (pass_bytes(w) <= 220 * 1024) {
+            pass_warps = w;
+            break;
+        }
+    const int threads = pass_warps * 32;
+    const size_t pass_smem = pass_bytes(pass_warps);
+    if (pass_smem > 227 * 1024) return CW_ERR_SHAPE;
 
     Scratch ws(stream);
     const size_t oSA = ws.reserve(sizeof(float) * (size_t)m * d);
@@ -714,10 +670,11 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     CW_CUDA_TRY(cudaMemcpyAsync(y0, c, sizeof(double) * d, cudaMemcpyDeviceToDevice, stream));
     CW_LAUNCH_CHECK();
 
-    const size_t pass_smem = ((sizeof(float) * (size_t)dpad * (1 + nsub) + 127) & ~size_t(127)) +
-                             sizeof(int32_t) * (size_t)pass_warps * kPassStages * 2 * (kPassCap + 8);
-    if (pass_smem > 227 * 1024) return CW_ERR_SHAPE;
-    auto pk = pass_warps == 12 ? k_lsqr_pass<16, 12> : (pass_warps == 8 ? k_lsqr_pass<16, 8> : k_lsqr_pass<16, 4>);
+    auto pk = pass_warps == 24   ? k_lsqr_pass<24>
+              : pass_warps == 16 ? k_lsqr_pass<16>
+              : pass_warps == 12 ? k_lsqr_pass<12>
+              : pass_warps == 8  ? k_lsqr_pass<8>
+                                 : k_lsqr_pass<4>;
     CW_CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem));
     PassArgs pa{A->row_ptr, A->col, A->val, vhat, b, z, ws.at<float2>(ogp), ws.at<double>(ozp), ws.at<double>(obp),
                 nullptr, status, n, d, dpad, 1.0f};
