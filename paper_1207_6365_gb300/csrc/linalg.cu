@@ -401,19 +401,26 @@ __global__ void k_gram_to_f32(const double* __restrict__ Gm, int64_t cnt, float*
 
 // Cholesky of a pb x pb (pb <= 32) diagonal block held by one warp, lane k
 // holding column k in registers (entries 0..k): right-looking, the pivot and
-// row j of R reach the other lanes by shuffles.  Returns false, the same on
-// every lane, when a pivot is not positive.
-__device__ __forceinline__ bool chol_block32(float (&col)[kCholB], int pb) {
+// row j of R reach the other lanes by shuffles; 1 / R_jj from one reciprocal
+// square root (two roundings; the factor is a preconditioner).  Returns false,
+// the same on every lane, when a pivot is not positive.  rinv_out (lane j)
+// receives 1 / R_jj.
+__device__ __forceinline__ bool chol_block32(float (&col)[kCholB], int pb, float& rinv_out) {
     const int lane = threadIdx.x & 31;
     bool ok = true;
+    rinv_out = 1.f;
 #pragma unroll
     for (int j = 0; j < kCholB; ++j) {
         const float piv = __shfl_sync(0xFFFFFFFFu, col[j], j);
         if (j < pb) {
             if (!(piv > 0.f)) ok = false;
-            const float r = sqrtf(piv);
-            if (lane == j) col[j] = r;
-            else if (lane > j) col[j] = col[j] / r;
+            const float rinv = rsqrtf(piv);
+            if (lane == j) {
+                col[j] = piv * rinv;
+                rinv_out = rinv;
+            } else if (lane > j) {
+                col[j] *= rinv;
+            }
         }
         const float rjk = col[j];
 #pragma unroll
@@ -443,7 +450,8 @@ __global__ void __launch_bounds__(512) k_chol_panel(float* __restrict__ W, int d
         float col[kCholB];
 #pragma unroll
         for (int q = 0; q < kCholB; ++q) col[q] = D[q][tid];
-        const bool ok = chol_block32(col, pb);
+        float rinv_unused;
+        const bool ok = chol_block32(col, pb, rinv_unused);
         if (!ok && tid == 0) {
             fail = 1;
             atomicExch(bad, 1u);
@@ -523,44 +531,55 @@ __global__ void __launch_bounds__(256) k_chol_update(float* __restrict__ W, int 
 // register arrays get the whole register budget.
 __device__ __forceinline__ int chol_off(int i, int nc) { return i * nc - (i * (i + 1)) / 2; }
 
-// warp 0: diagonal block of panel p0 (pb columns) into Dg and back into P;
-// returns false on a non-positive pivot (the same on every lane)
-__device__ __noinline__ bool chol_small_factor(float* P, float (*Dg)[kCholB + 1], int nc, int p0, int pb) {
+// Warp 0: the diagonal block of panel p0 (pb columns) from P into registers,
+// factored by chol_block32, written back to P and to Dg, with 1 / R_jj in
+// Dinv.  Not inlined, so its 32 registers of column do not add to the
+// kernel's peak.  Returns false (every lane) on a non-positive pivot.
+__device__ __noinline__ bool chol_small_diag(float* P, float (*Dg)[kCholB + 1], float* Dinv, int nc, int p0,
+                                             int pb) {
     const int lane = threadIdx.x & 31;
     float col[kCholB];
 #pragma unroll
     for (int q = 0; q < kCholB; ++q) col[q] = (q <= lane && lane < pb) ? P[chol_off(p0 + q, nc) + p0 + lane] : 0.f;
-    const bool ok = chol_block32(col, pb);
+    float rinv;
+    const bool ok = chol_block32(col, pb, rinv);
 #pragma unroll
     for (int q = 0; q < kCholB; ++q) {
         if (q <= lane && lane < pb) P[chol_off(p0 + q, nc) + p0 + lane] = col[q];
         Dg[q][lane] = col[q];
     }
+    Dinv[lane] = rinv;
     return ok;
 }
 
-// column k to the right of the block: R_pp^T x = P[p0.., k], rows in two halves of 16
-__device__ __noinline__ void chol_small_panel(float* P, const float (*Dg)[kCholB + 1], int nc, int p0, int pb,
-                                              int k) {
+// Column k (>= s0) of the panel rows right of the diagonal block: R_pp^T x =
+// P[p0.., k] by forward substitution in registers, rows 0..15 then 16..31;
+// the result goes to P and densely to Pan (zero past the last column, nc <= k
+// < s0 + tp, and below row pb).  Not inlined: the caller's loop would
+// otherwise hoist the Dg loads and spill.
+__device__ __noinline__ void chol_small_panel(float* P, float* Pan, const float (*Dg)[kCholB + 1],
+                                              const float* Dinv, int nc, int p0, int pb, int s0, int tp, int k) {
+    // rows 0..15 of the panel, then rows 16..31 (fewer live registers)
     float x[16], y[16];
-    int o = chol_off(p0, nc) + k;   // P index of (p0 + i, k), advanced row by row
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        x[i] = (i < pb) ? P[o] : 0.f;
-        o += nc - (p0 + i) - 1;
-    }
+    const bool live = k < nc;
+    int o = chol_off(p0, nc) + k;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-        x[q] = (q < pb) ? x[q] / Dg[q][q] : 0.f;
+        x[q] = (live && q < pb) ? P[o] : 0.f;
+        o += nc - (p0 + q) - 1;
+    }
+    const int o16 = o;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        x[q] *= Dinv[q];
 #pragma unroll
         for (int i = 0; i < 16; ++i)
             if (i > q) x[i] = fmaf(-Dg[q][i], x[q], x[i]);
     }
-    const int o16 = o;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        y[i] = (16 + i < pb) ? P[o] : 0.f;
-        o += nc - (p0 + 16 + i) - 1;
+    for (int q = 0; q < 16; ++q) {
+        y[q] = (live && 16 + q < pb) ? P[o] : 0.f;
+        o += nc - (p0 + 16 + q) - 1;
     }
 #pragma unroll
     for (int q = 0; q < 16; ++q)
@@ -568,97 +587,118 @@ __device__ __noinline__ void chol_small_panel(float* P, const float (*Dg)[kCholB
         for (int i = 0; i < 16; ++i) y[i] = fmaf(-Dg[q][16 + i], x[q], y[i]);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-        y[q] = (16 + q < pb) ? y[q] / Dg[16 + q][16 + q] : 0.f;
+        y[q] *= Dinv[16 + q];
 #pragma unroll
         for (int i = 0; i < 16; ++i)
             if (i > q) y[i] = fmaf(-Dg[16 + q][16 + i], y[q], y[i]);
     }
     o = chol_off(p0, nc) + k;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        if (i < pb) P[o] = x[i];
-        o += nc - (p0 + i) - 1;
+    for (int q = 0; q < 16; ++q) {
+        if (live && q < pb) P[o] = x[q];
+        o += nc - (p0 + q) - 1;
+        Pan[q * tp + (k - s0)] = (q < pb) ? x[q] : 0.f;
     }
     o = o16;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        if (16 + i < pb) P[o] = y[i];
-        o += nc - (p0 + 16 + i) - 1;
+    for (int q = 0; q < 16; ++q) {
+        if (live && 16 + q < pb) P[o] = y[q];
+        o += nc - (p0 + 16 + q) - 1;
+        Pan[(16 + q) * tp + (k - s0)] = (16 + q < pb) ? y[q] : 0.f;
     }
 }
 
-// P[i][k] -= sum_q R[p0+q][i] R[p0+q][k] for i in [i0, i0 + 4) (< d), the lane's
-// four columns kb + lane + 32c (>= i, < nc)
-__device__ __noinline__ void chol_small_update(float* P, int d, int nc, int p0, int pb, int i0, int kb) {
-    const int lane = threadIdx.x & 31;
-    float acc[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
-    int o = chol_off(p0, nc);
-    for (int q = 0; q < pb; ++q) {
-        const float* Rq = P + o;
-        float a[4], b[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = (i0 + r < d) ? Rq[i0 + r] : 0.f;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int k = kb + lane + 32 * c;
-            b[c] = (k < nc) ? Rq[k] : 0.f;
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
-        o += nc - (p0 + q) - 1;
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int i = i0 + r, k = kb + lane + 32 * c;
-            if (i < d && k < nc && k >= i) P[chol_off(i, nc) + k] -= acc[r][c];
-        }
-}
-
-__global__ void __launch_bounds__(512) k_chol_small(float* __restrict__ W, int d, int nc, unsigned* bad) {
-    extern __shared__ float P[];
+// Pan: the panel's rows of R right of the diagonal block, dense (row q at
+// Pan + q * tp, column k - s0), zero past the last column; the trailing
+// update is then a rank-32 product with 8 x 8 register tiles and 16-byte
+// shared-memory operand loads.
+__global__ void __launch_bounds__(512) k_chol_small(float* __restrict__ W, int d, int nc, int tpmax,
+                                                   unsigned* bad) {
+    extern __shared__ __align__(16) float P[];
     __shared__ float Dg[kCholB][kCholB + 1];   // R of the current diagonal block
+    __shared__ float Dinv[kCholB];             // 1 / its diagonal
     __shared__ int fail;
-    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, nw = nt >> 5;
-    for (int q = tid; q < nc * nc; q += nt) {
-        const int i = q / nc, k = q - i * nc;
-        if (k >= i) cp_async4(P + chol_off(i, nc) + k, W + q);
+    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    const int psz = ((nc * (nc + 1) / 2) + 3) & ~3;
+    float* Pan = P + psz;                      // [kCholB][tpmax]
+    for (int i = warp; i < nc; i += nw) {      // row i of the upper triangle, one warp per row
+        float* dst = P + chol_off(i, nc);
+        const float* src = W + (int64_t)i * nc;
+        for (int k = i + lane; k < nc; k += 32) cp_async4(dst + k, src + k);
     }
     cp_async_wait_all();
     if (tid == 0) fail = 0;
     __syncthreads();
     for (int p0 = 0; p0 < d; p0 += kCholB) {
         const int pb = min(kCholB, d - p0);
-        if (warp == 0) {
-            const bool ok = chol_small_factor(P, Dg, nc, p0, pb);
-            if (!ok && tid == 0) {
-                fail = 1;
-                atomicExch(bad, 1u);
-            }
+        const int s0 = p0 + pb;
+        if (warp == 0 && !chol_small_diag(P, Dg, Dinv, nc, p0, pb) && lane == 0) {
+            fail = 1;
+            atomicExch(bad, 1u);
         }
         __syncthreads();
         if (fail) return;
-        const int s0 = p0 + pb;
-        for (int k = s0 + tid; k < nc; k += nt) chol_small_panel(P, Dg, nc, p0, pb, k);
+        if (s0 >= nc) break;
+        // panel rows right of the block: R_pp^T x = P[p0.., k] by forward
+        // substitution in registers (thread = column); the result goes to P and
+        // densely to Pan (zero past the last column and below row pb)
+        const int T = nc - s0, tp = (T + 7) & ~7;
+        for (int k = s0 + tid; k < s0 + tp; k += nt) chol_small_panel(P, Pan, Dg, Dinv, nc, p0, pb, s0, tp, k);
         __syncthreads();
-        const int nbi = (d - s0 + 3) / 4, ng = (nc - s0 + 127) / 128;
-        for (int wt = warp; wt < nbi * ng; wt += nw) {
-            const int bi = wt / ng, g = wt - bi * ng;
-            const int i0 = s0 + 4 * bi, kb = s0 + 128 * g;
-            if (kb + 127 >= i0) chol_small_update(P, d, nc, p0, pb, i0, kb);   // else below the diagonal
+        if (s0 >= d) break;
+        // 8 x 8 tiles (ti <= tk) of the trailing upper triangle, rows < d
+        const int nti = (d - s0 + 7) / 8, ntk = tp / 8;
+        const int ntiles = nti * ntk - nti * (nti - 1) / 2;
+        for (int t = tid; t < ntiles; t += nt) {
+            int ti = 0, rem = t;
+            while (rem >= ntk - ti) {
+                rem -= ntk - ti;
+                ++ti;
+            }
+            const int tk = ti + rem;
+            float acc[8][8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+            const float* pa = Pan + 8 * ti;
+            const float* pk = Pan + 8 * tk;
+            for (int q = 0; q < pb; ++q) {
+                const float4 a0 = *reinterpret_cast<const float4*>(pa + q * tp);
+                const float4 a1 = *reinterpret_cast<const float4*>(pa + q * tp + 4);
+                const float4 b0 = *reinterpret_cast<const float4*>(pk + q * tp);
+                const float4 b1 = *reinterpret_cast<const float4*>(pk + q * tp + 4);
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int i = s0 + 8 * ti + r;
+                if (i >= d) break;
+                float* row = P + chol_off(i, nc);
+                float cur[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {   // the row's eight values first, then the stores
+                    const int k = s0 + 8 * tk + c;
+                    cur[c] = (k >= i && k < nc) ? row[k] : 0.f;
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int k = s0 + 8 * tk + c;
+                    if (k >= i && k < nc) row[k] = cur[c] - acc[r][c];
+                }
+            }
         }
         __syncthreads();
     }
-    for (int q = tid; q < nc * nc; q += nt) {
-        const int i = q / nc, k = q - i * nc;
-        if (k >= i) W[q] = P[chol_off(i, nc) + k];
+    for (int i = warp; i < nc; i += nw) {
+        const float* src = P + chol_off(i, nc);
+        float* dst = W + (int64_t)i * nc;
+        for (int k = i + lane; k < nc; k += 32) dst[k] = src[k];
     }
 }
 
@@ -737,6 +777,126 @@ __global__ void __launch_bounds__(256) k_tri_inv_f32(const float* __restrict__ W
         const float v = (i <= col) ? x[i] : 0.f;
         M[(int64_t)i * d + col] = (double)v;
         M32T[(int64_t)col * d + i] = v;
+    }
+}
+
+// ---- blocked inverse of the float32 Cholesky factor (blocks of 32) -------
+//
+// With R = [R_IK] in 32 x 32 blocks, the blocks of M = R^-1 satisfy
+// M_II = R_II^-1 and, for I < J, M_IJ = -M_II sum_{K=I+1..J} R_IK M_KJ.
+// k_tri_diag_inv forms every M_II (one warp each, lane c back-substitutes
+// column c); k_tri_inv_blk then builds block column J in one CTA, from block
+// row J - 1 up to block row 0, each step a 32 x 32 product over the blocks
+// already found and a multiply by M_II.
+
+__global__ void __launch_bounds__(32) k_tri_diag_inv(const float* __restrict__ W, int d, int nc,
+                                                    float* __restrict__ Dinv) {
+    __shared__ float Rb[kCholB][kCholB + 1];
+    __shared__ float X[kCholB][kCholB + 1];
+    const int I = blockIdx.x, lane = threadIdx.x;
+    const int i0 = I * kCholB, ib = min(kCholB, d - i0);
+    for (int r = 0; r < kCholB; ++r)
+        Rb[r][lane] = (r < ib && lane < ib && lane >= r) ? W[(int64_t)(i0 + r) * nc + i0 + lane] : 0.f;
+    __syncwarp();
+    // column c = lane of R_II^-1: x_c = 1 / R_cc, x_i = -(sum_{i<k<=c} R_ik x_k) / R_ii
+    const int c = lane;
+    for (int r = 0; r < kCholB; ++r) X[r][c] = 0.f;
+    if (c < ib) {
+        X[c][c] = 1.f / Rb[c][c];
+        for (int i = c - 1; i >= 0; --i) {
+            float sacc = 0.f;
+            for (int k = i + 1; k <= c; ++k) sacc = fmaf(Rb[i][k], X[k][c], sacc);
+            X[i][c] = -sacc / Rb[i][i];
+        }
+    }
+    __syncwarp();
+    float* out = Dinv + (size_t)I * kCholB * kCholB;
+    for (int r = 0; r < kCholB; ++r) out[r * kCholB + lane] = X[r][lane];
+}
+
+__global__ void __launch_bounds__(256) k_tri_inv_blk(const float* __restrict__ W, int d, int nc,
+                                                    const float* __restrict__ Dinv, double* __restrict__ M,
+                                                    float* __restrict__ M32T) {
+    extern __shared__ __align__(16) float sh[];
+    const int J = blockIdx.x, tid = threadIdx.x;
+    const int j0 = J * kCholB, jb = min(kCholB, d - j0);
+    const int rows = j0 + kCholB;                 // block rows 0..J of the column block
+    const int rw = j0 + 1;
+    float* Mc = sh;                               // [rows][32]: M_KJ, K <= J
+    float* T = Mc + (size_t)rows * kCholB;        // [32][33]
+    float* Dv = T + kCholB * (kCholB + 1);        // [J + 1][32][32]: M_II
+    float* Rb0 = Dv + (size_t)(J + 1) * kCholB * kCholB;   // two buffers [32][rw]: block row I of R
+    float* Rb1 = Rb0 + (size_t)kCholB * rw;
+    // block row I of R, columns 32 (I + 1) .. j0 + jb - 1, into buf (4-byte async copies)
+    auto load_row = [&](int I, float* buf) {
+        const int i0 = I * kCholB, k0 = i0 + kCholB, w = j0 + jb - k0;
+        for (int q = tid; q < kCholB * w; q += blockDim.x) {
+            const int r = q / w, k = q - r * w;
+            cp_async4(buf + r * rw + k, W + (int64_t)(i0 + r) * nc + k0 + k);
+        }
+    };
+    for (int q = tid; q < (J + 1) * kCholB * kCholB; q += blockDim.x) cp_async4(Dv + q, Dinv + q);
+    if (J >= 1) load_row(J - 1, Rb0);
+    cp_async_commit();
+    for (int q = tid; q < rows * kCholB; q += blockDim.x) {
+        const int r = q / kCholB, c = q % kCholB;
+        Mc[q] = (r >= j0 && r - j0 < jb && c < jb) ? Dinv[(size_t)J * kCholB * kCholB + (r - j0) * kCholB + c] : 0.f;
+    }
+    const int tr = tid >> 3, tc = (tid & 7) * 4;  // T rows tr, columns tc .. tc + 3
+    int buf = 0;
+    for (int I = J - 1; I >= 0; --I) {
+        float* Rb = buf ? Rb1 : Rb0;
+        if (I >= 1) load_row(I - 1, buf ? Rb0 : Rb1);   // next block row, in flight during this step
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const int i0 = I * kCholB;
+        const int k0 = i0 + kCholB, w = j0 + jb - k0;
+        float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+        const float* rrow = Rb + tr * rw;
+        const float* mrow = Mc + (size_t)k0 * kCholB + tc;
+#pragma unroll 4
+        for (int k = 0; k < w; ++k) {
+            const float rv = rrow[k];
+            const float4 mv = *reinterpret_cast<const float4*>(mrow + (size_t)k * kCholB);
+            t0 = fmaf(rv, mv.x, t0);
+            t1 = fmaf(rv, mv.y, t1);
+            t2 = fmaf(rv, mv.z, t2);
+            t3 = fmaf(rv, mv.w, t3);
+        }
+        T[tr * (kCholB + 1) + tc] = t0;
+        T[tr * (kCholB + 1) + tc + 1] = t1;
+        T[tr * (kCholB + 1) + tc + 2] = t2;
+        T[tr * (kCholB + 1) + tc + 3] = t3;
+        __syncthreads();
+        const float* dinv = Dv + (size_t)I * kCholB * kCholB + tr * kCholB;
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+        for (int q = tr; q < kCholB; ++q) {
+            const float dv = dinv[q];
+            m0 = fmaf(dv, T[q * (kCholB + 1) + tc], m0);
+            m1 = fmaf(dv, T[q * (kCholB + 1) + tc + 1], m1);
+            m2 = fmaf(dv, T[q * (kCholB + 1) + tc + 2], m2);
+            m3 = fmaf(dv, T[q * (kCholB + 1) + tc + 3], m3);
+        }
+        float* out = Mc + (size_t)(i0 + tr) * kCholB + tc;
+        out[0] = -m0;
+        out[1] = -m1;
+        out[2] = -m2;
+        out[3] = -m3;
+        buf ^= 1;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // column block J of M (float64, row-major) and of M32T (float32, column-major)
+    for (int q = tid; q < d * kCholB; q += blockDim.x) {
+        const int i = q / kCholB, c = q % kCholB;
+        if (c >= jb) continue;
+        const float v = (i < rows) ? Mc[(size_t)i * kCholB + c] : 0.f;
+        M[(int64_t)i * d + j0 + c] = (double)v;
+    }
+    for (int q = tid; q < jb * d; q += blockDim.x) {
+        const int c = q / d, i = q % d;
+        M32T[(int64_t)(j0 + c) * d + i] = (i < rows) ? Mc[(size_t)i * kCholB + c] : 0.f;
     }
 }
 
@@ -903,12 +1063,15 @@ int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double
         CW_PROF("k_gram_to_f32", stream);
         k_gram_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(Gm, tot, W);
     }
-    const size_t psm = sizeof(float) * ((size_t)nc * (nc + 1) / 2);
-    const bool small = psm + 1024 <= 227 * 1024;
+    // one-CTA factorization when the packed triangle and a dense 32-row panel fit
+    const int tpmax = (nc + 7) & ~7;
+    const size_t psm = sizeof(float) * ((((size_t)nc * (nc + 1) / 2) + 3) & ~size_t(3)) +
+                       sizeof(float) * (size_t)kCholB * tpmax;
+    const bool small = psm + 6 * 1024 <= 227 * 1024 && nc <= 512;
     if (small) {
         CW_CUDA_TRY(cudaFuncSetAttribute(k_chol_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
         CW_PROF("k_chol_small", stream);
-        k_chol_small<<<1, 512, psm, stream>>>(W, d, nc, bad);
+        k_chol_small<<<1, 512, psm, stream>>>(W, d, nc, tpmax, bad);
     }
     for (int p0 = 0; !small && p0 < d; p0 += kCholB) {
         {
@@ -928,16 +1091,26 @@ int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double
         CW_PROF("k_chol_finish", stream);
         k_chol_finish<<<1, 1024, 0, stream>>>(W, d, nc, c, klb);
     }
-    const size_t packed = sizeof(float) * ((size_t)d * (d + 1) / 2);
-    const size_t xs = sizeof(float) * 8 * 1024;
-    if (xs + packed <= 200 * 1024) {
-        CW_CUDA_TRY(cudaFuncSetAttribute(k_tri_inv_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(xs + packed)));
-        CW_PROF("k_tri_inv_f32", stream);
-        k_tri_inv_f32<true><<<(d + 7) / 8, 256, xs + packed, stream>>>(W, d, nc, M, M32T);
-    } else {
-        CW_PROF("k_tri_inv_f32", stream);
-        k_tri_inv_f32<false><<<(d + 7) / 8, 256, xs, stream>>>(W, d, nc, M, M32T);
+    // M = R^-1: diagonal block inverses, then one CTA per block column
+    {
+        const int nb = (d + kCholB - 1) / kCholB;
+        float* Dinv = reinterpret_cast<float*>(Gm);   // Gram no longer needed; nb * 32 * 32 floats fit
+        {
+            CW_PROF("k_tri_diag_inv", stream);
+            k_tri_diag_inv<<<nb, 32, 0, stream>>>(W, d, nc, Dinv);
+        }
+        // Mc + T + the diagonal inverses + two block rows of R
+        const size_t ism = sizeof(float) * ((size_t)nb * kCholB * kCholB + kCholB * (kCholB + 1) +
+                                            (size_t)nb * kCholB * kCholB +
+                                            2 * (size_t)kCholB * ((nb - 1) * kCholB + 1));
+        if (ism <= 200 * 1024) {
+            CW_CUDA_TRY(cudaFuncSetAttribute(k_tri_inv_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+            CW_PROF("k_tri_inv_blk", stream);
+            k_tri_inv_blk<<<nb, 256, ism, stream>>>(W, d, nc, Dinv, M, M32T);
+        } else {   // large d: one warp per column of M, R read from global memory
+            CW_PROF("k_tri_inv_f32", stream);
+            k_tri_inv_f32<false><<<(d + 7) / 8, 256, sizeof(float) * 8 * 1024, stream>>>(W, d, nc, M, M32T);
+        }
     }
     CW_LAUNCH_CHECK();
     unsigned h[2] = {0, 0};

@@ -299,6 +299,7 @@ struct PostArgs {
     int nblk;
     int d;
     const float* M32T;    // M = R^-1 (float32 values), column-major: M32T[j * d + i] = M_ij
+    const float* M32P;    // the same, packed by columns: M_ij (i <= j) at j (j + 1) / 2 + i
     const double* y0;     // R x0
     double* v;
     double* w;
@@ -311,53 +312,74 @@ struct PostArgs {
     int first;
 };
 
+// Sum over the block, the same on every thread and in every run: a shuffle
+// tree in each warp (skipped by warps whose values are all zero), then warp 0
+// adds the per-warp sums the same way.  float64 issues slowly on this part,
+// so only these few warp instructions use it.  red: 33 doubles.
 __device__ double block_sum(double v, double* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    __syncthreads();
+    if (__any_sync(0xFFFFFFFFu, v != 0.0))
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     if (lane == 0) red[warp] = v;
     __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += red[w];  // every thread, same order
-    return t;
+    if (warp == 0) {
+        double t = lane < nw ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+        if (lane == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
 }
 
+// SMEM_M: the packed triangle of M is copied to shared memory at the start
+// (one round of 16-byte copies, overlapped with the partial-sum reduction),
+// and both products with M read it from there.
+template <bool SMEM_M>
 __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
-    __shared__ double red[32];
+    extern __shared__ __align__(16) float Ms[];
+    __shared__ double red[33];
     __shared__ double sg[1024];
     __shared__ double sv[1024];
     LsqrState* st = a.st;
     if (st->done) return;
     const int d = a.d;
+    if (SMEM_M) {
+        const int nq = (d * (d + 1) / 2 + 3) / 4;
+        for (int q = threadIdx.x; q < nq; q += blockDim.x) cp_async16(Ms + 4 * q, a.M32P + 4 * q);
+        cp_async_commit();
+    }
     // reduce the pass partials (two-word sums) -> g = A^T z as float32 (hi, lo)
-    // pairs in shared memory; `gp` threads per column take fixed stripes of
-    // blocks, four independent loads in flight, stripes combined in order
+    // pairs in shared memory: `gp` threads per column, thread g taking blocks
+    // g, g + gp, ... in order, eight independent loads in flight (the next
+    // eight issued before the current ones are added); the gp sums combined in order
     __shared__ float ghi[1024], glo[1024];
     {
         __shared__ float2 gstripe[1024];
         const int gp = blockDim.x / d >= 4 ? 4 : (blockDim.x / d >= 2 ? 2 : 1);
+        constexpr int U = 8;
         for (int tq = threadIdx.x; tq < d * gp; tq += blockDim.x) {
             const int j = tq % d, g = tq / d;
+            const int nb = (a.nblk - g + gp - 1) / gp;   // blocks g + gp * t, t < nb
             float hi = 0.f, lo = 0.f;
-            int b = g;
-            for (; b + 3 * gp < a.nblk; b += 4 * gp) {
-                float2 x[4];
+            float2 cur[U], nxt[U];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) x[u] = a.gpart[(size_t)(b + u * gp) * d + j];
+            for (int u = 0; u < U; ++u)
+                cur[u] = u < nb ? a.gpart[(size_t)(g + gp * u) * d + j] : make_float2(0.f, 0.f);
+            for (int t0 = 0; t0 < nb; t0 += U) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float t = hi + x[u].x;
-                    const float bp = t - hi;
-                    lo += (hi - (t - bp)) + (x[u].x - bp) + x[u].y;
-                    hi = t;
+                for (int u = 0; u < U; ++u)
+                    nxt[u] = t0 + U + u < nb ? a.gpart[(size_t)(g + gp * (t0 + U + u)) * d + j] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (t0 + u < nb) {
+                        const float t = hi + cur[u].x;
+                        const float bp = t - hi;
+                        lo += (hi - (t - bp)) + (cur[u].x - bp) + cur[u].y;
+                        hi = t;
+                    }
                 }
-            }
-            for (; b < a.nblk; b += gp) {
-                const float2 x = a.gpart[(size_t)b * d + j];
-                const float t = hi + x.x;
-                const float bp = t - hi;
-                lo += (hi - (t - bp)) + (x.x - bp) + x.y;
-                hi = t;
+#pragma unroll
+                for (int u = 0; u < U; ++u) cur[u] = nxt[u];
             }
             gstripe[g * d + j] = make_float2(hi, lo);
         }
@@ -374,6 +396,7 @@ __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
             ghi[j] = hi;
             glo[j] = lo;
         }
+        if (SMEM_M) cp_async_wait_all();
         __syncthreads();
     }
     double zz = 0.0, bb = 0.0;
@@ -388,39 +411,33 @@ __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
     // scale of u = z * s_new: z = A x0 - b = -r0 on the first step
     const double s_new = beta > 0.0 ? (a.first ? -1.0 / beta : 1.0 / beta) : 0.0;
     // t = M^T (A^T z): exact float32 products (fma two-product) and two-word
-    // sums; `gper` threads per column over fixed slices, combined in order
-    __shared__ float2 tpart[1024];
+    // sums; one warp per column (columns w, w + 32, ...), lane l taking rows
+    // l, l + 32, ... in order, then a fixed shuffle tree of two-word sums
     {
-        const int gper = blockDim.x / d >= 4 ? 4 : (blockDim.x / d >= 2 ? 2 : 1);
-        for (int tq = threadIdx.x; tq < d * gper; tq += blockDim.x) {
-            const int j = tq % d, g = tq / d;
-            const int len = j + 1, lo = (int)((int64_t)len * g / gper), hi = (int)((int64_t)len * (g + 1) / gper);
-            const float* mcol = a.M32T + (size_t)j * d;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+        for (int j = warp; j < d; j += nwarp) {
+            const float* mcol = SMEM_M ? Ms + j * (j + 1) / 2 : a.M32T + (size_t)j * d;
             float sh = 0.f, sl2 = 0.f;
-            int i = lo;
-            for (; i < hi; i += 8) {
-                float mv[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) mv[u] = (i + u < hi) ? mcol[i + u] : 0.f;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (i + u >= hi) break;
-                    const float p = mv[u] * ghi[i + u];
-                    float e = fmaf(mv[u], ghi[i + u], -p);
-                    e = fmaf(mv[u], glo[i + u], e);
-                    const float t = sh + p;
-                    const float bp = t - sh;
-                    sl2 += (sh - (t - bp)) + (p - bp) + e;
-                    sh = t;
-                }
+            for (int i = lane; i <= j; i += 32) {
+                const float m = mcol[i];
+                const float p = m * ghi[i];
+                float e = fmaf(m, ghi[i], -p);
+                e = fmaf(m, glo[i], e);
+                const float t = sh + p;
+                const float bp = t - sh;
+                sl2 += (sh - (t - bp)) + (p - bp) + e;
+                sh = t;
             }
-            tpart[g * d + j] = make_float2(sh, sl2);
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < d; j += blockDim.x) {
-            double t = 0.0;
-            for (int g = 0; g < gper; ++g) t += (double)tpart[g * d + j].x + (double)tpart[g * d + j].y;
-            sv[j] = t;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xFFFFFFFFu, sh, o);
+                const float ol = __shfl_xor_sync(0xFFFFFFFFu, sl2, o);
+                const float t = sh + oh;
+                const float bp = t - sh;
+                sl2 += (sh - (t - bp)) + (oh - bp) + ol;
+                sh = t;
+            }
+            if (lane == 0) sv[j] = (double)sh + (double)sl2;
         }
         __syncthreads();
     }
@@ -462,27 +479,38 @@ __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
             }
         }
     } else {
-        const double alpha_old = st->alpha;
-        const double anorm2 = st->anorm2 + alpha_old * alpha_old + beta * beta;
-        const double rho = hypot(st->rhobar, beta);
-        const double c = st->rhobar / rho, sn = beta / rho;
-        const double theta = sn * alpha;
-        const double phi = c * st->phibar;
-        const double phibar = sn * st->phibar;
+        // the plane rotation and its scalars once (thread 0), then the vector updates
+        __shared__ double sc[8];
+        if (threadIdx.x == 0) {
+            const double alpha_old = st->alpha;
+            const double anorm2 = st->anorm2 + alpha_old * alpha_old + beta * beta;
+            const double rho = hypot(st->rhobar, beta);
+            const double c = st->rhobar / rho, sn = beta / rho;
+            const double rinv = 1.0 / rho;
+            sc[0] = c * st->phibar * rinv;     // phi / rho
+            sc[1] = sn * alpha * rinv;         // theta / rho
+            sc[2] = alpha > 0.0 ? 1.0 / alpha : 0.0;
+            sc[3] = anorm2;
+            sc[4] = c;
+            sc[5] = sn * st->phibar;           // phibar
+        }
+        __syncthreads();
+        const double k_dy = sc[0], k_w = sc[1], ainv = sc[2];
         double yl = 0.0;
         for (int j = threadIdx.x; j < d; j += blockDim.x) {
-            const double vj = alpha > 0.0 ? sv[j] / alpha : 0.0;
+            const double vj = sv[j] * ainv;
             const double wj = a.w[j];
-            const double dyj = a.dy[j] + (phi / rho) * wj;
+            const double dyj = fma(k_dy, wj, a.dy[j]);
             a.dy[j] = dyj;
-            a.w[j] = vj - (theta / rho) * wj;
+            a.w[j] = fma(-k_w, wj, vj);
             a.v[j] = vj;
             sv[j] = vj;
             const double yj = a.y0[j] + dyj;
-            yl += yj * yj;
+            yl = fma(yj, yj, yl);
         }
         const double ynorm = sqrt(block_sum(yl, red));
         if (threadIdx.x == 0) {
+            const double anorm2 = sc[3], c = sc[4], phibar = sc[5];
             const double anorm = sqrt(anorm2);
             const double rnorm = phibar;
             const double arnorm = phibar * alpha * fabs(c);
@@ -521,13 +549,23 @@ __global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
             const int len = d - i, lo = i + (int)((int64_t)len * g / gper), hi = i + (int)((int64_t)len * (g + 1) / gper);
             float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
             int j = lo;
-            for (; j + 3 < hi; j += 4) {
-                s0 = fmaf(a.M32T[(size_t)j * d + i], vf[j], s0);
-                s1 = fmaf(a.M32T[(size_t)(j + 1) * d + i], vf[j + 1], s1);
-                s2 = fmaf(a.M32T[(size_t)(j + 2) * d + i], vf[j + 2], s2);
-                s3 = fmaf(a.M32T[(size_t)(j + 3) * d + i], vf[j + 3], s3);
+            if (SMEM_M) {
+                for (; j + 3 < hi; j += 4) {
+                    s0 = fmaf(Ms[j * (j + 1) / 2 + i], vf[j], s0);
+                    s1 = fmaf(Ms[(j + 1) * (j + 2) / 2 + i], vf[j + 1], s1);
+                    s2 = fmaf(Ms[(j + 2) * (j + 3) / 2 + i], vf[j + 2], s2);
+                    s3 = fmaf(Ms[(j + 3) * (j + 4) / 2 + i], vf[j + 3], s3);
+                }
+                for (; j < hi; ++j) s0 = fmaf(Ms[j * (j + 1) / 2 + i], vf[j], s0);
+            } else {
+                for (; j + 3 < hi; j += 4) {
+                    s0 = fmaf(a.M32T[(size_t)j * d + i], vf[j], s0);
+                    s1 = fmaf(a.M32T[(size_t)(j + 1) * d + i], vf[j + 1], s1);
+                    s2 = fmaf(a.M32T[(size_t)(j + 2) * d + i], vf[j + 2], s2);
+                    s3 = fmaf(a.M32T[(size_t)(j + 3) * d + i], vf[j + 3], s3);
+                }
+                for (; j < hi; ++j) s0 = fmaf(a.M32T[(size_t)j * d + i], vf[j], s0);
             }
-            for (; j < hi; ++j) s0 = fmaf(a.M32T[(size_t)j * d + i], vf[j], s0);
             vpart[g * d + i] = (s0 + s1) + (s2 + s3);
         }
         __syncthreads();
@@ -551,20 +589,33 @@ __global__ void k_to_f32_transposed(double* __restrict__ M, int d, float* __rest
     }
 }
 
+// M32P = the upper triangle of M (float32, column-major M32T) packed by columns.
+__global__ void k_pack_upper_f32(const float* __restrict__ M32T, int d, float* __restrict__ M32P) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)d * d) return;
+    const int j = (int)(q / d), i = (int)(q % d);
+    if (i <= j) M32P[(int64_t)j * (j + 1) / 2 + i] = M32T[q];
+}
+
 // y = float32 copy of x (n entries).
 __global__ void k_copy_f32(const double* __restrict__ x, int n, float* __restrict__ y) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q < n) y[q] = (float)x[q];
 }
 
-// y = R x (upper triangular, float64, one thread per row)
-__global__ void k_upper_matvec(const double* __restrict__ R, int d, const double* __restrict__ x,
-                               double* __restrict__ y, const double* __restrict__ add) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int j = i; j < d; ++j) s += R[(size_t)i * d + j] * x[j];
-        y[i] = (add ? add[i] : 0.0) + s;
-    }
+// y = add + R x (R upper triangular, float64 row-major): one warp per row,
+// lane l taking columns i + l, i + 32 + l, ..., then a fixed shuffle tree.
+// Rows spread over many SMs: float64 issues slowly on this part.
+__global__ void __launch_bounds__(256) k_upper_matvec(const double* __restrict__ R, int d,
+                                                     const double* __restrict__ x, double* __restrict__ y,
+                                                     const double* __restrict__ add) {
+    const int lane = threadIdx.x & 31;
+    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (i >= d) return;
+    double s = 0.0;
+    for (int j = i + lane; j < d; j += 32) s = fma(R[(size_t)i * d + j], x[j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if (lane == 0) y[i] = (add ? add[i] : 0.0) + s;
 }
 
 }  // namespace cw
@@ -607,6 +658,8 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     const size_t oR = ws.reserve(sizeof(double) * (size_t)d * d);
     const size_t oM = ws.reserve(sizeof(double) * (size_t)d * d);
     const size_t oM32 = ws.reserve(sizeof(float) * (size_t)d * d);
+    const size_t packed_floats = ((size_t)d * (d + 1) / 2 + 3) & ~size_t(3);
+    const size_t oM32P = ws.reserve(sizeof(float) * packed_floats);
     const size_t oc = ws.reserve(sizeof(double) * (size_t)d);
     const size_t ox0 = ws.reserve(sizeof(double) * (size_t)d);
     const size_t oy0 = ws.reserve(sizeof(double) * (size_t)d);
@@ -657,9 +710,15 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
         }
         CW_LAUNCH_CHECK();
     }
+    float* M32P = ws.at<float>(oM32P);
+    {
+        const int64_t dd1 = (int64_t)d * d;
+        CW_PROF("k_pack_upper_f32", stream);
+        k_pack_upper_f32<<<(unsigned)((dd1 + 255) / 256), 256, 0, stream>>>(M32T, d, M32P);
+    }
     {
         CW_PROF("k_upper_matvec", stream);  // x0 = M c: the sketch-and-solve start
-        k_upper_matvec<<<(d + 127) / 128, 128, 0, stream>>>(M, d, c, x0, nullptr);
+        k_upper_matvec<<<(d + 7) / 8, 256, 0, stream>>>(M, d, c, x0, nullptr);
     }
     CW_LAUNCH_CHECK();
     // first pass input: vhat = x0 (float32); y0 = R x0 = c
@@ -683,12 +742,19 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
         pk<<<grid, threads, pass_smem, stream>>>(pa);  // z = A x0 - b
     }
     CW_LAUNCH_CHECK();
-    PostArgs qa{ws.at<float2>(ogp), ws.at<double>(ozp), ws.at<double>(obp), grid, d, M32T, y0,
+    // the post kernel keeps the packed triangle of M in shared memory when it fits
+    const size_t post_smem = sizeof(float) * packed_floats;
+    const bool post_sm = post_smem <= 160 * 1024;
+    auto postk = post_sm ? k_lsqr_post<true> : k_lsqr_post<false>;
+    if (post_sm)
+        CW_CUDA_TRY(cudaFuncSetAttribute(postk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)post_smem));
+    const size_t post_dyn = post_sm ? post_smem : 0;
+    PostArgs qa{ws.at<float2>(ogp), ws.at<double>(ozp), ws.at<double>(obp), grid, d, M32T, M32P, y0,
                 ws.at<double>(ov), ws.at<double>(ow), ws.at<double>(ody), ws.at<double>(og), vhat, state, rtol,
                 max_iter, 1};
     {
         CW_PROF("k_lsqr_post", stream);
-        k_lsqr_post<<<1, 1024, 0, stream>>>(qa);
+        postk<<<1, 1024, post_dyn, stream>>>(qa);
     }
     CW_LAUNCH_CHECK();
     pa.zin = z;
@@ -711,7 +777,7 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
             }
             {
                 CW_PROF("k_lsqr_post", stream);
-                k_lsqr_post<<<1, 1024, 0, stream>>>(qa);
+                postk<<<1, 1024, post_dyn, stream>>>(qa);
             }
         }
         CW_LAUNCH_CHECK();
@@ -720,7 +786,7 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     // x = x0 + M dy
     {
         CW_PROF("k_upper_matvec", stream);
-        k_upper_matvec<<<(d + 127) / 128, 128, 0, stream>>>(M, d, ws.at<double>(ody), x, x0);
+        k_upper_matvec<<<(d + 7) / 8, 256, 0, stream>>>(M, d, ws.at<double>(ody), x, x0);
     }
     CW_LAUNCH_CHECK();
     CW_CUDA_TRY(cudaStreamSynchronize(stream));
