@@ -87,6 +87,7 @@ def parse():
     ap.add_argument("--rows", type=int, default=N_ROWS,
                     help="rows of A (a smaller case of the same workload for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the per-step timings of the other rows")
     ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -327,6 +328,85 @@ def run_reference(args):
     return 0
 
 
+def _timed(fn, stream, reps=3, warm=1):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _stage_ms(cw, names, reps):
+    out = {}
+    for nm in names:
+        cnt, tot = cw.profile_get(nm)
+        if cnt:
+            out[nm] = tot / reps
+    return out
+
+
+def row_timings(cw, A, b, stream, peak):
+    """Per-call times of the method's other steps (CUDA events on the launching
+    stream; per-kernel times from the library's own events).  The dense rows use
+    a Gaussian A of the dense-sketch workload's shape (n = 2^22, d = 512; for
+    timing only: the kernels' work does not depend on the values)."""
+    import torch
+    rows = {}
+    reps = 3
+    SA = torch.empty(M, D, device=A.row_ptr.device)
+    Sb = torch.empty(M, device=A.row_ptr.device)
+    sort_k = ("k_tile_hist", "k_scan_chunk_sums", "k_scan_bins", "k_scan_tiles", "k_coarse_scatter", "k_fine_sort",
+              "k_set_last")
+    cw.profile_reset()
+    cw.profile_enable(True)
+    ms = _timed(lambda: cw.cw_sketch_csr(A, b, M, SEED, SA, Sb), stream, reps=reps, warm=0)
+    cw.profile_enable(False)
+    st = _stage_ms(cw, sort_k + ("k_apply_csr",), reps)
+    rows["A1_A2_hash_sort_ms"] = sum(v for k, v in st.items() if k in sort_k)
+    rows["A3_segmented_sum_ms"] = st.get("k_apply_csr")
+    rows["A1_A3_sketch_csr_ms"] = ms
+    rows["A4_qr_fp64_ms"] = _timed(lambda: cw.cw_qr(SA, Sb), stream, reps=2)
+    rows["A5_sketch_and_solve_ms"] = _timed(lambda: cw.cw_solve_sketch(A, b, M, SEED), stream, reps=2)
+    del SA, Sb
+    # dense rows: n = 2^22, d = 512, m = 65536, k = 32
+    n3, d3, k3 = 1 << 22, 512, 32
+    g = torch.Generator(device=A.row_ptr.device).manual_seed(1003)
+    A3 = torch.randn(n3, d3, device=A.row_ptr.device, generator=g)
+    G3 = torch.randn(d3, k3, device=A.row_ptr.device, dtype=torch.float64, generator=g)
+    SA3 = torch.empty(M, d3, device=A.row_ptr.device)
+    ms = _timed(lambda: cw.cw_sketch_dense(A3, None, M, SEED, SA3), stream, reps=reps)
+    ab = n3 * d3 * 4 + M * d3 * 4
+    rows["A3_sketch_dense_ms"] = ms
+    rows["A3_sketch_dense_GBps"] = ab / (ms / 1000.0) / 1e9
+    rows["A3_sketch_dense_frac"] = rows["A3_sketch_dense_GBps"] / peak
+    del SA3
+    lev_k = ("k_apply_dense_precise", "k_qr_householder", "k_qr_finalize", "k_trsm_upper", "k_leverage")
+    cw.cw_leverage(A3, M, SEED, G3)
+    torch.cuda.synchronize()
+    cw.profile_reset()
+    cw.profile_enable(True)
+    ms = _timed(lambda: cw.cw_leverage(A3, M, SEED, G3), stream, reps=2, warm=0)
+    cw.profile_enable(False)
+    st = _stage_ms(cw, lev_k, 2)
+    rows["A7_leverage_total_ms"] = ms
+    rows["A7_stages_ms"] = st
+    if "k_leverage" in st:
+        lb = n3 * d3 * 4 + n3 * 4
+        rows["A7_leverage_pass_GBps"] = lb / (st["k_leverage"] / 1000.0) / 1e9
+        rows["A7_leverage_pass_frac"] = rows["A7_leverage_pass_GBps"] / peak
+    rows["dense_workload"] = "A: n=2^22 x d=512 float32 N(0,1) (timing only), m=65536, G: 512 x 32, seed 1"
+    del A3, G3
+    torch.cuda.empty_cache()
+    return rows
+
+
 def run_cw(args):
     import torch
     import paper_1207_6365_gb300 as cw
@@ -458,6 +538,10 @@ def run_cw(args):
                "d2h_bytes_per_step": d2h, "steps": esteps, "ms_per_step": ems / esteps}
         del Ad, bd, rp_h, col_h, val_h, b_h
 
+    rows = None
+    if rank == 0 and not args.no_rows:
+        rows = row_timings(cw, A, b, stream, peak)
+
     cpu_baseline = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -482,7 +566,7 @@ def run_cw(args):
                 "sketch": {"ms": sk_ms, "nnz_per_s": nnz / (sk_ms / 1000.0),
                            "alg_GBps": sk_bytes / (sk_ms / 1000.0) / 1e9,
                            "frac_of_peak": sk_bytes / (sk_ms / 1000.0) / 1e9 / peak},
-                "stages": stages}
+                "stages": stages, "rows": rows}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
