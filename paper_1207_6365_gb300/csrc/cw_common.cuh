@@ -152,6 +152,7 @@ enum : unsigned {
     kDevDupColumn = 2u,
     kDevBadRowPtr = 4u,
     kDevNonFinite = 8u,
+    kDevTimeout = 16u,   // a bounded device-side wait gave up
 };
 
 // Per-device status word (allocated once per device, never freed).

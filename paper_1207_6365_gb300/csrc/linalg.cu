@@ -102,9 +102,9 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-__global__ void __launch_bounds__(256) k_qr_householder(QrArgs a) {
+__global__ void __launch_bounds__(1024) k_qr_householder(QrArgs a) {
     extern __shared__ double sv[];  // this block's reflector entries (rows r0..r1)
-    __shared__ double s_red[8];
+    __shared__ double s_red[32];
     const unsigned G = gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int64_t per = (a.m + G - 1) / G;
@@ -155,10 +155,17 @@ __global__ void __launch_bounds__(256) k_qr_householder(QrArgs a) {
         __syncthreads();
         // partial dots v^T W[:, k] for k > j
         for (int k = j + 1 + warp; k < a.nc; k += nwarps) {
-            const double* colk = a.W + (int64_t)k * a.m;
-            double s = 0.0;
-            for (int64_t q = lane; q < rows; q += 32) s += sv[q] * colk[r0 + q];
-            s = warp_sum(s);
+            const double* colk = a.W + (int64_t)k * a.m + r0;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // four independent chains
+            int64_t q = lane;
+            for (; q + 96 < rows; q += 128) {
+                s0 = fma(sv[q], colk[q], s0);
+                s1 = fma(sv[q + 32], colk[q + 32], s1);
+                s2 = fma(sv[q + 64], colk[q + 64], s2);
+                s3 = fma(sv[q + 96], colk[q + 96], s3);
+            }
+            for (; q < rows; q += 32) s0 = fma(sv[q], colk[q], s0);
+            const double s = warp_sum((s0 + s1) + (s2 + s3));
             if (lane == 0) a.dotp[(size_t)blockIdx.x * a.nc + k] = s;
         }
         if (!grid_barrier(a.bar, G, a.tflag)) return;
@@ -173,17 +180,33 @@ __global__ void __launch_bounds__(256) k_qr_householder(QrArgs a) {
         // update W[:, k] -= v * wv[k]; norm of the next column
         double nrm = 0.0;
         for (int k = j + 1 + warp; k < a.nc; k += nwarps) {
-            double* colk = a.W + (int64_t)k * a.m;
+            double* colk = a.W + (int64_t)k * a.m + r0;
             const double wk = a.wv[k];
+            // rows i < j of this block are untouched (sv = 0 there)
             double s = 0.0;
-            for (int64_t q = lane; q < rows; q += 32) {
-                const int64_t i = r0 + q;
-                double x = colk[i];
-                if (i >= j) {
-                    x -= sv[q] * wk;
-                    colk[i] = x;
+            int64_t q = lane;
+            for (; q + 96 < rows; q += 128) {
+                double x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = colk[q + 32 * u];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t i = r0 + q + 32 * u;
+                    if (i >= j) {
+                        x[u] = fma(-sv[q + 32 * u], wk, x[u]);
+                        colk[q + 32 * u] = x[u];
+                    }
+                    if (k == j + 1 && i >= j + 1) s = fma(x[u], x[u], s);
                 }
-                if (k == j + 1 && i >= j + 1) s += x * x;
+            }
+            for (; q < rows; q += 32) {
+                const int64_t i = r0 + q;
+                double x = colk[q];
+                if (i >= j) {
+                    x = fma(-sv[q], wk, x);
+                    colk[q] = x;
+                }
+                if (k == j + 1 && i >= j + 1) s = fma(x, x, s);
             }
             if (k == j + 1) nrm = warp_sum(s);
         }
@@ -956,7 +979,7 @@ int qr_grid(int64_t m, int threads, size_t smem) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_qr_householder, threads, smem) != cudaSuccess)
         per = 1;
     per = per < 1 ? 1 : (per > 2 ? 2 : per);
-    int g = num_sms() * per;
+    int g = num_sms() * per;   // one CTA of 32 warps per SM in practice
     const int64_t want = (m + 63) / 64;  // at least 64 rows per block
     if (want < g) g = (int)(want < 1 ? 1 : want);
     return g;
@@ -970,7 +993,7 @@ int qr_grid(int64_t m, int threads, size_t smem) {
 int qr64(const float* SA, int64_t m, int d, const float* Sb, double* R, double* c, cudaStream_t stream,
          const double* SA64) {
     const int nc = d + (Sb ? 1 : 0);
-    const int threads = 256;
+    const int threads = 1024;
     int G = qr_grid(m, threads, 48 * 1024);
     const size_t smem = sizeof(double) * (size_t)((m + G - 1) / G);
     if (smem > 200 * 1024) return CW_ERR_SHAPE;  // m too large for the resident-grid design

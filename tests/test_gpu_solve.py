@@ -190,8 +190,23 @@ def test_leverage_matches_same_algorithm_ill_conditioned(cw):
     assert 0.8 < np.median(lev / u) < 1.25
 
 
-@pytest.mark.parametrize("n,d,m,k", [(20001, 100, 1024, 32), (5000, 33, 700, 7), (3000, 520, 2048, 40)])
+@pytest.mark.parametrize("n,d,m,k", [(20001, 100, 1024, 32), (5000, 33, 700, 7), (3000, 520, 2048, 40),
+                                     (30001, 200, 2048, 32), (10000, 128, 1024, 7)])
 def test_leverage_shapes(cw, n, d, m, k):
     _, lev, lev_o = _lev_case(cw, n, d, m, k, 1e3, seed=n % 97)
     rel = np.abs(lev - lev_o) / lev_o
     assert rel.max() <= 1e-3, rel.max()
+
+
+def test_leverage_tensor_core_path_runs(cw):
+    """k <= 32 with 16-byte aligned rows takes the tcgen05 kernel; other shapes the CUDA-core one."""
+    cw.profile_reset()
+    cw.profile_enable(True)
+    try:
+        _lev_case(cw, 4097, 96, 1024, 32, 10.0, seed=5)
+        n_tc = cw.profile_get("k_leverage_tc")[0]
+        _lev_case(cw, 4097, 33, 1024, 32, 10.0, seed=5)
+        n_cc = cw.profile_get("k_leverage")[0]
+    finally:
+        cw.profile_enable(False)
+    assert n_tc == 1 and n_cc == 1
