@@ -260,10 +260,16 @@ __global__ void __launch_bounds__(256) k_coarse_scatter(HashParams hp, int64_t i
 // the bin's records by bucket, stable, written to the same region in bucket
 // order as {a | sign << 31 (dense) or a, len | sign << 31 (CSR)} and sigma*b;
 // bucket_ptr for the bin's buckets.  This is the permutation P of Section 5.2.
+//
+// A bin of at most `cap` records is first copied into shared memory (16-byte
+// asynchronous copies, all in flight at once), so both passes over it (count,
+// then scatter) read shared memory and the records cross DRAM once; larger
+// bins are read from global memory twice.
 template <int MODE, bool HAS_B>
 __global__ void __launch_bounds__(512) k_fine_sort(const int4* __restrict__ rec, const uint32_t* __restrict__ coarse_ptr,
-                                                   int64_t m, int gshift, int2* __restrict__ out2,
+                                                   int64_t m, int gshift, int cap, int2* __restrict__ out2,
                                                    float* __restrict__ outb, int32_t* __restrict__ bucket_ptr) {
+    extern __shared__ int4 srec[];   // [cap]
     __shared__ uint32_t cnt[16 * kMaxGroupBuckets];
     __shared__ uint32_t bstart[kMaxGroupBuckets + 1];
     __shared__ uint32_t wsum[32];
@@ -275,13 +281,21 @@ __global__ void __launch_bounds__(512) k_fine_sort(const int4* __restrict__ rec,
     const int64_t b0 = (int64_t)g << gshift;
     const int nb = (int)((m - b0) < (int64_t)G ? (m - b0) : (int64_t)G);
     for (int q = threadIdx.x; q < nwarps * G; q += blockDim.x) cnt[q] = 0;
-    __syncthreads();
     const uint32_t len = r1 - r0;
+    const bool staged = len <= (uint32_t)cap;
+    if (staged) {
+        for (uint32_t k = threadIdx.x; k < len; k += blockDim.x) cp_async16(&srec[k], &rec[r0 + k]);
+        cp_async_commit();
+        cp_async_wait_all();
+    }
+    __syncthreads();
+    // record k (global index) from shared memory when staged
+    auto ldrec = [&](uint32_t k) -> int4 { return staged ? srec[k - r0] : __ldg(&rec[k]); };
     const uint32_t seg = ((len + nwarps - 1) / nwarps + 31) & ~31u;
     const uint32_t s0 = r0 + min(len, seg * warp), s1 = r0 + min(len, seg * (warp + 1));
     uint32_t* wc = cnt + warp * G;
 #pragma unroll 4
-    for (uint32_t k = s0 + lane; k < s1; k += 32) atomicAdd(&wc[(uint32_t)__ldg(&rec[k].x) & (G - 1)], 1u);
+    for (uint32_t k = s0 + lane; k < s1; k += 32) atomicAdd(&wc[(uint32_t)ldrec(k).x & (G - 1)], 1u);
     __syncthreads();
     // bucket totals -> exclusive scan (G <= blockDim)
     uint32_t tot = 0;
@@ -322,7 +336,7 @@ __global__ void __launch_bounds__(512) k_fine_sort(const int4* __restrict__ rec,
 #pragma unroll
       for (int u = 0; u < PF; ++u) {
           const uint32_t k = kb0 + 32 * u + lane;
-          rq[u] = (k < s1) ? __ldg(&rec[k]) : make_int4(0, 0, 0, 0);
+          rq[u] = (k < s1) ? ldrec(k) : make_int4(0, 0, 0, 0);
       }
 #pragma unroll
       for (int u = 0; u < PF; ++u) {
@@ -665,13 +679,18 @@ int ilog2_ceil(uint64_t v) {
 }  // namespace
 
 // Coarse bins: about 1024 (long runs of each bin per 8192-row tile keep the
-// coarse scatter's writes coalesced), at most kMaxBins, at most
-// kMaxGroupBuckets buckets per bin.
+// coarse scatter's writes coalesced), more for large n so that a bin fits the
+// fine sort's shared-memory stage, at most kMaxBins, at most kMaxGroupBuckets
+// buckets per bin.
 int plan_sketch(int mode, int64_t n, int64_t d, int64_t m, SketchPlan* p) {
     const int gmin = ilog2_ceil(((uint64_t)m + kMaxBins - 1) / kMaxBins);
     const int gmax = ilog2_ceil((uint64_t)kMaxGroupBuckets);
     if (gmin > gmax) return CW_ERR_SHAPE;
-    int gs = ilog2_ceil(((uint64_t)m + 1023) / 1024);
+    // about 1024 bins, more (up to kMaxBins) so that a bin averages at most 8192
+    // rows: k_fine_sort then stages whole bins in shared memory
+    uint64_t want_bins = 1024;
+    while (want_bins < (uint64_t)kMaxBins && want_bins * 8192 < (uint64_t)n) want_bins *= 2;
+    int gs = ilog2_ceil(((uint64_t)m + want_bins - 1) / want_bins);
     gs = std::max(gs, gmin);
     gs = std::min(gs, gmax);
     gs = std::min(gs, ilog2_ceil((uint64_t)m));
@@ -785,10 +804,15 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
         CW_PROF("k_coarse_scatter", stream);                                                               \
         kf<<<p.ntiles, 256, k3smem, stream>>>(hp, i0, n, p.gshift, p.nbins, H, row_ptr, b, rec, status);   \
     } while (0)
-#define CW_K4A(MODE, HB)                                                                      \
-    do {                                                                                      \
-        CW_PROF("k_fine_sort", stream);                                                       \
-        k_fine_sort<MODE, HB><<<p.nbins, 512, 0, stream>>>(rec, CP, m, p.gshift, r2, rb, bptr); \
+    // bins of up to fcap records are staged in shared memory by k_fine_sort
+    const int fcap = 12 * 1024;
+    const size_t k4smem = sizeof(int4) * (size_t)fcap;
+#define CW_K4A(MODE, HB)                                                                                \
+    do {                                                                                                \
+        auto kf = k_fine_sort<MODE, HB>;                                                                \
+        CW_CUDA_TRY(set_smem(kf, k4smem));                                                              \
+        CW_PROF("k_fine_sort", stream);                                                                 \
+        kf<<<p.nbins, 512, k4smem, stream>>>(rec, CP, m, p.gshift, fcap, r2, rb, bptr);                 \
     } while (0)
     if (mode == kModeCSR) {
         if (has_b) { CW_K3(kModeCSR, true); CW_K4A(kModeCSR, true); }
