@@ -387,7 +387,8 @@ def row_timings(cw, A, b, stream, peak):
     rows["A3_sketch_dense_GBps"] = ab / (ms / 1000.0) / 1e9
     rows["A3_sketch_dense_frac"] = rows["A3_sketch_dense_GBps"] / peak
     del SA3
-    lev_k = ("k_apply_dense_precise", "k_qr_householder", "k_qr_finalize", "k_trsm_upper", "k_leverage")
+    lev_k = ("k_apply_dense_precise", "k_qr_householder", "k_qr_finalize", "k_trsm_upper", "k_m_digits",
+             "k_leverage_tc", "k_leverage")
     cw.cw_leverage(A3, M, SEED, G3)
     torch.cuda.synchronize()
     cw.profile_reset()
@@ -397,10 +398,15 @@ def row_timings(cw, A, b, stream, peak):
     st = _stage_ms(cw, lev_k, 2)
     rows["A7_leverage_total_ms"] = ms
     rows["A7_stages_ms"] = st
-    if "k_leverage" in st:
+    lk = "k_leverage_tc" if "k_leverage_tc" in st else ("k_leverage" if "k_leverage" in st else None)
+    if lk:
         lb = n3 * d3 * 4 + n3 * 4
-        rows["A7_leverage_pass_GBps"] = lb / (st["k_leverage"] / 1000.0) / 1e9
+        rows["A7_leverage_pass_kernel"] = lk
+        rows["A7_leverage_pass_GBps"] = lb / (st[lk] / 1000.0) / 1e9
         rows["A7_leverage_pass_frac"] = rows["A7_leverage_pass_GBps"] / peak
+        # bf16 products actually issued: 15 digit pairs of 2 n d k flops (tensor path)
+        if lk == "k_leverage_tc":
+            rows["A7_leverage_tc_TFLOPs"] = 15 * 2.0 * n3 * d3 * k3 / (st[lk] / 1000.0) / 1e12
     rows["dense_workload"] = "A: n=2^22 x d=512 float32 N(0,1) (timing only), m=65536, G: 512 x 32, seed 1"
     del A3, G3
     torch.cuda.empty_cache()
