@@ -151,10 +151,10 @@ constexpr int kTcSBO = (kTcK / 8) * 128;           // bytes between core matrice
 constexpr int kTcASlice = kTcRows * kTcK * 2;      // 16 KB per A digit slice
 constexpr int kTcBSlice = kTcN * kTcK * 2;         // 4 KB per M digit slice
 constexpr int kTcBChunk = kTcDig * kTcBSlice;      // 20 KB per chunk of M
-constexpr int kTcRawStride = kTcK + 4;             // floats per staged row (conflict-free 16-byte reads)
+constexpr int kTcRawStride = kTcK + 4;             // floats per staged row of A (conflict-free 16-byte reads)
 constexpr int kTcRaw = kTcRows * kTcRawStride * 4; // bytes per staged chunk of A
 constexpr size_t kTcSmem = (size_t)kTcDig * kTcASlice + 2 * (size_t)kTcRaw + 2 * (size_t)kTcBChunk +
-                           2 * kTcN * sizeof(float);
+                           3 * kTcN * sizeof(float);
 
 // byte offset of element (r, k) in the canonical K-major layout without
 // swizzle: 8 x 8 core matrices of 16-byte rows, LBO along K, SBO along M/N
@@ -219,202 +219,249 @@ struct TcLevArgs {
     unsigned* status;
 };
 
-__global__ void __launch_bounds__(kTcRows) k_leverage_tc(TcLevArgs a) {
+constexpr int kTcWork = 256;               // two threads per row: chunk columns 0..31 / 32..63
+constexpr int kTcThreads = kTcWork + 32;   // plus one warp that issues the MMAs
+
+// Eight working warps and one that issues the MMAs.  Thread t < 256 owns row
+// t % 128 of the tile and half h = t / 128 of each chunk's columns (digits of
+// columns 32h ..) and of the 32 output columns (drain: warp w reads the
+// tensor-memory lanes of rows 32 (w % 4) .., columns 16 (w / 4) ..).  Two
+// tensor-memory accumulator sets alternate, so the MMAs of chunk q run while
+// the working warps drain chunk q - 1; A and the M digits of chunk q + 1 are
+// copied in (cp.async) during chunk q.  (A variant with sixteen working warps,
+// double-buffered digit slices and A prefetched into registers, which also
+// overlaps the digits of chunk q + 1 with the MMAs of chunk q, measured
+// slower: 8.4 against 7.5 ms at n = 2^22, d = 512.)
+__global__ void __launch_bounds__(kTcThreads) k_leverage_tc(TcLevArgs a) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ uint32_t tmem_base;
-    __shared__ __align__(8) uint64_t mbar;
-    unsigned char* sAs = tsm;                                         // kTcDig slices
-    float* sRaw = reinterpret_cast<float*>(tsm + kTcDig * kTcASlice);  // 2 x [128][kTcRawStride]
-    unsigned char* sB = tsm + kTcDig * kTcASlice + 2 * kTcRaw;        // 2 x kTcBChunk
-    float* sCs = reinterpret_cast<float*>(sB + 2 * kTcBChunk);       // 2 x [32]
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t emax_half[2][kTcRows];
+    __shared__ float lev_half[2][kTcRows];
+    unsigned char* sAs = tsm;                                          // kTcDig slices
+    float* sRaw = reinterpret_cast<float*>(tsm + kTcDig * kTcASlice);   // 2 x [128][kTcRawStride]
+    unsigned char* sB = tsm + kTcDig * kTcASlice + 2 * kTcRaw;         // 2 x kTcBChunk
+    // column scales, three sets: step q's are read by its drain during step q + 1,
+    // while the copies for step q + 2 land
+    float* sCs = reinterpret_cast<float*>(sB + 2 * kTcBChunk);        // 3 x [32]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool worker = tid < kTcWork;
+    const int row_t = tid & (kTcRows - 1), half = (tid >> 7) & 1;      // tile row, column half
     const int nchunk = (a.d + kTcK - 1) / kTcK;
     const int64_t ntiles = (a.n + kTcRows - 1) / kTcRows;
     const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int64_t nsteps = my_tiles * nchunk;
 
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc_smem(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc_smem(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc_smem(&mbar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n" ::"r"(tc_smem(&tmem_base)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(tc_smem(&tmem_base)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_base;
+    constexpr uint32_t kTbuf = kTcLev * kTcN;   // 160 columns per accumulator set
 
-    // step q = (tile, chunk): this thread copies its row of the A chunk and a
-    // share of the chunk's M digits and scales
+    auto step_tile = [&](int64_t q) { return blockIdx.x + (q / nchunk) * gridDim.x; };
+    // step q: warp w copies rows 16w .. 16w + 15 of the A chunk (two rows of 256
+    // bytes per instruction) and a share of the chunk's M digits and scales
     auto issue = [&](int64_t q) {
-        const int64_t tile = blockIdx.x + (q / nchunk) * gridDim.x;
+        const int64_t tile = step_tile(q);
         const int c = (int)(q % nchunk);
         const int buf = (int)(q & 1);
-        const int64_t row = tile * kTcRows + tid;
-        float* dst = sRaw + (size_t)buf * kTcRows * kTcRawStride + (size_t)tid * kTcRawStride;
-        const float* src = a.A + row * a.lda + (int64_t)c * kTcK;
+        const int vq = lane & 15;
+        const int col = c * kTcK + 4 * vq;
 #pragma unroll
-        for (int v = 0; v < kTcK / 4; ++v) {
-            const int col = c * kTcK + 4 * v;
-            if (row < a.n && col < a.d) cp_async16(dst + 4 * v, src + 4 * v);
-            else *reinterpret_cast<float4*>(dst + 4 * v) = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int rr = 0; rr < 8; ++rr) {
+            const int rt = warp * 16 + 2 * rr + (lane >> 4);
+            const int64_t row = tile * kTcRows + rt;
+            float* dst = sRaw + (size_t)buf * kTcRows * kTcRawStride + (size_t)rt * kTcRawStride + 4 * vq;
+            if (row < a.n && col < a.d) cp_async16(dst, a.A + row * a.lda + col);
+            else *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const unsigned char* bsrc = reinterpret_cast<const unsigned char*>(a.Bd) + (size_t)c * kTcBChunk;
         unsigned char* bdst = sB + (size_t)buf * kTcBChunk;
-        for (int v = tid; v < kTcBChunk / 16; v += kTcRows) cp_async16(bdst + 16 * v, bsrc + 16 * v);
-        if (tid < kTcN / 4) cp_async16(sCs + buf * kTcN + 4 * tid, a.cs + (size_t)c * kTcN + 4 * tid);
+        for (int v = tid; v < kTcBChunk / 16; v += kTcWork) cp_async16(bdst + 16 * v, bsrc + 16 * v);
+        if (tid < kTcN / 4) cp_async16(sCs + (q % 3) * kTcN + 4 * tid, a.cs + (size_t)c * kTcN + 4 * tid);
+    };
+    auto wait_mma = [&](int64_t q) -> bool {
+        const int b = (int)(q & 1);
+        const uint32_t par = (uint32_t)((q >> 1) & 1);
+        for (int it = 0; it < (1 << 22); ++it) {
+            uint32_t done;
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(tc_smem(&mbar[b])), "r"(par)
+                : "memory");
+            if (__all_sync(0xFFFFFFFFu, done != 0)) return true;
+        }
+        return false;
     };
 
-    float acc_hi[kTcN], acc_lo[kTcN];
+    float acc_hi[16], acc_lo[16];
 #pragma unroll
-    for (int l = 0; l < kTcN; ++l) acc_hi[l] = acc_lo[l] = 0.f;
+    for (int l = 0; l < 16; ++l) acc_hi[l] = acc_lo[l] = 0.f;
+    uint32_t emax = 7, emax_next = 7;   // this row's exponent bound: chunk being drained / being cut
     bool dead = false;
-    if (nsteps > 0) issue(0);
+    if (nsteps > 0 && worker) issue(0);
     cp_async_commit();
-    for (int64_t q = 0; q < nsteps && !dead; ++q) {
-        if (q + 1 < nsteps) issue(q + 1);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncthreads();
-        const int buf = (int)(q & 1);
-        const int c = (int)(q % nchunk);
-        // digits of this thread's row of the chunk
-        const float* raw = sRaw + (size_t)buf * kTcRows * kTcRawStride + (size_t)tid * kTcRawStride;
-        uint32_t emax = 0;
+    for (int64_t q = 0; q <= nsteps; ++q) {
+        if (q < nsteps) {
+            const int buf = (int)(q & 1);
+            if (q + 1 < nsteps && worker) issue(q + 1);
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();
+            const float* raw = sRaw + (size_t)buf * kTcRows * kTcRawStride + (size_t)row_t * kTcRawStride + half * 32;
+            if (worker) {
+                uint32_t em = 0;
 #pragma unroll
-        for (int v = 0; v < kTcK / 4; ++v) {
-            const float4 x = *reinterpret_cast<const float4*>(raw + 4 * v);
-            emax = max(emax, max(max((__float_as_uint(x.x) >> 23) & 0xFF, (__float_as_uint(x.y) >> 23) & 0xFF),
-                                 max((__float_as_uint(x.z) >> 23) & 0xFF, (__float_as_uint(x.w) >> 23) & 0xFF)));
-        }
-        // |A_ij| < 2^E with E = emax - 126; digits of A_ij 2^(7 - E) = A_ij 2^(133 - emax)
-        if (emax < 7) emax = 7;
-        const float sc = __uint_as_float((260u - emax) << 23);
-        for (int kq = 0; kq < kTcK / 8; ++kq) {
-            float x[8];
-            const float4 x0 = *reinterpret_cast<const float4*>(raw + 8 * kq);
-            const float4 x1 = *reinterpret_cast<const float4*>(raw + 8 * kq + 4);
-            x[0] = x0.x * sc; x[1] = x0.y * sc; x[2] = x0.z * sc; x[3] = x0.w * sc;
-            x[4] = x1.x * sc; x[5] = x1.y * sc; x[6] = x1.z * sc; x[7] = x1.w * sc;
-#pragma unroll
-            for (int s = 0; s < kTcDig; ++s) {
-                float dg[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    dg[u] = rintf(x[u]);
-                    x[u] = (x[u] - dg[u]) * 128.f;
+                for (int v = 0; v < 8; ++v) {
+                    const float4 x = *reinterpret_cast<const float4*>(raw + 4 * v);
+                    em = max(em, max(max((__float_as_uint(x.x) >> 23) & 0xFF, (__float_as_uint(x.y) >> 23) & 0xFF),
+                                     max((__float_as_uint(x.z) >> 23) & 0xFF, (__float_as_uint(x.w) >> 23) & 0xFF)));
                 }
-                uint4 pk;
-                __nv_bfloat162 b0 = __floats2bfloat162_rn(dg[0], dg[1]), b1 = __floats2bfloat162_rn(dg[2], dg[3]);
-                __nv_bfloat162 b2 = __floats2bfloat162_rn(dg[4], dg[5]), b3 = __floats2bfloat162_rn(dg[6], dg[7]);
-                pk.x = *reinterpret_cast<uint32_t*>(&b0);
-                pk.y = *reinterpret_cast<uint32_t*>(&b1);
-                pk.z = *reinterpret_cast<uint32_t*>(&b2);
-                pk.w = *reinterpret_cast<uint32_t*>(&b3);
-                *reinterpret_cast<uint4*>(sAs + s * kTcASlice + tc_off(tid, 8 * kq)) = pk;
+                emax_half[half][row_t] = em;
             }
-        }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t a0 = tc_smem(sAs), b0s = tc_smem(sB + (size_t)buf * kTcBChunk);
-            for (int g = 0; g < kTcLev; ++g) {
-                for (int sd = 0; sd <= g; ++sd) {
-                    const int td = g - sd;
-                    if (sd >= kTcDig || td >= kTcDig) continue;
+            __syncthreads();
+            if (worker) {
+                // |A_ij| < 2^E with E = emax - 126; digits of A_ij 2^(7 - E) = A_ij 2^(133 - emax)
+                uint32_t e2 = max(emax_half[0][row_t], emax_half[1][row_t]);
+                if (e2 < 7) e2 = 7;
+                emax_next = e2;
+                const float sc = __uint_as_float((260u - e2) << 23);
 #pragma unroll
-                    for (int ks = 0; ks < kTcK / 16; ++ks) {
-                        const uint64_t ad = tc_desc(a0 + sd * kTcASlice + ks * 2 * kTcLBO);
-                        const uint64_t bd = tc_desc(b0s + td * kTcBSlice + ks * 2 * kTcLBO);
-                        const uint32_t accum = (sd == 0 && ks == 0) ? 0u : 1u;
-                        asm volatile(
-                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + g * kTcN),
-                            "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(accum));
+                for (int kq = 0; kq < 4; ++kq) {
+                    const float4 x0 = *reinterpret_cast<const float4*>(raw + 8 * kq);
+                    const float4 x1 = *reinterpret_cast<const float4*>(raw + 8 * kq + 4);
+                    float x[8] = {x0.x * sc, x0.y * sc, x0.z * sc, x0.w * sc, x1.x * sc, x1.y * sc, x1.z * sc, x1.w * sc};
+#pragma unroll
+                    for (int sd = 0; sd < kTcDig; ++sd) {
+                        // digit = x rounded to the nearest integer by adding and subtracting
+                        // 1.5 * 2^23 (|x| < 2^22; float32 adds round to nearest even); a digit
+                        // (|d| <= 128) is a bf16 exactly: the upper half of its float32 bits
+                        uint32_t db[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const float dg = __fsub_rn(__fadd_rn(x[u], 12582912.f), 12582912.f);
+                            x[u] = (x[u] - dg) * 128.f;
+                            db[u] = __float_as_uint(dg);
+                        }
+                        uint4 pk;
+                        pk.x = __byte_perm(db[0], db[1], 0x7632);
+                        pk.y = __byte_perm(db[2], db[3], 0x7632);
+                        pk.z = __byte_perm(db[4], db[5], 0x7632);
+                        pk.w = __byte_perm(db[6], db[7], 0x7632);
+                        *reinterpret_cast<uint4*>(sAs + sd * kTcASlice + tc_off(row_t, half * 32 + 8 * kq)) = pk;
                     }
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             tc_smem(&mbar))
-                         : "memory");
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncthreads();
+            if (tid == kTcWork) {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t a0 = tc_smem(sAs), b0s = tc_smem(sB + (size_t)buf * kTcBChunk);
+                // The M digit slices lie one after another along N (slice t = rows 32t ..
+                // 32t + 31 of one 160-row operand), so digit slice s of A times the first
+                // 5 - s slices of M lands level s + t in accumulator columns 32 (s + t):
+                // one MMA per (s, K-step) with N = 32 (5 - s) adds every pair of a level
+                // into that level's columns.
+                const uint32_t dbase = tmem + (uint32_t)buf * kTbuf;
+                for (int sd = 0; sd < kTcDig; ++sd) {
+                    const uint32_t nn = (uint32_t)(kTcN * (kTcLev - sd));
+                    const uint32_t idesc = (kTcIdesc & ~(0x3Fu << 17)) | ((nn >> 3) << 17);
+#pragma unroll
+                    for (int ks = 0; ks < kTcK / 16; ++ks) {
+                        const uint64_t ad = tc_desc(a0 + sd * kTcASlice + ks * 2 * kTcLBO);
+                        const uint64_t bd = tc_desc(b0s + ks * 2 * kTcLBO);
+                        const uint32_t accum = (sd == 0 && ks == 0) ? 0u : 1u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dbase + sd * kTcN),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 tc_smem(&mbar[buf]))
+                             : "memory");
+            }
         }
-        {
-            const uint32_t par = (uint32_t)(q & 1);
-            bool ok = false;
-            for (int it = 0; it < (1 << 22); ++it) {
-                uint32_t done;
-                asm volatile(
-                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                    : "=r"(done)
-                    : "r"(tc_smem(&mbar)), "r"(par)
-                    : "memory");
-                if (__all_sync(0xFFFFFFFFu, done != 0)) {
-                    ok = true;
-                    break;
+        if (q >= 1) {
+            // drain step q - 1 (its MMAs were waited for at the end of the previous iteration)
+            const int64_t qp = q - 1;
+            const int bp = (int)(qp & 1);
+            const int cp = (int)(qp % nchunk);
+            if (worker) {
+                // level g of the chunk weighs 2^(E - 7) 2^(F_cl - 7) 128^-g
+                const float rs0 = __uint_as_float((emax - 6u) << 23);   // 2^(E - 7) = 2^(emax - 133)
+                const float* csb = sCs + (qp % 3) * kTcN + half * 16;
+                uint32_t r[kTcLev][16];
+#pragma unroll
+                for (int g = 0; g < kTcLev; ++g) {
+                    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)bp * kTbuf +
+                                           g * kTcN + half * 16;
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                        "[%16];\n"
+                        : "=r"(r[g][0]), "=r"(r[g][1]), "=r"(r[g][2]), "=r"(r[g][3]), "=r"(r[g][4]), "=r"(r[g][5]),
+                          "=r"(r[g][6]), "=r"(r[g][7]), "=r"(r[g][8]), "=r"(r[g][9]), "=r"(r[g][10]), "=r"(r[g][11]),
+                          "=r"(r[g][12]), "=r"(r[g][13]), "=r"(r[g][14]), "=r"(r[g][15])
+                        : "r"(taddr));
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                for (int g = 0; g < kTcLev; ++g) {
+                    const float rsg = rs0 * __uint_as_float((127u - 7u * (uint32_t)g) << 23);   // * 2^-7g
+#pragma unroll
+                    for (int l = 0; l < 16; ++l) {
+                        const float term = (__uint_as_float(r[g][l]) * csb[l]) * rsg;
+                        const float t = acc_hi[l] + term;
+                        const float bpv = t - acc_hi[l];
+                        acc_lo[l] += (acc_hi[l] - (t - bpv)) + (term - bpv);
+                        acc_hi[l] = t;
+                    }
+                }
+                if (cp == nchunk - 1) {
+                    float sum = 0.f;
+#pragma unroll
+                    for (int l = 0; l < 16; ++l) {
+                        const float y = acc_hi[l] + acc_lo[l];
+                        if (half * 16 + l < a.k) sum = fmaf(y, y, sum);
+                        acc_hi[l] = acc_lo[l] = 0.f;
+                    }
+                    lev_half[half][row_t] = sum;
                 }
             }
-            if (!ok) {
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncthreads();
+            if (cp == nchunk - 1 && tid < kTcRows) {
+                const int64_t row = step_tile(qp) * kTcRows + tid;
+                if (row < a.n) a.lev[row] = (lev_half[0][tid] + lev_half[1][tid]) / (float)a.k;
+            }
+        }
+        if (q < nsteps) {
+            if (!wait_mma(q)) {
                 if (lane == 0) {
                     flag_error(a.status, kDevTimeout);
                     atomicExch(a.tflag, 1u);
                 }
                 dead = true;
             }
-        }
-        if (__syncthreads_or(dead)) {
-            dead = true;
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        // drain: this warp's 32 rows, 32 columns of each level accumulator
-        // level g of the chunk weighs 2^(E - 7) 2^(F_cl - 7) 128^-g: column part from
-        // sCs, row part rs0 = 2^(E - 7) = 2^(emax - 133), times 2^-7g
-        const float rs0 = __uint_as_float((emax - 6u) << 23);
-        for (int g = 0; g < kTcLev; ++g) {
-            uint32_t r[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + g * kTcN;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            const float rsg = rs0 * __uint_as_float((127u - 7u * (uint32_t)g) << 23);   // * 2^-7g
-            const float* csb = sCs + buf * kTcN;
-#pragma unroll
-            for (int l = 0; l < kTcN; ++l) {
-                const float term = (__uint_as_float(r[l]) * csb[l]) * rsg;
-                const float t = acc_hi[l] + term;
-                const float bp = t - acc_hi[l];
-                acc_lo[l] += (acc_hi[l] - (t - bp)) + (term - bp);
-                acc_hi[l] = t;
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        if (c == nchunk - 1) {
-            const int64_t tile = blockIdx.x + (q / nchunk) * gridDim.x;
-            const int64_t row = tile * kTcRows + tid;
-            float sum = 0.f;
-#pragma unroll
-            for (int l = 0; l < kTcN; ++l) {
-                const float y = acc_hi[l] + acc_lo[l];
-                if (l < a.k) sum = fmaf(y, y, sum);
-                acc_hi[l] = acc_lo[l] = 0.f;
-            }
-            if (row < a.n) a.lev[row] = sum / (float)a.k;
+            if (__syncthreads_or(dead)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            emax = emax_next;
         }
     }
     cp_async_wait<0>();
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
 }
 
 }  // namespace cw
@@ -474,7 +521,7 @@ extern "C" int cw_leverage(const float* A, int64_t n, int64_t d, int64_t lda, in
             const int grid = (int)(ntiles < num_sms() ? ntiles : num_sms());
             {
                 CW_PROF("k_leverage_tc", stream);
-                k_leverage_tc<<<grid, kTcRows, kTcSmem, stream>>>(ta);
+                k_leverage_tc<<<grid, kTcThreads, kTcSmem, stream>>>(ta);
             }
             CW_LAUNCH_CHECK();
         }
