@@ -222,10 +222,15 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def source_hash():
+# the sources each profiled kernel is built from: a capture stays valid until they change
+KERNEL_SOURCES = {"k_lsqr_pass": ("lsqr.cu", "cw_common.cuh"), "k_apply_csr": ("sketch.cu", "cw_common.cuh")}
+
+
+def source_hash(kernel=None):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1207_6365_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    names = KERNEL_SOURCES.get(kernel) or sorted(os.listdir(csrc))
+    for name in names:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -240,7 +245,7 @@ def ncu_traffic(kernel):
     text = open(path).read()
     mh = re.search(r"source_hash:\s*([0-9a-f]+)", text)
     mt = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not mh or not mt or mh.group(1) != source_hash():
+    if not mh or not mt or mh.group(1) != source_hash(kernel):
         return None
     return float(mt.group(1))
 
