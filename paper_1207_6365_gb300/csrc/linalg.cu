@@ -317,38 +317,52 @@ __global__ void __launch_bounds__(256) k_gram_tile(const float* __restrict__ SA,
     float vacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float sbb = 0.f;
     const int ci0 = ti * kGT, cj0 = tj * kGT;
-    for (int64_t rb = r0; rb < r1; rb += kGK) {
-        if (Sb && ti == tj && threadIdx.x < kGK) Ss[threadIdx.x] = (rb + threadIdx.x < r1) ? Sb[rb + threadIdx.x] : 0.f;
-        // stage: 16 rows x 128 columns of each operand; thread loads 2 x 4 floats per operand
+    // the stage of 16 rows x 128 columns of each operand: a thread holds 2 x 4
+    // floats of each; the next stage's loads are in flight during this one's products
+    float4 va[2], vb[2];
+    float sbv = 0.f;
+    auto load_stage = [&](int64_t rb) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int q = threadIdx.x + 256 * h;   // 0..511 -> (row kk, column quad cq)
             const int kk = q >> 5, cq = (q & 31) * 4;
             const int64_t r = rb + kk;
-            float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = make_float4(0.f, 0.f, 0.f, 0.f);
+            va[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+            vb[h] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (r < r1) {
                 const float* row = SA + r * d;
                 if (vec && ci0 + cq + 3 < d) {
-                    va = *reinterpret_cast<const float4*>(row + ci0 + cq);
+                    va[h] = *reinterpret_cast<const float4*>(row + ci0 + cq);
                 } else {
-                    va.x = ci0 + cq < d ? row[ci0 + cq] : 0.f;
-                    va.y = ci0 + cq + 1 < d ? row[ci0 + cq + 1] : 0.f;
-                    va.z = ci0 + cq + 2 < d ? row[ci0 + cq + 2] : 0.f;
-                    va.w = ci0 + cq + 3 < d ? row[ci0 + cq + 3] : 0.f;
+                    va[h].x = ci0 + cq < d ? row[ci0 + cq] : 0.f;
+                    va[h].y = ci0 + cq + 1 < d ? row[ci0 + cq + 1] : 0.f;
+                    va[h].z = ci0 + cq + 2 < d ? row[ci0 + cq + 2] : 0.f;
+                    va[h].w = ci0 + cq + 3 < d ? row[ci0 + cq + 3] : 0.f;
                 }
                 if (vec && cj0 + cq + 3 < d) {
-                    vb = *reinterpret_cast<const float4*>(row + cj0 + cq);
+                    vb[h] = *reinterpret_cast<const float4*>(row + cj0 + cq);
                 } else {
-                    vb.x = cj0 + cq < d ? row[cj0 + cq] : 0.f;
-                    vb.y = cj0 + cq + 1 < d ? row[cj0 + cq + 1] : 0.f;
-                    vb.z = cj0 + cq + 2 < d ? row[cj0 + cq + 2] : 0.f;
-                    vb.w = cj0 + cq + 3 < d ? row[cj0 + cq + 3] : 0.f;
+                    vb[h].x = cj0 + cq < d ? row[cj0 + cq] : 0.f;
+                    vb[h].y = cj0 + cq + 1 < d ? row[cj0 + cq + 1] : 0.f;
+                    vb[h].z = cj0 + cq + 2 < d ? row[cj0 + cq + 2] : 0.f;
+                    vb[h].w = cj0 + cq + 3 < d ? row[cj0 + cq + 3] : 0.f;
                 }
             }
-            *reinterpret_cast<float4*>(&As[kk][cq]) = va;
-            *reinterpret_cast<float4*>(&Bs[kk][cq]) = vb;
         }
+        if (Sb && ti == tj && threadIdx.x < kGK) sbv = (rb + threadIdx.x < r1) ? Sb[rb + threadIdx.x] : 0.f;
+    };
+    if (r0 < r1) load_stage(r0);
+    for (int64_t rb = r0; rb < r1; rb += kGK) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = threadIdx.x + 256 * h;
+            const int kk = q >> 5, cq = (q & 31) * 4;
+            *reinterpret_cast<float4*>(&As[kk][cq]) = va[h];
+            *reinterpret_cast<float4*>(&Bs[kk][cq]) = vb[h];
+        }
+        if (Sb && ti == tj && threadIdx.x < kGK) Ss[threadIdx.x] = sbv;
         __syncthreads();
+        if (rb + kGK < r1) load_stage(rb + kGK);
 #pragma unroll
         for (int kk = 0; kk < kGK; ++kk) {
             const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
