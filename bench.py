@@ -379,6 +379,11 @@ def row_timings(cw, A, b, stream, peak):
     rows["A1_A3_sketch_csr_ms"] = ms
     rows["A4_qr_fp64_ms"] = _timed(lambda: cw.cw_qr(SA, Sb), stream, reps=2)
     rows["A5_sketch_and_solve_ms"] = _timed(lambda: cw.cw_solve_sketch(A, b, M, SEED), stream, reps=2)
+    # generalized sparse embedding: q = 1024 blocks, v = 16, kappa = 4 (t = 65536 rows, as SA above)
+    gq, gv, gk = 1024, 16, 4
+    rows["N4_general_sketch_ms"] = _timed(lambda: cw.cw_sketch_csr_general(A, b, gq, gv, gk, SEED, SA, Sb), stream,
+                                          reps=reps)
+    rows["N4_general_sketch_config"] = "q=%d, v=%d, kappa=%d on the large sparse matrix" % (gq, gv, gk)
     del SA, Sb
     # dense rows: n = 2^22, d = 512, m = 65536, k = 32
     n3, d3, k3 = 1 << 22, 512, 32

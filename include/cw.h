@@ -130,6 +130,31 @@ int cw_sketch_csr_rows(const cw_csr *A, int64_t i0, const float *b, int64_t m, u
                        float *SA, float *Sb, cw_stream stream);
 
 /*
+ * cw_sketch_csr_general - SA = S A and Sb = S b for a generalized sparse
+ * embedding S (paper Section "Generalized Sparse Embedding Matrices", "The
+ * construction"): an outer hash h: [n] -> [q] groups the rows into q blocks;
+ * block i is multiplied by B^(i), kappa independent v-row sparse embeddings
+ * stacked and each scaled by 1 / sqrt(kappa) (the Kane-Nelson form of
+ * Theorem "general"), so S has t = q * v * kappa rows.
+ * Row i of A with outer bucket h(i) and inner bucket h_b(i), sign s_b(i), of
+ * inner sketch b adds s_b(i) / sqrt(kappa) * A_i to output row
+ * h(i) * v * kappa + b * v + h_b(i).
+ * h is the bucket cubic of `seed` over q buckets (the same function
+ * cw_hash(seed, q) returns); inner sketch b uses the bucket and sign cubics of
+ * seed_b over v buckets, where seed_0, ..., seed_{kappa-1} are the next kappa
+ * raw SplitMix64 outputs after the eight accepted coefficient draws of seed.
+ * A: as cw_sketch_csr.  1 <= q, 1 <= v, q * v <= 2^19, 1 <= kappa <= 4096,
+ * q * v * kappa <= 2^31 - 1.
+ * SA: (q * v * kappa) x d floats, row-major, fully overwritten.
+ * Sb: q * v * kappa floats, overwritten; may be NULL (ignored when b is NULL).
+ * Runs the CSR sketch kappa times (one per inner sketch; O(nnz(A) * kappa)
+ * work, as in Lemma "time"), each pass deterministic as cw_sketch_csr.
+ * Asynchronous.
+ */
+int cw_sketch_csr_general(const cw_csr *A, const float *b, int64_t q, int64_t v, int32_t kappa,
+                          uint64_t seed, float *SA, float *Sb, cw_stream stream);
+
+/*
  * cw_sketch_csr_noalloc - cw_sketch_csr for callers that cannot allocate
  * device memory during the call: code that runs under its own allocator owning
  * the device's memory, latency-critical paths where a pool allocation could

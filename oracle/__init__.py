@@ -14,6 +14,10 @@ Contents, each following the paper passage named in its docstring:
 * ``sketch_csr`` / ``sketch_dense`` / ``sketch_vec``: SA and Sb by the plain
   loop over rows in ascending order, float64 sums (Section 2; Theorem "lin reg"
   sketches A and b with the same S).
+* ``sketch_csr_general`` / ``dense_S_general`` / ``general_seeds``: the
+  generalized sparse embedding (Section "Generalized Sparse Embedding
+  Matrices": blockdiag(B^(1..q)) P with kappa stacked sketches per block), as a
+  row loop in C and as the explicit matrix built block by block.
 * ``qr_r`` / ``solve_sketch``: Householder QR of SA (LAPACK through numpy), R
   normalised to a positive diagonal, then x' = R^-1 Q^T Sb (proof of Theorem
   "renRegAlg": "a QR factorization of SA and then computing R^-1 Q^T SB").
@@ -56,7 +60,7 @@ def build(force=False):
              or os.path.getmtime(_LIBPATH) < os.path.getmtime(_SRC))
     if force or stale:
         tmp = _LIBPATH + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIBPATH)
     return _LIBPATH
 
@@ -71,9 +75,12 @@ def _load():
             lib.orc_hash.argtypes = [_u64, _i64, _i64, _i64, _p, _p]
             lib.orc_sketch_csr.argtypes = [_i64, _i64, _p, _p, _p, _p, _i64, _u64, _i64, _p, _p]
             lib.orc_sketch_dense.argtypes = [_i64, _i64, _i64, _p, _p, _i64, _u64, _i64, _p, _p]
+            lib.orc_seeds_after_coeffs.argtypes = [_u64, _i64, _p]
+            lib.orc_sketch_csr_general.argtypes = [_i64, _i64, _p, _p, _p, _p, _i64, _i64, _i64, _u64, _p, _p]
             lib.orc_csr_matvec.argtypes = [_i64, _p, _p, _p, _p, _p]
             lib.orc_csr_rmatvec.argtypes = [_i64, _i64, _p, _p, _p, _p, _p]
             for f in (lib.orc_coeffs, lib.orc_poly_values, lib.orc_hash, lib.orc_sketch_csr,
+                      lib.orc_seeds_after_coeffs, lib.orc_sketch_csr_general,
                       lib.orc_sketch_dense, lib.orc_csr_matvec, lib.orc_csr_rmatvec):
                 f.restype = None
             _lib = lib
@@ -159,6 +166,57 @@ def sketch_vec(x, m, seed, i0=0):
     x = _np(x, np.float32)
     SA, _ = sketch_dense(x.reshape(-1, 1), None, m, seed, i0)
     return SA[:, 0]
+
+
+# ---------------------------------------------------------------- generalized sparse embedding
+
+def general_seeds(seed, kappa):
+    """Seeds of the kappa inner sketches: the raw SplitMix64 outputs that follow
+    the eight accepted coefficient draws of ``seed``."""
+    out = np.zeros(kappa, dtype=np.uint64)
+    _load().orc_seeds_after_coeffs(_u64(seed), _i64(kappa), _ptr(out))
+    return [int(x) for x in out]
+
+
+def dense_S_general(seed, q, v, kappa, n):
+    """The explicit t x n generalized sparse embedding (t = q v kappa), built as
+    the paper writes it (Section "Generalized Sparse Embedding Matrices", "The
+    construction"): a permutation P that lists the rows of block 1, then block
+    2, ... (h = the bucket map of ``seed`` over q buckets, rows in ascending
+    order within a block), times the block-diagonal matrix of B^(1..q), where
+    B^(i) stacks kappa sparse embeddings (Section 2) Phi_b D_b / sqrt(kappa) of
+    v rows each.  Inner sketch b hashes a row by its index in A.  Tiny n only.
+    """
+    h, _ = hash(seed, q, 0, n)
+    seeds = general_seeds(seed, kappa)
+    order = np.argsort(h, kind="stable")
+    P = np.zeros((n, n))
+    P[np.arange(n), order] = 1.0
+    blocks = []
+    for i in range(q):
+        rows_i = order[h[order] == i]          # rows of A in h^-1(i), ascending
+        Bi = np.zeros((v * kappa, len(rows_i)))
+        for bidx in range(kappa):
+            hb, sb = hash(seeds[bidx], v, 0, n)
+            for c, r in enumerate(rows_i):
+                Bi[bidx * v + hb[r], c] = sb[r] / np.sqrt(kappa)
+        blocks.append(Bi)
+    return sla.block_diag(*blocks) @ P if n > 0 else np.zeros((q * v * kappa, 0))
+
+
+def sketch_csr_general(row_ptr, col, val, d, b, q, v, kappa, seed):
+    """(SA, Sb) of the generalized sparse embedding by the plain row loop (C core)."""
+    row_ptr = _np(row_ptr, np.int32)
+    col = _np(col, np.int32)
+    val = _np(val, np.float32)
+    b = _np(b, np.float32)
+    n = row_ptr.shape[0] - 1
+    t = q * v * kappa
+    SA = np.zeros((t, d))
+    Sb = np.zeros(t) if b is not None else None
+    _load().orc_sketch_csr_general(_i64(n), _i64(d), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(b), _i64(q),
+                                   _i64(v), _i64(kappa), _u64(seed), _ptr(SA), _ptr(Sb))
+    return SA, Sb
 
 
 def csr_matvec(row_ptr, col, val, x):

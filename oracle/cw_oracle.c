@@ -25,7 +25,9 @@
  */
 #include <stdint.h>
 #include <stddef.h>
+#include <stdlib.h>
 #include <string.h>
+#include <math.h>
 
 #define ORC_P ((uint64_t)0x1FFFFFFFFFFFFFFFull) /* 2^61 - 1 */
 
@@ -141,6 +143,63 @@ void orc_sketch_csr(int64_t n, int64_t d, const int32_t *row_ptr, const int32_t 
             SA[h * d + col[k]] += (double)s * (double)val[k];
         if (Sb) Sb[h] += (double)s * (double)b[i];
     }
+}
+
+/*
+ * Seeds of the inner sketches of a generalized sparse embedding: the `count`
+ * raw SplitMix64 outputs that follow the eight accepted coefficient draws of
+ * `seed` in its stream (this build's reading; the paper only asks the inner
+ * sketches B^(i) to be independent of h and of each other).
+ */
+void orc_seeds_after_coeffs(uint64_t seed, int64_t count, uint64_t *out)
+{
+    uint64_t state = seed;
+    int64_t k;
+    int taken = 0;
+    while (taken < 8) {
+        if ((orc_splitmix_next(&state) & ORC_P) != ORC_P) ++taken;
+    }
+    for (k = 0; k < count; ++k) out[k] = orc_splitmix_next(&state);
+}
+
+/*
+ * Generalized sparse embedding (Section "Generalized Sparse Embedding
+ * Matrices", "The construction"), row by row: row i lies in block h(i) of q
+ * (h = the bucket map of `seed` over q buckets); inner sketch b (seed_b, v
+ * buckets) sends it, with sign sigma_b(i) and weight 1 / sqrt(kappa), to row
+ * h(i) * v * kappa + b * v + h_b(i) of the t = q * v * kappa output rows.
+ * SA: t x d float64, Sb: t float64 (skipped when b == NULL), overwritten.
+ */
+void orc_sketch_csr_general(int64_t n, int64_t d, const int32_t *row_ptr, const int32_t *col,
+                            const float *val, const float *b, int64_t q, int64_t v, int64_t kappa,
+                            uint64_t seed, double *SA, double *Sb)
+{
+    orc_poly Pout;
+    int64_t i, k, j;
+    const int64_t t = q * v * kappa;
+    const double w = 1.0 / sqrt((double)kappa);
+    uint64_t *seeds = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)kappa);
+    orc_poly *inner = (orc_poly *)malloc(sizeof(orc_poly) * (size_t)kappa);
+    orc_coefficients(seed, &Pout);
+    orc_seeds_after_coeffs(seed, kappa, seeds);
+    for (j = 0; j < kappa; ++j) orc_coefficients(seeds[j], &inner[j]);
+    memset(SA, 0, sizeof(double) * (size_t)t * (size_t)d);
+    if (Sb) memset(Sb, 0, sizeof(double) * (size_t)t);
+    for (i = 0; i < n; ++i) {
+        int64_t blk, hb;
+        int s0, sb;
+        orc_bucket_sign(&Pout, (uint64_t)i, (uint64_t)q, &blk, &s0);
+        for (j = 0; j < kappa; ++j) {
+            int64_t row;
+            orc_bucket_sign(&inner[j], (uint64_t)i, (uint64_t)v, &hb, &sb);
+            row = blk * v * kappa + j * v + hb;
+            for (k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+                SA[row * d + col[k]] += w * (double)sb * (double)val[k];
+            if (Sb) Sb[row] += w * (double)sb * (double)b[i];
+        }
+    }
+    free(seeds);
+    free(inner);
 }
 
 /* Same for dense row-major A (n x d, leading dimension lda). */

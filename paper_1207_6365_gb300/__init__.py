@@ -18,7 +18,7 @@ from . import _build
 
 __all__ = [
     "CWError", "lib", "load", "status_string", "device_status", "cw_csr_check",
-    "cw_hash", "cw_sketch_csr", "cw_sketch_csr_rows", "cw_sketch_dense", "cw_sketch_vec",
+    "cw_hash", "cw_sketch_csr", "cw_sketch_csr_rows", "cw_sketch_csr_general", "cw_sketch_dense", "cw_sketch_vec",
     "cw_qr", "cw_solve_sketch", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
     "EXPORTS", "HEADER",
 ]
@@ -26,7 +26,8 @@ __all__ = [
 HEADER = os.path.join(_build.ROOT, "include", "cw.h")
 EXPORTS = (
     "cw_status_string", "cw_version", "cw_device_status", "cw_csr_check", "cw_hash", "cw_sketch_csr",
-    "cw_sketch_csr_rows", "cw_sketch_csr_noalloc", "cw_sketch_dense", "cw_sketch_vec", "cw_qr", "cw_solve_sketch",
+    "cw_sketch_csr_rows", "cw_sketch_csr_general", "cw_sketch_csr_noalloc", "cw_sketch_dense", "cw_sketch_vec",
+    "cw_qr", "cw_solve_sketch",
     "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage", "cw_launch_count", "cw_profile_enable",
     "cw_profile_get", "cw_profile_reset",
 )
@@ -55,6 +56,7 @@ _SIGS = {
     "cw_sketch_csr": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_csr_rows": ([ctypes.POINTER(_CSR), _i64, _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_csr_noalloc": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
+    "cw_sketch_csr_general": ([ctypes.POINTER(_CSR), _p, _i64, _i64, _i32, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_dense": ([_p, _i64, _i64, _i64, _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_vec": ([_p, _i64, _i64, _u64, _p, _p], ctypes.c_int),
     "cw_qr": ([_p, _i64, _i64, _p, _p, _p, _p], ctypes.c_int),
@@ -181,6 +183,19 @@ def cw_sketch_csr_rows(A, i0, b, m, seed, SA=None, Sb=None):
     _check(load().cw_sketch_csr_rows(ctypes.byref(c), i0, _ptr(b, torch.float32, "b"), m, seed,
                                      _ptr(SA, torch.float32, "SA"), _ptr(Sb, torch.float32, "Sb"), _stream()),
            "cw_sketch_csr_rows")
+    return SA, Sb
+
+
+def cw_sketch_csr_general(A, b, q, v, kappa, seed, SA=None, Sb=None):
+    dev = A.val.device
+    t = q * v * kappa
+    SA = torch.empty(t, A.d, dtype=torch.float32, device=dev) if SA is None else SA
+    if b is not None and Sb is None:
+        Sb = torch.empty(t, dtype=torch.float32, device=dev)
+    c = _csr(A)
+    _check(load().cw_sketch_csr_general(ctypes.byref(c), _ptr(b, torch.float32, "b"), q, v, kappa, seed,
+                                        _ptr(SA, torch.float32, "SA"), _ptr(Sb, torch.float32, "Sb"),
+                                        _stream()), "cw_sketch_csr_general")
     return SA, Sb
 
 

@@ -28,6 +28,12 @@ struct HashParams {
     uint64_t minv;    // floor((2^64 - 1) / m) for the Barrett remainder
     uint32_t mmask;   // m - 1 when m is a power of two
     uint32_t pow2;    // 1 when m is a power of two
+    // optional outer bucket (generalized sparse embedding): bucket = ho * m + h
+    // with ho = g_outer(x) mod q from a third cubic
+    uint64_t co[4];
+    uint64_t q, qinv;
+    uint32_t qmask, qpow2;
+    uint32_t outer;
 };
 
 // SplitMix64 step as published (state advance by the golden gamma, then the
@@ -57,6 +63,38 @@ inline HashParams make_hash_params(uint64_t seed, int64_t m) {
     hp.minv = ~0ull / (uint64_t)m;
     hp.pow2 = ((uint64_t)m & ((uint64_t)m - 1)) == 0 ? 1u : 0u;
     hp.mmask = hp.pow2 ? (uint32_t)((uint64_t)m - 1) : 0u;
+    for (int k = 0; k < 4; ++k) hp.co[k] = 0;
+    hp.q = 1;
+    hp.qinv = ~0ull;
+    hp.qmask = 0;
+    hp.qpow2 = 1;
+    hp.outer = 0;
+    return hp;
+}
+
+// The next `count` raw SplitMix64 outputs after the 8 accepted coefficient
+// draws of `seed` (the seeds of the inner sketches of a generalized sparse
+// embedding).
+inline void splitmix64_after_coeffs(uint64_t seed, int count, uint64_t* out) {
+    uint64_t st = seed;
+    for (int k = 0; k < 8;) {
+        if ((splitmix64_next(st) & kP61) != kP61) ++k;
+    }
+    for (int k = 0; k < count; ++k) out[k] = splitmix64_next(st);
+}
+
+// Inner sketch b of a generalized sparse embedding: bucket and sign cubics of
+// seed_b (over v buckets), outer bucket cubic = the bucket cubic of `seed`
+// (over q buckets); composite bucket h(i) * v + h_b(i) over q * v buckets.
+inline HashParams make_general_hash_params(uint64_t seed, uint64_t seed_b, int64_t q, int64_t v) {
+    HashParams hp = make_hash_params(seed_b, v);
+    const HashParams ho = make_hash_params(seed, q);
+    for (int k = 0; k < 4; ++k) hp.co[k] = ho.cb[k];
+    hp.q = (uint64_t)q;
+    hp.qinv = ho.minv;
+    hp.qpow2 = ho.pow2;
+    hp.qmask = ho.mmask;
+    hp.outer = 1;
     return hp;
 }
 
@@ -130,19 +168,36 @@ __device__ __forceinline__ uint32_t make_key(uint64_t gb, uint64_t gs, const Has
     return bucket_of(gb, hp) | ((uint32_t)(gs & 1u) << 31);
 }
 
-// Walks both polynomials together and yields keys.
-struct KeyWalk {
-    CubicWalk b, s;
+__device__ __forceinline__ uint32_t outer_bucket_of(uint64_t g, const HashParams& hp) {
+    if (hp.qpow2) return (uint32_t)g & hp.qmask;
+    uint64_t q = __umul64hi(g, hp.qinv);
+    uint64_t r = g - q * hp.q;
+    if (r >= hp.q) r -= hp.q;
+    return (uint32_t)r;
+}
+
+// Walks the polynomials together and yields keys; OUTER adds the outer bucket
+// of a generalized embedding (hp.outer set): key bucket = ho * hp.m + h.
+template <bool OUTER>
+struct KeyWalkT {
+    CubicWalk b, s, o;
     __device__ __forceinline__ void init(const HashParams& hp, uint64_t x0, uint64_t step) {
         b.init(hp.cb, x0, step);
         s.init(hp.cs, x0, step);
+        if (OUTER) o.init(hp.co, x0, step);
     }
-    __device__ __forceinline__ uint32_t key(const HashParams& hp) const { return make_key(b.g, s.g, hp); }
+    __device__ __forceinline__ uint32_t key(const HashParams& hp) const {
+        const uint32_t k = make_key(b.g, s.g, hp);
+        if (!OUTER) return k;
+        return (outer_bucket_of(o.g, hp) * (uint32_t)hp.m + (k & 0x7FFFFFFFu)) | (k & 0x80000000u);
+    }
     __device__ __forceinline__ void step() {
         b.step();
         s.step();
+        if (OUTER) o.step();
     }
 };
+using KeyWalk = KeyWalkT<false>;
 
 // ---------------------------------------------------------------- errors and status
 

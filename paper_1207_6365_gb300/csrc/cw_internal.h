@@ -15,12 +15,23 @@ struct SketchWorkspace {
     unsigned* status;  // device word for the sticky input-error flags
 };
 
+struct HashParams;
+
+// One inner sketch of a generalized sparse embedding (CSR only): its hash
+// (composite bucket over q * v buckets) and where its buckets land: bucket u
+// goes to output row (u / v) * stride + off + u % v, scaled by `scale`.
+struct SketchLayout {
+    const HashParams* hp;
+    int64_t v, stride, off;
+    float scale;
+};
+
 // SA / Sb of a CSR, dense or vector input (see sketch.cu).  With `ext`, all
 // scratch is carved from ext->base (CW_ERR_SHAPE when it does not fit).
 int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const int32_t* row_ptr,
                 const int32_t* col, const float* val, const float* A, const float* b, int64_t m,
                 uint64_t seed, float* SA, float* Sb, int32_t* bucket_ptr_out, cudaStream_t stream,
-                double* SA64 = nullptr, const SketchWorkspace* ext = nullptr);
+                double* SA64 = nullptr, const SketchWorkspace* ext = nullptr, const SketchLayout* lay = nullptr);
 int validate_common(int64_t n, int64_t d, int64_t m);
 
 // float64 Householder QR of [SA | Sb]; synchronises.  SA64 (row-major float64)

@@ -19,6 +19,7 @@
 //                       row is written once.  No global atomics, no floating
 //                       point atomics: results are bitwise reproducible.
 #include <algorithm>
+#include <vector>
 #include <cmath>
 
 #include "cw_common.cuh"
@@ -38,6 +39,7 @@ enum SketchMode { kModeCSR = 0, kModeDense = 1, kModeVec = 2 };
 
 // ---------------------------------------------------------------- K1: tile histograms
 
+template <bool OUTER>
 __global__ void __launch_bounds__(256) k_tile_hist(HashParams hp, int64_t i0, int64_t n, int gshift,
                                                    int nbins, uint32_t* __restrict__ H) {
     __shared__ uint32_t h[kMaxBins];
@@ -46,7 +48,7 @@ __global__ void __launch_bounds__(256) k_tile_hist(HashParams hp, int64_t i0, in
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r0 = (int64_t)blockIdx.x * kTileRows + warp * kTileRowsPerWarp + lane;
     if (r0 < n) {
-        KeyWalk kw;
+        KeyWalkT<OUTER> kw;
         kw.init(hp, (uint64_t)(i0 + r0), 32);
 #pragma unroll 4
         for (int j = 0; j < kTileRowsPerLane; ++j) {
@@ -163,7 +165,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // Per row one 16-byte record {key, a, len, sigma*b}: a = row start (CSR) or
 // the row index (dense); written in coarse-bin order, stable within a bin.
-template <int MODE, bool HAS_B>
+template <int MODE, bool HAS_B, bool OUTER>
 __global__ void __launch_bounds__(256) k_coarse_scatter(HashParams hp, int64_t i0, int64_t n, int gshift,
                                                         int nbins, const uint32_t* __restrict__ O,
                                                         const int32_t* __restrict__ row_ptr,
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(256) k_coarse_scatter(HashParams hp, int64_t i
     uint32_t* wk = skeys + warp * kTileRowsPerWarp;
     uint32_t* wc = cnt + warp * nbins;
     if (r0 < n) {
-        KeyWalk kw;
+        KeyWalkT<OUTER> kw;
         kw.init(hp, (uint64_t)(i0 + r0), 32);
 #pragma unroll 4
         for (int j = 0; j < kTileRowsPerLane; ++j) {
@@ -386,6 +388,10 @@ struct CsrApplyArgs {
     int dpad;
     int acc_global;          // accumulate in the SA row itself (very wide rows)
     int vec4;                // SA rows 16-byte aligned and d % 4 == 0
+    // output row of bucket u: (u / map_v) * map_stride + map_off + u % map_v
+    // (map_v == 0: row u), values times `scale`
+    int64_t map_v, map_stride, map_off;
+    float scale;
 };
 
 // Persistent warps take whole buckets from a counter; sub-warp `sub` of
@@ -405,7 +411,9 @@ __global__ void __launch_bounds__(256) k_apply_csr(CsrApplyArgs a) {
         bk = __shfl_sync(0xFFFFFFFFu, bk, 0);
         if ((int64_t)bk >= a.m) break;
         const int s = a.bucket_ptr[bk], e = a.bucket_ptr[bk + 1];
-        float* SArow = a.SA + (size_t)bk * a.d;
+        const int64_t orow = a.map_v ? ((int64_t)bk / a.map_v) * a.map_stride + a.map_off + (int64_t)bk % a.map_v
+                                     : (int64_t)bk;
+        float* SArow = a.SA + (size_t)orow * a.d;
         float* myacc;
         if (a.acc_global) {
             for (int c = lane; c < a.d; c += 32) SArow[c] = 0.f;
@@ -487,6 +495,7 @@ __global__ void __launch_bounds__(256) k_apply_csr(CsrApplyArgs a) {
                         const float* o = accw + cp * a.dpad + c;
                         v.x += o[0]; v.y += o[1]; v.z += o[2]; v.w += o[3];
                     }
+                    if (a.scale != 1.f) v = make_float4(v.x * a.scale, v.y * a.scale, v.z * a.scale, v.w * a.scale);
                     *reinterpret_cast<float4*>(SArow + c) = v;
                 }
             } else {
@@ -494,11 +503,14 @@ __global__ void __launch_bounds__(256) k_apply_csr(CsrApplyArgs a) {
                     float v = accw[c];
 #pragma unroll
                     for (int cp = 1; cp < COPIES; ++cp) v += accw[cp * a.dpad + c];
-                    SArow[c] = v;
+                    SArow[c] = v * a.scale;
                 }
             }
+        } else if (a.scale != 1.f) {
+            __syncwarp();
+            for (int c = lane; c < a.d; c += 32) SArow[c] *= a.scale;
         }
-        if (HAS_B && a.Sb && lane == 0) a.Sb[bk] = sbacc;
+        if (HAS_B && a.Sb && lane == 0) a.Sb[orow] = sbacc * a.scale;
         __syncwarp();
     }
 }
@@ -739,8 +751,10 @@ static int persistent_grid(F* f, int threads, size_t smem) {
 int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const int32_t* row_ptr,
                 const int32_t* col, const float* val, const float* A, const float* b, int64_t m,
                 uint64_t seed, float* SA, float* Sb, int32_t* bucket_ptr_out, cudaStream_t stream,
-                double* SA64, const SketchWorkspace* ext) {
+                double* SA64, const SketchWorkspace* ext, const SketchLayout* lay) {
     const bool has_b = b != nullptr && (mode == kModeVec || Sb != nullptr);
+    if (lay && mode != kModeCSR) return CW_ERR_ARG;
+    if (n == 0 && lay) return CW_OK;   // the caller zeroed the whole output
     if (n == 0) {
         if (SA && d > 0) CW_CUDA_TRY(cudaMemsetAsync(SA, 0, sizeof(float) * (size_t)m * (size_t)d, stream));
         if (SA64 && d > 0) CW_CUDA_TRY(cudaMemsetAsync(SA64, 0, sizeof(double) * (size_t)m * (size_t)d, stream));
@@ -753,7 +767,7 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     if (st != CW_OK) return st;
     unsigned* status = ext ? ext->status : device_status_word();
     if (!status) return CW_ERR_CUDA;
-    const HashParams hp = make_hash_params(seed, m);
+    const HashParams hp = lay ? *lay->hp : make_hash_params(seed, m);
 
     Scratch ws = ext ? Scratch(stream, ext->base, ext->bytes) : Scratch(stream);
     const size_t oH = ws.reserve(sizeof(uint32_t) * (size_t)p.ntiles * p.nbins);
@@ -778,7 +792,10 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
 
     {
         CW_PROF("k_tile_hist", stream);
-        k_tile_hist<<<p.ntiles, 256, 0, stream>>>(hp, i0, n, p.gshift, p.nbins, H);
+        if (hp.outer)
+            k_tile_hist<true><<<p.ntiles, 256, 0, stream>>>(hp, i0, n, p.gshift, p.nbins, H);
+        else
+            k_tile_hist<false><<<p.ntiles, 256, 0, stream>>>(hp, i0, n, p.gshift, p.nbins, H);
     }
     CW_LAUNCH_CHECK();
     dim3 sg((p.nbins + 255) / 256, p.nchunks);
@@ -799,7 +816,8 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     const size_t k3smem = sizeof(uint32_t) * (size_t)kTileWarps * (p.nbins + kTileRowsPerWarp);
 #define CW_K3(MODE, HB)                                                                                    \
     do {                                                                                                   \
-        auto kf = k_coarse_scatter<MODE, HB>;                                                              \
+        auto kf = k_coarse_scatter<MODE, HB, false>;                                                       \
+        if (MODE == kModeCSR && hp.outer) kf = k_coarse_scatter<MODE, HB, (MODE == kModeCSR)>;             \
         CW_CUDA_TRY(set_smem(kf, k3smem));                                                                 \
         CW_PROF("k_coarse_scatter", stream);                                                               \
         kf<<<p.ntiles, 256, k3smem, stream>>>(hp, i0, n, p.gshift, p.nbins, H, row_ptr, b, rec, status);   \
@@ -836,7 +854,8 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     if (mode == kModeCSR) {
         const bool vec4 = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(SA) & 15) == 0);
         CsrApplyArgs a{r2, rb, bptr, col, val, SA, Sb, counter, status, m, (int)d, p.dpad, p.acc_global,
-                       vec4 ? 1 : 0};
+                       vec4 ? 1 : 0, lay ? lay->v : 0, lay ? lay->stride : 0, lay ? lay->off : 0,
+                       lay ? lay->scale : 1.f};
 #define CW_K4C(LPR, HB)                                                   \
     do {                                                                  \
         auto kf = k_apply_csr<LPR, 8, HB>;                                \
@@ -917,6 +936,44 @@ extern "C" int cw_sketch_csr_rows(const cw_csr* A, int64_t i0, const float* b, i
 extern "C" int cw_sketch_csr(const cw_csr* A, const float* b, int64_t m, uint64_t seed, float* SA, float* Sb,
                              cw_stream stream) {
     return cw_sketch_csr_rows(A, 0, b, m, seed, SA, Sb, stream);
+}
+
+// Generalized sparse embedding (Section "Generalized Sparse Embedding
+// Matrices"): one pass of the CSR sketch per inner sketch b = 0..kappa-1 with
+// the composite bucket h(i) * v + h_b(i) over q * v buckets; bucket u of pass
+// b lands in output row (u / v) * v * kappa + b * v + u % v, scaled by
+// 1 / sqrt(kappa).  The passes write disjoint rows and every row of the
+// q * v * kappa output is written once.
+extern "C" int cw_sketch_csr_general(const cw_csr* A, const float* b, int64_t q, int64_t v, int32_t kappa,
+                                     uint64_t seed, float* SA, float* Sb, cw_stream stream) {
+    if (!A || !SA) return CW_ERR_ARG;
+    if (q < 1 || v < 1 || kappa < 1 || kappa > 4096) return CW_ERR_SHAPE;
+    if (q > (1ll << 19) || v > (1ll << 19) || q * v > (1ll << 19)) return CW_ERR_SHAPE;
+    const int64_t rows = q * v * (int64_t)kappa;
+    if (rows > 0x7FFFFFFFll) return CW_ERR_OVERFLOW;
+    int st = validate_common(A->n, A->d, q * v);
+    if (st != CW_OK) return st;
+    if (A->d < 1) return CW_ERR_SHAPE;
+    if (A->nnz < 0 || A->nnz > 0x7FFFFFFFll) return CW_ERR_OVERFLOW;
+    if (A->n > 0 && (!A->row_ptr || (A->nnz > 0 && (!A->col || !A->val)))) return CW_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    float* sb = b ? Sb : nullptr;
+    if (A->n == 0) {
+        CW_CUDA_TRY(cudaMemsetAsync(SA, 0, sizeof(float) * (size_t)rows * (size_t)A->d, s));
+        if (sb) CW_CUDA_TRY(cudaMemsetAsync(sb, 0, sizeof(float) * (size_t)rows, s));
+        return CW_OK;
+    }
+    std::vector<uint64_t> seeds((size_t)kappa);
+    splitmix64_after_coeffs(seed, kappa, seeds.data());
+    const float scale = (float)(1.0 / std::sqrt((double)kappa));
+    for (int32_t pb = 0; pb < kappa; ++pb) {
+        const HashParams hp = make_general_hash_params(seed, seeds[(size_t)pb], q, v);
+        const SketchLayout lay{&hp, v, v * (int64_t)kappa, (int64_t)pb * v, scale};
+        st = sketch_impl(kModeCSR, A->n, A->d, 0, 0, A->row_ptr, A->col, A->val, nullptr, b, q * v, seed, SA, sb,
+                         nullptr, s, nullptr, nullptr, &lay);
+        if (st != CW_OK) return st;
+    }
+    return CW_OK;
 }
 
 extern "C" int cw_sketch_dense(const float* A, int64_t n, int64_t d, int64_t lda, const float* b, int64_t m,

@@ -23,7 +23,7 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for n in ("cw_sketch_csr", "cw_sketch_dense", "cw_sketch_vec", "cw_solve_sketch", "cw_lsqr_precond",
-              "cw_leverage", "cw_hash", "cw_qr"):
+              "cw_leverage", "cw_hash", "cw_qr", "cw_sketch_csr_general"):
         assert n in names
 
 
@@ -56,6 +56,13 @@ def test_host_side_validation_rejects_bad_arguments():
     assert lib.cw_sketch_csr(ctypes.byref(c), null, 1 << 20, 1, ctypes.c_void_p(16), null, null) == -2
     c.nnz = 2**31
     assert lib.cw_sketch_csr(ctypes.byref(c), null, 8, 1, ctypes.c_void_p(16), null, null) == -3
+    c.nnz = 10
+    assert lib.cw_sketch_csr_general(ctypes.byref(c), null, 1 << 10, 1 << 10, 1, 1, ctypes.c_void_p(16), null,
+                                     null) == -2
+    assert lib.cw_sketch_csr_general(ctypes.byref(c), null, 4, 4, 0, 1, ctypes.c_void_p(16), null, null) == -2
+    assert lib.cw_sketch_csr_general(ctypes.byref(c), null, 1 << 19, 1, 4096, 1, ctypes.c_void_p(16), null,
+                                     null) == -3
+    assert lib.cw_sketch_csr_general(null, null, 4, 4, 1, 1, null, null, null) == -1
     assert lib.cw_sketch_dense(null, 10, 4, 2, null, 8, 1, ctypes.c_void_p(16), null, null) == -1
     assert lib.cw_sketch_dense(ctypes.c_void_p(16), 10, 4, 2, null, 8, 1, ctypes.c_void_p(16), null, null) == -2
     assert lib.cw_qr(ctypes.c_void_p(16), 4, 8, null, null, null, null) == -2
