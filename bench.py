@@ -88,6 +88,7 @@ def parse():
                     help="rows of A (a smaller case of the same workload for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-step timings of the other rows")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-regression row")
     ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -423,6 +424,61 @@ def row_timings(cw, A, b, stream, peak):
     return rows
 
 
+def batch_timings(cw, stream, count=512):
+    """The batched workload: 512 CSR problems, n log-uniform in [2^12, 2^18],
+    d in {16, 32, 64, 128}, 4-32 distinct uniform columns per row, N(0,1),
+    m = 4 d^2, seeds 1..512.  Times the batch (one graph launch: batched sketch
+    and one persistent solve kernel, autotuned) and the same problems solved
+    one at a time with cw_solve_sketch, both with CUDA events on the stream."""
+    import torch
+    import workloads as W
+    shapes = W.batch_shapes(count, seed=1)
+    probs = []
+    for sh in shapes:
+        A, b = W.batch_problem(sh, device="cuda")
+        probs.append((A, b, sh["m"], sh["seed"]))
+    torch.cuda.synchronize()
+    out = {"N1_workload": "%d CSR problems: n log-uniform in [2^12, 2^18] (total %d rows, %d nnz), d in "
+                          "{16, 32, 64, 128}, 4-32 distinct uniform columns per row, N(0,1) values, "
+                          "b = A x0 + 0.1 noise, m = 4 d^2, seeds 1..%d"
+                          % (count, sum(p[0].n for p in probs), sum(int(p[0].col.numel()) for p in probs), count)}
+    B = cw.Batch(probs, autotune=True)
+    out["N1_plan"] = B.info()
+    B.run()
+    st = B.finish()
+    out["N1_status_counts"] = {str(k): st.count(k) for k in sorted(set(st))}
+    l0 = cw.launch_count()
+    ms = _timed(B.run, stream, reps=5, warm=1)
+    out["N1_batched_ms"] = ms
+    out["N1_batched_launches_per_call"] = (cw.launch_count() - l0) / 6
+    out["N1_batched_problems_per_s"] = count / (ms / 1000.0)
+    out["N1_solve_phases_ms"] = B.phases()
+    B.close()
+    # per-stage times from a direct-launch plan (the graph hides its kernels)
+    E = cw.Batch(probs, eager=True)
+    E.run()
+    E.finish()
+    torch.cuda.synchronize()
+    cw.profile_reset()
+    cw.profile_enable(True)
+    E.run()
+    torch.cuda.synchronize()
+    cw.profile_enable(False)
+    names = ("kb_tile_hist", "kb_scan_chunk_sums", "kb_scan_bins", "kb_scan_tiles", "kb_coarse_scatter",
+             "kb_fine_sort", "kb_set_last", "kb_apply_csr", "k_batch_solve")
+    out["N1_stages_ms"] = _stage_ms(cw, names, 1)
+    E.close()
+    # one problem at a time through the single-problem API
+    def one_by_one():
+        for A, b, m, seed in probs:
+            cw.cw_solve_sketch(A, b, m, seed)
+    out["N1_one_at_a_time_ms"] = _timed(one_by_one, stream, reps=1, warm=1)
+    out["N1_speedup"] = out["N1_one_at_a_time_ms"] / out["N1_batched_ms"]
+    del probs
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_cw(args):
     import torch
     import paper_1207_6365_gb300 as cw
@@ -557,6 +613,8 @@ def run_cw(args):
     rows = None
     if rank == 0 and not args.no_rows:
         rows = row_timings(cw, A, b, stream, peak)
+        if not args.no_batch:
+            rows.update(batch_timings(cw, stream))
 
     cpu_baseline = None
     if rank == 0 and not args.no_cpu_baseline:

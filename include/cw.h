@@ -155,6 +155,86 @@ int cw_sketch_csr_general(const cw_csr *A, const float *b, int64_t q, int64_t v,
                           uint64_t seed, float *SA, float *Sb, cw_stream stream);
 
 /*
+ * Batched sketch-and-solve: many independent regressions of uneven size
+ * solved by one graph launch.  Problem p gives x'_p = argmin ||S_p A_p x -
+ * S_p b_p|| (Theorem "lin reg"), S_p the sparse embedding of Section 2 with
+ * its own m_p and seed_p (the same S_p cw_sketch_csr(A_p, b_p, m_p, seed_p)
+ * applies), solved through R of a QR factorisation of S_p A_p (proof of
+ * Theorem "renRegAlg").
+ *
+ * cw_batch_problem: A (device CSR, 1 <= d <= 128, n and nnz as for
+ * cw_sketch_csr), b (device, n floats), m (d <= m <= 2^19), seed, x (device,
+ * d doubles: the result), SA (device m x d floats) and Sb (device m floats):
+ * where S_p A_p and S_p b_p are written, or NULL to keep them in memory the
+ * plan owns.
+ */
+typedef struct {
+    cw_csr A;
+    const float *b;
+    int64_t m;
+    uint64_t seed;
+    double *x;
+    float *SA;
+    float *Sb;
+} cw_batch_problem;
+
+typedef struct cw_batch cw_batch; /* opaque plan */
+
+#define CW_BATCH_AUTOTUNE 1 /* time slab sizes and CTAs per SM on this batch */
+#define CW_BATCH_EAGER 2    /* launch the kernels directly instead of a CUDA graph */
+
+/*
+ * cw_batch_create - plan a batch of `count` problems (host array; the device
+ * arrays it points to must stay valid and at the same addresses for the life
+ * of the plan, since the graph reads them there).  Allocates the plan's
+ * device memory (scratch, and SA / Sb where NULL), uploads the descriptors and
+ * captures the batch in a CUDA graph: the batched sketch (eight launches over
+ * all problems) and one persistent cooperative solve kernel.  With
+ * CW_BATCH_AUTOTUNE, times slab sizes {512, 1024, 2048, 4096} x {1, 2} CTAs
+ * per SM on the batch (running it) and keeps the fastest; the choice is
+ * appended to the file named by the CW_TUNE_CACHE environment variable when
+ * set, and read back from it for the same shapes.  Synchronises `stream`.
+ * Errors: CW_ERR_ARG (NULL pointers), CW_ERR_SHAPE (a problem outside the
+ * limits above), CW_ERR_OVERFLOW, CW_ERR_CUDA; *plan is NULL then.
+ */
+int cw_batch_create(const cw_batch_problem *probs, int32_t count, int32_t flags, cw_stream stream,
+                    cw_batch **plan);
+
+/* cw_batch_run - solve the whole batch once (one graph launch).  Asynchronous. */
+int cw_batch_run(cw_batch *plan, cw_stream stream);
+
+/*
+ * cw_batch_finish - wait for the batch and read each problem's status into
+ * `status` (host, count ints, or NULL): 0 solved in the batch, 3 re-solved by
+ * the float64 Householder QR because the batch's Cholesky factor failed or
+ * its refinement did not converge, 4 S_p A_p numerically rank deficient (the
+ * QR found it so; x_p is set to zero).  *fallbacks (or NULL) = how many went
+ * to the QR.  Returns CW_ERR_TIMEOUT if a grid barrier gave up, CW_ERR_ARG for
+ * input errors the sketch kernels flagged.  Synchronises `stream`.
+ */
+int cw_batch_finish(cw_batch *plan, cw_stream stream, int32_t *status, int32_t *fallbacks);
+
+/*
+ * cw_batch_info - info[0..7] = slab rows, CTAs per SM, solve grid, graph in
+ * use (1) or direct launches (0), work units, tuned (1 timed, 2 from the
+ * cache, 0 defaults), plan device bytes, refinement steps.
+ */
+int cw_batch_info(const cw_batch *plan, int64_t *info);
+
+/*
+ * cw_batch_phases - durations (ms, from the device's global timer) of the
+ * solve kernel's phases in the last completed run: [0] Gram units, [1]
+ * Cholesky and x0, then for each refinement step the residual units and the
+ * corrections (a converged problem skips later steps; a step with nothing to
+ * do takes only its barrier).  Writes at most `max` values and returns how many
+ * (2 + 2 * steps), or a negative status.  Synchronises `stream`.
+ */
+int cw_batch_phases(const cw_batch *plan, cw_stream stream, double *ms, int32_t max);
+
+/* cw_batch_destroy - free the plan (NULL is allowed). */
+int cw_batch_destroy(cw_batch *plan);
+
+/*
  * cw_sketch_csr_noalloc - cw_sketch_csr for callers that cannot allocate
  * device memory during the call: code that runs under its own allocator owning
  * the device's memory, latency-critical paths where a pool allocation could

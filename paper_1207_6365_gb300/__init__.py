@@ -20,16 +20,16 @@ __all__ = [
     "CWError", "lib", "load", "status_string", "device_status", "cw_csr_check",
     "cw_hash", "cw_sketch_csr", "cw_sketch_csr_rows", "cw_sketch_csr_general", "cw_sketch_dense", "cw_sketch_vec",
     "cw_qr", "cw_solve_sketch", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
-    "EXPORTS", "HEADER",
+    "Batch", "EXPORTS", "HEADER",
 ]
 
 HEADER = os.path.join(_build.ROOT, "include", "cw.h")
 EXPORTS = (
     "cw_status_string", "cw_version", "cw_device_status", "cw_csr_check", "cw_hash", "cw_sketch_csr",
     "cw_sketch_csr_rows", "cw_sketch_csr_general", "cw_sketch_csr_noalloc", "cw_sketch_dense", "cw_sketch_vec",
-    "cw_qr", "cw_solve_sketch",
-    "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage", "cw_launch_count", "cw_profile_enable",
-    "cw_profile_get", "cw_profile_reset",
+    "cw_qr", "cw_solve_sketch", "cw_batch_create", "cw_batch_run", "cw_batch_finish", "cw_batch_info",
+    "cw_batch_phases", "cw_batch_destroy", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
+    "cw_launch_count", "cw_profile_enable", "cw_profile_get", "cw_profile_reset",
 )
 
 
@@ -44,6 +44,15 @@ class _CSR(ctypes.Structure):
                 ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
 
 
+class _BatchProblem(ctypes.Structure):
+    _fields_ = [("A", _CSR), ("b", ctypes.c_void_p), ("m", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("x", ctypes.c_void_p), ("SA", ctypes.c_void_p), ("Sb", ctypes.c_void_p)]
+
+
+BATCH_AUTOTUNE = 1
+BATCH_EAGER = 2
+
+
 _lock = threading.Lock()
 _lib = None
 _i64, _u64, _i32, _f64, _p = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
@@ -56,6 +65,12 @@ _SIGS = {
     "cw_sketch_csr": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_csr_rows": ([ctypes.POINTER(_CSR), _i64, _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_csr_noalloc": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
+    "cw_batch_create": ([_p, _i32, _i32, _p, _p], ctypes.c_int),
+    "cw_batch_run": ([_p, _p], ctypes.c_int),
+    "cw_batch_finish": ([_p, _p, _p, _p], ctypes.c_int),
+    "cw_batch_info": ([_p, _p], ctypes.c_int),
+    "cw_batch_phases": ([_p, _p, _p, _i32], ctypes.c_int),
+    "cw_batch_destroy": ([_p], ctypes.c_int),
     "cw_sketch_csr_general": ([ctypes.POINTER(_CSR), _p, _i64, _i64, _i32, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_dense": ([_p, _i64, _i64, _i64, _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_vec": ([_p, _i64, _i64, _u64, _p, _p], ctypes.c_int),
@@ -241,6 +256,83 @@ def cw_solve_sketch(A, b, m, seed, want_R=False):
                                   _ptr(x, torch.float64, "x"), _ptr(R, torch.float64, "R"), _stream()),
            "cw_solve_sketch")
     return (x, R) if want_R else x
+
+
+class Batch:
+    """A plan for many independent sketch-and-solve problems (cw_batch_*).
+
+    problems: list of (A, b, m, seed) with A a CUDA CSR (n, d, row_ptr, col,
+    val) and b a CUDA float32 vector; the tensors must stay alive and in place
+    while the plan exists.  ``keep_sketch`` gives each problem its own SA / Sb
+    tensors (``self.SA[p]``, ``self.Sb[p]``).  ``run()`` launches the batch;
+    ``finish()`` waits and returns the per-problem status list.  ``x[p]`` is
+    problem p's float64 solution.
+    """
+
+    def __init__(self, problems, autotune=False, eager=False, keep_sketch=False):
+        lib = load()
+        self._lib = lib
+        self._plan = ctypes.c_void_p(None)
+        self._keep = []
+        self.x, self.SA, self.Sb = [], [], []
+        arr = (_BatchProblem * len(problems))()
+        for i, (A, b, m, seed) in enumerate(problems):
+            dev = A.val.device
+            x = torch.zeros(A.d, dtype=torch.float64, device=dev)
+            self.x.append(x)
+            SA = torch.empty(m, A.d, dtype=torch.float32, device=dev) if keep_sketch else None
+            Sb = torch.empty(m, dtype=torch.float32, device=dev) if keep_sketch else None
+            self.SA.append(SA)
+            self.Sb.append(Sb)
+            arr[i].A = _csr(A)
+            arr[i].b = _ptr(b, torch.float32, "b")
+            arr[i].m = int(m)
+            arr[i].seed = int(seed)
+            arr[i].x = _ptr(x, torch.float64, "x")
+            arr[i].SA = _ptr(SA, torch.float32, "SA")
+            arr[i].Sb = _ptr(Sb, torch.float32, "Sb")
+            self._keep.append((A, b))
+        flags = (BATCH_AUTOTUNE if autotune else 0) | (BATCH_EAGER if eager else 0)
+        _check(lib.cw_batch_create(arr, len(problems), flags, _stream(), ctypes.byref(self._plan)),
+               "cw_batch_create")
+        self.count = len(problems)
+
+    def run(self):
+        _check(self._lib.cw_batch_run(self._plan, _stream()), "cw_batch_run")
+
+    def finish(self):
+        st = (ctypes.c_int32 * self.count)()
+        fb = ctypes.c_int32(0)
+        _check(self._lib.cw_batch_finish(self._plan, _stream(), st, ctypes.byref(fb)), "cw_batch_finish")
+        return list(st)
+
+    def info(self):
+        v = (ctypes.c_int64 * 8)()
+        _check(self._lib.cw_batch_info(self._plan, v), "cw_batch_info")
+        keys = ("slab", "ctas_per_sm", "grid", "graph", "units", "tuned", "device_bytes", "steps")
+        return dict(zip(keys, [int(t) for t in v]))
+
+    def phases(self):
+        """Phase durations (ms) of the last completed run of the solve kernel."""
+        v = (ctypes.c_double * 32)()
+        k = self._lib.cw_batch_phases(self._plan, _stream(), v, 32)
+        if k < 0:
+            _check(k, "cw_batch_phases")
+        names = ["gram", "cholesky"]
+        for s in range((k - 2) // 2):
+            names += ["residual_%d" % s, "correction_%d" % s]
+        return dict(zip(names, [float(v[i]) for i in range(k)]))
+
+    def close(self):
+        if self._plan:
+            self._lib.cw_batch_destroy(self._plan)
+            self._plan = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cw_solve_sketch_dense(A, b, m, seed, want_R=False):

@@ -318,6 +318,42 @@ class Scratch {
     size_t ext_bytes_ = 0;
 };
 
+// ---------------------------------------------------------------- bounded grid barrier
+
+constexpr long long kBarrierSpinLimit = 1ll << 24;  // ~1 s with 64 ns sleeps
+
+// bar[0] = arrival count, bar[1] = generation.  Returns false (after flagging
+// the status word) when the wait exceeded its limit; the caller must return.
+static __device__ __noinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* timeout_flag) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        __threadfence();
+        const unsigned gen = atomicAdd(&bar[1], 0u);
+        const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
+        if (arrived == nblocks) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            long long it = 0;
+            while (atomicAdd(&bar[1], 0u) == gen) {
+                __nanosleep(64);
+                if (++it > kBarrierSpinLimit) {
+                    atomicExch(timeout_flag, 1u);
+                    ok = 0;
+                    break;
+                }
+            }
+            if (ok && atomicAdd(timeout_flag, 0u)) ok = 0;
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
 inline int num_sms() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);

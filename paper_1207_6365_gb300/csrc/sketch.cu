@@ -22,6 +22,7 @@
 #include <vector>
 #include <cmath>
 
+#include "batch.h"
 #include "cw_common.cuh"
 #include "cw_internal.h"
 
@@ -39,14 +40,15 @@ enum SketchMode { kModeCSR = 0, kModeDense = 1, kModeVec = 2 };
 
 // ---------------------------------------------------------------- K1: tile histograms
 
+// Histogram of one 8192-row tile (rows r of [tile * 8192, ...) < n, hashed
+// with global index i0 + r) over the coarse bins, written to Hrow[0..nbins).
 template <bool OUTER>
-__global__ void __launch_bounds__(256) k_tile_hist(HashParams hp, int64_t i0, int64_t n, int gshift,
-                                                   int nbins, uint32_t* __restrict__ H) {
-    __shared__ uint32_t h[kMaxBins];
+__device__ __forceinline__ void tile_hist_body(const HashParams& hp, int64_t i0, int64_t n, int gshift, int nbins,
+                                               int64_t tile, uint32_t* __restrict__ Hrow, uint32_t* h) {
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r0 = (int64_t)blockIdx.x * kTileRows + warp * kTileRowsPerWarp + lane;
+    const int64_t r0 = tile * kTileRows + warp * kTileRowsPerWarp + lane;
     if (r0 < n) {
         KeyWalkT<OUTER> kw;
         kw.init(hp, (uint64_t)(i0 + r0), 32);
@@ -59,16 +61,21 @@ __global__ void __launch_bounds__(256) k_tile_hist(HashParams hp, int64_t i0, in
         }
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < nbins; b += blockDim.x) H[(size_t)blockIdx.x * nbins + b] = h[b];
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) Hrow[b] = h[b];
+}
+
+template <bool OUTER>
+__global__ void __launch_bounds__(256) k_tile_hist(HashParams hp, int64_t i0, int64_t n, int gshift,
+                                                   int nbins, uint32_t* __restrict__ H) {
+    __shared__ uint32_t h[kMaxBins];
+    tile_hist_body<OUTER>(hp, i0, n, gshift, nbins, blockIdx.x, H + (size_t)blockIdx.x * nbins, h);
 }
 
 // ---------------------------------------------------------------- S1-S3: scan of H (bin-major order)
 
 // P[c][b] = sum of H[t][b] over tiles t of chunk c.
-__global__ void k_scan_chunk_sums(const uint32_t* __restrict__ H, int ntiles, int nbins,
-                                  uint32_t* __restrict__ P) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
+__device__ __forceinline__ void scan_chunk_sums_body(const uint32_t* __restrict__ H, int ntiles, int nbins,
+                                                     uint32_t* __restrict__ P, int b, int c) {
     if (b >= nbins) return;
     const int t0 = c * kScanChunk, t1 = min(ntiles, t0 + kScanChunk);
     uint32_t s = 0;
@@ -77,12 +84,16 @@ __global__ void k_scan_chunk_sums(const uint32_t* __restrict__ H, int ntiles, in
     P[(size_t)c * nbins + b] = s;
 }
 
+__global__ void k_scan_chunk_sums(const uint32_t* __restrict__ H, int ntiles, int nbins,
+                                  uint32_t* __restrict__ P) {
+    scan_chunk_sums_body(H, ntiles, nbins, P, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
+}
+
 // Single CTA: per-bin totals, exclusive scan over bins (-> coarse_ptr), then
 // P[c][b] becomes the offset of chunk c within bin b plus the bin's start.
-__global__ void __launch_bounds__(1024) k_scan_bins(uint32_t* __restrict__ P, int nchunks, int nbins,
-                                                    uint32_t* __restrict__ coarse_ptr, uint32_t n) {
-    __shared__ uint32_t tot[kMaxBins];
-    __shared__ uint32_t wsum[32];
+__device__ __forceinline__ void scan_bins_body(uint32_t* __restrict__ P, int nchunks, int nbins,
+                                               uint32_t* __restrict__ coarse_ptr, uint32_t n, uint32_t* tot,
+                                               uint32_t* wsum) {
     const int tid = threadIdx.x;
     for (int b = tid; b < nbins; b += blockDim.x) {
         uint32_t s = 0;
@@ -137,11 +148,16 @@ __global__ void __launch_bounds__(1024) k_scan_bins(uint32_t* __restrict__ P, in
     if (tid == 0) coarse_ptr[nbins] = n;
 }
 
+__global__ void __launch_bounds__(1024) k_scan_bins(uint32_t* __restrict__ P, int nchunks, int nbins,
+                                                    uint32_t* __restrict__ coarse_ptr, uint32_t n) {
+    __shared__ uint32_t tot[kMaxBins];
+    __shared__ uint32_t wsum[32];
+    scan_bins_body(P, nchunks, nbins, coarse_ptr, n, tot, wsum);
+}
+
 // H[t][b] <- output offset of tile t's rows of bin b (in place).
-__global__ void k_scan_tiles(uint32_t* __restrict__ H, const uint32_t* __restrict__ P, int ntiles,
-                             int nbins) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
+__device__ __forceinline__ void scan_tiles_body(uint32_t* __restrict__ H, const uint32_t* __restrict__ P, int ntiles,
+                                                int nbins, int b, int c) {
     if (b >= nbins) return;
     const int t0 = c * kScanChunk, t1 = min(ntiles, t0 + kScanChunk);
     uint32_t run = P[(size_t)c * nbins + b];
@@ -155,6 +171,11 @@ __global__ void k_scan_tiles(uint32_t* __restrict__ H, const uint32_t* __restric
     }
 }
 
+__global__ void k_scan_tiles(uint32_t* __restrict__ H, const uint32_t* __restrict__ P, int ntiles,
+                             int nbins) {
+    scan_tiles_body(H, P, ntiles, nbins, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------- K3: coarse stable scatter
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -165,19 +186,19 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // Per row one 16-byte record {key, a, len, sigma*b}: a = row start (CSR) or
 // the row index (dense); written in coarse-bin order, stable within a bin.
+// Tile `tile` of the rows; Orow = the tile's output offsets per bin.
 template <int MODE, bool HAS_B, bool OUTER>
-__global__ void __launch_bounds__(256) k_coarse_scatter(HashParams hp, int64_t i0, int64_t n, int gshift,
-                                                        int nbins, const uint32_t* __restrict__ O,
-                                                        const int32_t* __restrict__ row_ptr,
-                                                        const float* __restrict__ b, int4* __restrict__ rec,
-                                                        unsigned* status) {
-    extern __shared__ uint32_t sm3[];
+__device__ __forceinline__ void coarse_scatter_body(const HashParams& hp, int64_t i0, int64_t n, int gshift,
+                                                    int nbins, int64_t tile, const uint32_t* __restrict__ Orow,
+                                                    const int32_t* __restrict__ row_ptr,
+                                                    const float* __restrict__ b, int4* __restrict__ rec,
+                                                    unsigned* status, uint32_t* sm3) {
     uint32_t* cnt = sm3;                                // [kTileWarps][nbins]
     uint32_t* skeys = sm3 + kTileWarps * nbins;         // [kTileWarps][kTileRowsPerWarp]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int q = threadIdx.x; q < kTileWarps * nbins; q += blockDim.x) cnt[q] = 0;
     __syncthreads();
-    const int64_t r0 = (int64_t)blockIdx.x * kTileRows + warp * kTileRowsPerWarp + lane;
+    const int64_t r0 = tile * kTileRows + warp * kTileRowsPerWarp + lane;
     uint32_t* wk = skeys + warp * kTileRowsPerWarp;
     uint32_t* wc = cnt + warp * nbins;
     if (r0 < n) {
@@ -194,7 +215,7 @@ __global__ void __launch_bounds__(256) k_coarse_scatter(HashParams hp, int64_t i
     }
     __syncthreads();
     for (int bin = threadIdx.x; bin < nbins; bin += blockDim.x) {
-        uint32_t run = O[(size_t)blockIdx.x * nbins + bin];
+        uint32_t run = Orow[bin];
 #pragma unroll
         for (int w = 0; w < kTileWarps; ++w) {
             const uint32_t t = cnt[w * nbins + bin];
@@ -256,6 +277,17 @@ __global__ void __launch_bounds__(256) k_coarse_scatter(HashParams hp, int64_t i
     }
 }
 
+template <int MODE, bool HAS_B, bool OUTER>
+__global__ void __launch_bounds__(256) k_coarse_scatter(HashParams hp, int64_t i0, int64_t n, int gshift,
+                                                        int nbins, const uint32_t* __restrict__ O,
+                                                        const int32_t* __restrict__ row_ptr,
+                                                        const float* __restrict__ b, int4* __restrict__ rec,
+                                                        unsigned* status) {
+    extern __shared__ uint32_t sm3[];
+    coarse_scatter_body<MODE, HAS_B, OUTER>(hp, i0, n, gshift, nbins, blockIdx.x, O + (size_t)blockIdx.x * nbins,
+                                            row_ptr, b, rec, status, sm3);
+}
+
 // ---------------------------------------------------------------- K4a: fine stable sort per group
 
 // One CTA per coarse bin (G = 2^gshift consecutive buckets): counting sort of
@@ -267,18 +299,23 @@ __global__ void __launch_bounds__(256) k_coarse_scatter(HashParams hp, int64_t i
 // asynchronous copies, all in flight at once), so both passes over it (count,
 // then scatter) read shared memory and the records cross DRAM once; larger
 // bins are read from global memory twice.
+struct FineSortSmem {
+    uint32_t cnt[16 * kMaxGroupBuckets];
+    uint32_t bstart[kMaxGroupBuckets + 1];
+    uint32_t wsum[32];
+};
+
 template <int MODE, bool HAS_B>
-__global__ void __launch_bounds__(512) k_fine_sort(const int4* __restrict__ rec, const uint32_t* __restrict__ coarse_ptr,
-                                                   int64_t m, int gshift, int cap, int2* __restrict__ out2,
-                                                   float* __restrict__ outb, int32_t* __restrict__ bucket_ptr) {
-    extern __shared__ int4 srec[];   // [cap]
-    __shared__ uint32_t cnt[16 * kMaxGroupBuckets];
-    __shared__ uint32_t bstart[kMaxGroupBuckets + 1];
-    __shared__ uint32_t wsum[32];
+__device__ __forceinline__ void fine_sort_body(const int4* __restrict__ rec, const uint32_t* __restrict__ coarse_ptr,
+                                               int64_t m, int gshift, int cap, int2* __restrict__ out2,
+                                               float* __restrict__ outb, int32_t* __restrict__ bucket_ptr, int g,
+                                               int4* srec, FineSortSmem& fs) {
+    uint32_t* cnt = fs.cnt;
+    uint32_t* bstart = fs.bstart;
+    uint32_t* wsum = fs.wsum;
     const int nwarps = blockDim.x >> 5;
     const int G = 1 << gshift;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = blockIdx.x;
     const uint32_t r0 = coarse_ptr[g], r1 = coarse_ptr[g + 1];
     const int64_t b0 = (int64_t)g << gshift;
     const int nb = (int)((m - b0) < (int64_t)G ? (m - b0) : (int64_t)G);
@@ -371,6 +408,15 @@ __global__ void __launch_bounds__(512) k_fine_sort(const int4* __restrict__ rec,
     }
 }
 
+template <int MODE, bool HAS_B>
+__global__ void __launch_bounds__(512) k_fine_sort(const int4* __restrict__ rec, const uint32_t* __restrict__ coarse_ptr,
+                                                   int64_t m, int gshift, int cap, int2* __restrict__ out2,
+                                                   float* __restrict__ outb, int32_t* __restrict__ bucket_ptr) {
+    extern __shared__ int4 srec[];   // [cap]
+    __shared__ FineSortSmem fs;
+    fine_sort_body<MODE, HAS_B>(rec, coarse_ptr, m, gshift, cap, out2, outb, bucket_ptr, blockIdx.x, srec, fs);
+}
+
 // ---------------------------------------------------------------- K4b: CSR apply
 
 struct CsrApplyArgs {
@@ -398,18 +444,13 @@ struct CsrApplyArgs {
 // COPIES = 32 / LPR adds the bucket's rows sub, sub + COPIES, ... (in order)
 // into its own shared-memory copy of the SA row; the copies are summed in a
 // fixed order.  No block barriers, no floating-point atomics.
+// One bucket bk of a.m: its SA row (and Sb entry) from the bucket's records.
+// accw: the warp's COPIES * dpad shared-memory accumulators (unused with
+// acc_global).
 template <int LPR, int U, bool HAS_B>
-__global__ void __launch_bounds__(256) k_apply_csr(CsrApplyArgs a) {
+__device__ __forceinline__ void apply_csr_bucket(const CsrApplyArgs& a, unsigned bk, float* accw, int lane, int sub, int sl) {
     constexpr int COPIES = 32 / LPR;
-    extern __shared__ __align__(16) float smacc[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sub = lane / LPR, sl = lane % LPR;
-    float* accw = a.acc_global ? nullptr : smacc + (size_t)warp * COPIES * a.dpad;
-    for (;;) {
-        unsigned bk = 0;
-        if (lane == 0) bk = atomicAdd(a.counter, 1u);
-        bk = __shfl_sync(0xFFFFFFFFu, bk, 0);
-        if ((int64_t)bk >= a.m) break;
+    {
         const int s = a.bucket_ptr[bk], e = a.bucket_ptr[bk + 1];
         const int64_t orow = a.map_v ? ((int64_t)bk / a.map_v) * a.map_stride + a.map_off + (int64_t)bk % a.map_v
                                      : (int64_t)bk;
@@ -512,6 +553,22 @@ __global__ void __launch_bounds__(256) k_apply_csr(CsrApplyArgs a) {
         }
         if (HAS_B && a.Sb && lane == 0) a.Sb[orow] = sbacc * a.scale;
         __syncwarp();
+    }
+}
+
+template <int LPR, int U, bool HAS_B>
+__global__ void __launch_bounds__(256) k_apply_csr(CsrApplyArgs a) {
+    constexpr int COPIES = 32 / LPR;
+    extern __shared__ __align__(16) float smacc[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = lane / LPR, sl = lane % LPR;
+    float* accw = a.acc_global ? nullptr : smacc + (size_t)warp * COPIES * a.dpad;
+    for (;;) {
+        unsigned bk = 0;
+        if (lane == 0) bk = atomicAdd(a.counter, 1u);
+        bk = __shfl_sync(0xFFFFFFFFu, bk, 0);
+        if ((int64_t)bk >= a.m) break;
+        apply_csr_bucket<LPR, U, HAS_B>(a, bk, accw, lane, sub, sl);
     }
 }
 
@@ -669,6 +726,117 @@ __global__ void __launch_bounds__(256) k_apply_vec(const float* __restrict__ rb,
 }
 
 __global__ void k_set_last(int32_t* bucket_ptr, int64_t m, int32_t n) { bucket_ptr[m] = n; }
+
+// ---------------------------------------------------------------- batched sketch (many problems)
+//
+// The same stages over a table of problems: each block finds its problem from
+// a block -> problem table (tiles, scan chunks, coarse bins) and runs the
+// single-problem body on that problem's slice of the shared scratch arrays;
+// the apply kernel's warps take buckets from one queue over all problems.
+
+__global__ void __launch_bounds__(256) kb_tile_hist(BatchSketch B) {
+    __shared__ uint32_t h[kMaxBins];
+    const BatchProb& P = B.probs[B.tile_prob[blockIdx.x]];
+    const int64_t lt = (int64_t)blockIdx.x - P.tile0;
+    tile_hist_body<false>(P.hp, 0, P.n, P.gshift, P.nbins, lt, B.H + P.H0 + lt * P.nbins, h);
+}
+
+__global__ void kb_scan_chunk_sums(BatchSketch B) {
+    const BatchProb& P = B.probs[B.chunk_prob[blockIdx.y]];
+    scan_chunk_sums_body(B.H + P.H0, P.ntiles, P.nbins, B.P + P.P0, blockIdx.x * blockDim.x + threadIdx.x,
+                         (int)blockIdx.y - P.chunk0);
+}
+
+__global__ void __launch_bounds__(1024) kb_scan_bins(BatchSketch B) {
+    __shared__ uint32_t tot[kMaxBins];
+    __shared__ uint32_t wsum[32];
+    const BatchProb& P = B.probs[blockIdx.x];
+    scan_bins_body(B.P + P.P0, P.nchunks, P.nbins, B.CP + P.CP0, (uint32_t)P.n, tot, wsum);
+}
+
+__global__ void kb_scan_tiles(BatchSketch B) {
+    const BatchProb& P = B.probs[B.chunk_prob[blockIdx.y]];
+    scan_tiles_body(B.H + P.H0, B.P + P.P0, P.ntiles, P.nbins, blockIdx.x * blockDim.x + threadIdx.x,
+                    (int)blockIdx.y - P.chunk0);
+}
+
+__global__ void __launch_bounds__(256) kb_coarse_scatter(BatchSketch B) {
+    extern __shared__ uint32_t sm3[];
+    const BatchProb& P = B.probs[B.tile_prob[blockIdx.x]];
+    const int64_t lt = (int64_t)blockIdx.x - P.tile0;
+    coarse_scatter_body<kModeCSR, true, false>(P.hp, 0, P.n, P.gshift, P.nbins, lt, B.H + P.H0 + lt * P.nbins,
+                                               P.row_ptr, P.b, B.rec + P.rec0, B.status, sm3);
+}
+
+// bins of up to this many rows are staged in shared memory (32 KB: several
+// CTAs per SM, the batch's bins hold ~2048 rows)
+constexpr int kBatchFineCap = 2048;
+
+__global__ void __launch_bounds__(512) kb_fine_sort(BatchSketch B, int cap) {
+    extern __shared__ int4 srec[];
+    __shared__ FineSortSmem fs;
+    const BatchProb& P = B.probs[B.bin_prob[blockIdx.x]];
+    fine_sort_body<kModeCSR, true>(B.rec + P.rec0, B.CP + P.CP0, P.m, P.gshift, cap, B.r2 + P.rec0, B.rb + P.rec0,
+                                   B.bptr + P.bp0, (int)blockIdx.x - P.bin0, srec, fs);
+}
+
+__global__ void kb_set_last(BatchSketch B) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < B.count) B.bptr[B.probs[p].bp0 + B.probs[p].m] = (int32_t)B.probs[p].n;
+}
+
+constexpr int kBatchApplyChunk = 16;  // buckets per queue grab
+
+template <int LPR, int U>
+__global__ void __launch_bounds__(256) kb_apply_csr(BatchSketch B) {
+    constexpr int COPIES = 32 / LPR;
+    extern __shared__ __align__(16) float smacc[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = lane / LPR, sl = lane % LPR;
+    float* accw = B.acc_global ? nullptr : smacc + (size_t)warp * COPIES * B.dpad;
+    int64_t lo = 0, hi = 0;  // global bucket range of the cached problem
+    CsrApplyArgs a{};
+    int skip = 0;
+    for (;;) {
+      unsigned g0 = 0;
+      if (lane == 0) g0 = atomicAdd(B.counter, (unsigned)kBatchApplyChunk);
+      g0 = __shfl_sync(0xFFFFFFFFu, g0, 0);
+      if ((int64_t)g0 >= B.total_buckets) break;
+      const int64_t ge = (int64_t)g0 + kBatchApplyChunk;
+      const unsigned g1 = (unsigned)(ge < B.total_buckets ? ge : B.total_buckets);
+      for (unsigned gb = g0; gb < g1; ++gb) {
+        if ((int64_t)gb < lo || (int64_t)gb >= hi) {
+            int l = 0, r = B.count - 1;  // last p with bk_base[p] <= gb
+            while (l < r) {
+                const int mid = (l + r + 1) >> 1;
+                if (B.bk_base[mid] <= (int64_t)gb) l = mid; else r = mid - 1;
+            }
+            const BatchProb& P = B.probs[l];
+            lo = B.bk_base[l];
+            hi = B.bk_base[l + 1];
+            a.rs = B.r2 + P.rec0;
+            a.rb = B.rb + P.rec0;
+            a.bucket_ptr = B.bptr + P.bp0;
+            a.col = P.col;
+            a.val = P.val;
+            a.SA = P.SA;
+            a.Sb = P.Sb;
+            a.status = B.status;
+            a.m = P.m;
+            a.d = P.d;
+            a.dpad = B.acc_global ? B.dpad : (int)((P.d + 31) & ~31) + 4;  // this problem's width (<= B.dpad)
+            a.acc_global = B.acc_global;
+            a.vec4 = P.vec4;
+            a.map_v = 0;
+            a.scale = 1.f;
+            skip = P.skip_empty;
+        }
+        const unsigned bk = (unsigned)((int64_t)gb - lo);
+        if (skip && a.bucket_ptr[bk] == a.bucket_ptr[bk + 1]) continue;  // zero row nobody reads
+        apply_csr_bucket<LPR, U, true>(a, bk, accw, lane, sub, sl);
+      }
+    }
+}
 
 // ---------------------------------------------------------------- host driver
 
@@ -903,6 +1071,146 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
         const int grid = persistent_grid(k_apply_vec, 256, 0);
         CW_PROF("k_apply_vec", stream);
         k_apply_vec<<<grid, 256, 0, stream>>>(rb, bptr, m, Sb, counter);
+    }
+    CW_LAUNCH_CHECK();
+    return CW_OK;
+}
+
+int batch_sketch_plan(const BatchSpec* specs, int count, BatchSketchHost* host, BatchSketch* dev) {
+    host->probs.assign((size_t)count, BatchProb{});
+    host->tile_prob.clear();
+    host->chunk_prob.clear();
+    host->bin_prob.clear();
+    host->bk_base.assign((size_t)count + 1, 0);
+    host->H_elems = host->P_elems = host->CP_elems = host->rows = host->bptr_elems = 0;
+    int32_t tiles = 0, chunks = 0, bins = 0, max_nbins = 1;
+    int lpr = 16, dpad = 0, acc_global = 0;
+    size_t acc_smem = 0;
+    for (int p = 0; p < count; ++p) {
+        const BatchSpec& s = specs[p];
+        SketchPlan sp;
+        int st = plan_sketch(kModeCSR, s.n, s.d, s.m, &sp);
+        if (st != CW_OK) return st;
+        // coarse bins of about 2048 rows (at most 256 buckets each): a small
+        // problem gets a few bins, not the ~1024 a single large sketch uses
+        {
+            const uint64_t want = std::max<uint64_t>(1, ((uint64_t)s.n + 2047) / 2048);
+            int gs = ilog2_ceil(((uint64_t)s.m + want - 1) / want);
+            gs = std::max(gs, ilog2_ceil(((uint64_t)s.m + kMaxBins - 1) / kMaxBins));
+            gs = std::min(gs, ilog2_ceil((uint64_t)kMaxGroupBuckets));
+            gs = std::min(gs, ilog2_ceil((uint64_t)s.m));
+            sp.gshift = gs;
+            sp.nbins = (int)(((uint64_t)s.m + (1ull << gs) - 1) >> gs);
+        }
+        BatchProb& P = host->probs[(size_t)p];
+        P.hp = make_hash_params(s.seed, s.m);
+        P.n = s.n;
+        P.d = (int32_t)s.d;
+        P.m = (int32_t)s.m;
+        P.gshift = sp.gshift;
+        P.nbins = sp.nbins;
+        P.ntiles = sp.ntiles;
+        P.nchunks = sp.nchunks;
+        P.tile0 = tiles;
+        P.chunk0 = chunks;
+        P.bin0 = bins;
+        P.vec4 = (s.d % 4 == 0) && ((reinterpret_cast<uintptr_t>(s.SA) & 15) == 0) ? 1 : 0;
+        P.H0 = host->H_elems;
+        P.P0 = host->P_elems;
+        P.CP0 = host->CP_elems;
+        P.rec0 = host->rows;
+        P.bp0 = host->bptr_elems;
+        P.bk0 = host->bk_base[(size_t)p];
+        P.row_ptr = s.row_ptr;
+        P.col = s.col;
+        P.val = s.val;
+        P.b = s.b;
+        P.SA = s.SA;
+        P.Sb = s.Sb;
+        for (int t = 0; t < sp.ntiles; ++t) host->tile_prob.push_back(p);
+        for (int c = 0; c < sp.nchunks; ++c) host->chunk_prob.push_back(p);
+        for (int g = 0; g < sp.nbins; ++g) host->bin_prob.push_back(p);
+        tiles += sp.ntiles;
+        chunks += sp.nchunks;
+        bins += sp.nbins;
+        max_nbins = std::max(max_nbins, sp.nbins);
+        host->H_elems += (int64_t)sp.ntiles * sp.nbins;
+        host->P_elems += (int64_t)sp.nchunks * sp.nbins;
+        host->CP_elems += sp.nbins + 1;
+        host->rows += s.n;
+        host->bptr_elems += s.m + 1;
+        host->bk_base[(size_t)p + 1] = host->bk_base[(size_t)p] + s.m;
+        lpr = std::max(lpr, sp.lpr);
+        dpad = std::max(dpad, sp.dpad);
+        acc_global = std::max(acc_global, sp.acc_global);
+    }
+    if (acc_global) acc_smem = 0;
+    else acc_smem = (size_t)8 * (32 / lpr) * dpad * sizeof(float);
+    dev->count = count;
+    dev->total_tiles = tiles;
+    dev->total_chunks = chunks;
+    dev->total_bins = bins;
+    dev->max_nbins = max_nbins;
+    dev->bin_groups = (max_nbins + 255) / 256;
+    dev->total_buckets = host->bk_base[(size_t)count];
+    dev->lpr = lpr;
+    dev->dpad = dpad;
+    dev->acc_global = acc_global;
+    dev->acc_smem = acc_smem;
+    auto kf = lpr == 16 ? kb_apply_csr<16, 8> : kb_apply_csr<32, 8>;
+    if (set_smem(kf, acc_smem) != cudaSuccess) return CW_ERR_CUDA;
+    dev->apply_grid = persistent_grid(kf, 256, acc_smem);
+    const size_t k3smem = sizeof(uint32_t) * (size_t)kTileWarps * (max_nbins + kTileRowsPerWarp);
+    if (set_smem(kb_coarse_scatter, k3smem) != cudaSuccess) return CW_ERR_CUDA;
+    if (set_smem(kb_fine_sort, sizeof(int4) * (size_t)kBatchFineCap) != cudaSuccess) return CW_ERR_CUDA;
+    return CW_OK;
+}
+
+int batch_sketch_enqueue(const BatchSketch& B, cudaStream_t stream) {
+    CW_CUDA_TRY(cudaMemsetAsync(B.counter, 0, sizeof(unsigned), stream));
+    if (B.total_tiles > 0) {
+        {
+            CW_PROF("kb_tile_hist", stream);
+            kb_tile_hist<<<B.total_tiles, 256, 0, stream>>>(B);
+        }
+        dim3 sg(B.bin_groups, B.total_chunks);
+        {
+            CW_PROF("kb_scan_chunk_sums", stream);
+            kb_scan_chunk_sums<<<sg, 256, 0, stream>>>(B);
+        }
+        {
+            CW_PROF("kb_scan_bins", stream);
+            kb_scan_bins<<<B.count, 1024, 0, stream>>>(B);
+        }
+        {
+            CW_PROF("kb_scan_tiles", stream);
+            kb_scan_tiles<<<sg, 256, 0, stream>>>(B);
+        }
+        const size_t k3smem = sizeof(uint32_t) * (size_t)kTileWarps * (B.max_nbins + kTileRowsPerWarp);
+        {
+            CW_PROF("kb_coarse_scatter", stream);
+            kb_coarse_scatter<<<B.total_tiles, 256, k3smem, stream>>>(B);
+        }
+    } else {
+        // no rows anywhere: every coarse bin is empty
+        CW_CUDA_TRY(cudaMemsetAsync(B.CP, 0, sizeof(uint32_t) * (size_t)(B.total_bins + B.count), stream));
+    }
+    CW_LAUNCH_CHECK();
+    {
+        CW_PROF("kb_fine_sort", stream);
+        kb_fine_sort<<<B.total_bins, 512, sizeof(int4) * (size_t)kBatchFineCap, stream>>>(B, kBatchFineCap);
+    }
+    {
+        CW_PROF("kb_set_last", stream);
+        kb_set_last<<<(B.count + 255) / 256, 256, 0, stream>>>(B);
+    }
+    CW_LAUNCH_CHECK();
+    {
+        CW_PROF("kb_apply_csr", stream);
+        if (B.lpr == 16)
+            kb_apply_csr<16, 8><<<B.apply_grid, 256, B.acc_smem, stream>>>(B);
+        else
+            kb_apply_csr<32, 8><<<B.apply_grid, 256, B.acc_smem, stream>>>(B);
     }
     CW_LAUNCH_CHECK();
     return CW_OK;

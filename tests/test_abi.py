@@ -79,3 +79,21 @@ def test_built_for_sm103a():
     from paper_1207_6365_gb300 import _build
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
     assert os.path.exists(_build.LIB)
+
+
+def test_batch_plan_rejects_bad_arguments_before_any_launch():
+    lib = cw.load()
+    plan = ctypes.c_void_p(None)
+    assert lib.cw_batch_create(None, 1, 0, None, ctypes.byref(plan)) == -1
+    arr = (cw._BatchProblem * 1)()
+    assert lib.cw_batch_create(arr, 0, 0, None, ctypes.byref(plan)) == -1
+    arr[0].A.n, arr[0].A.d, arr[0].A.nnz, arr[0].m = 10, 200, 10, 40000   # d > 128
+    arr[0].x = 16
+    assert lib.cw_batch_create(arr, 1, 0, None, ctypes.byref(plan)) == -2
+    arr[0].A.d, arr[0].m = 16, 8                                           # m < d
+    assert lib.cw_batch_create(arr, 1, 0, None, ctypes.byref(plan)) == -2
+    arr[0].m = 64
+    arr[0].x = None                                                        # no output
+    assert lib.cw_batch_create(arr, 1, 0, None, ctypes.byref(plan)) == -1
+    assert plan.value is None
+    assert lib.cw_batch_destroy(None) == 0

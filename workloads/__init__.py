@@ -25,8 +25,15 @@ Section 6 of the paper):
   sign-fixed Q factors of Gaussian matrices (Haar distributed), float32.
 * ``rhs``: b = A x0 + noise * N(0,1), x0 ~ N(0,1)^d, float32.
 * ``gaussian``: G ~ N(0,1)^{d x k}, float64.
+* ``batch_shapes`` / ``batch_problem``: the batched regression workload, many
+  independent problems with n log-uniform in [2^lo, 2^hi] (n = floor(2^U),
+  U uniform), d drawn uniformly from a set, row lengths uniform in
+  [kmin, kmax] (at most d) with uniform distinct columns, N(0,1) values,
+  b = A x0 + 0.1 N(0,1), sketch rows m = 4 d^2, seed of problem p = p + 1.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 import torch
@@ -43,6 +50,8 @@ __all__ = [
     "gaussian",
     "geometric_sigma",
     "zipf_probs",
+    "batch_shapes",
+    "batch_problem",
 ]
 
 _CHUNK = 1 << 18
@@ -221,3 +230,25 @@ def gaussian(d, k, seed, device="cpu"):
     """G ~ N(0,1)^{d x k}, float64 (the Johnson-Lindenstrauss matrix of Section 6)."""
     g = _gen(seed, device)
     return torch.randn(d, k, dtype=torch.float64, device=device, generator=g)
+
+
+def batch_shapes(count, seed, log2n=(12, 18), dset=(16, 32, 64, 128), krange=(4, 32)):
+    """Per problem a dict(n, d, m, kmin, kmax, seed) of the batched workload."""
+    g = _gen(seed, "cpu")
+    u = torch.rand(count, dtype=torch.float64, generator=g) * (log2n[1] - log2n[0]) + log2n[0]
+    di = torch.randint(0, len(dset), (count,), generator=g)
+    out = []
+    for p in range(count):
+        d = int(dset[int(di[p])])
+        out.append(dict(n=int(math.floor(2.0 ** float(u[p]))), d=d, m=4 * d * d, kmin=min(krange[0], d),
+                        kmax=min(krange[1], d), seed=p + 1))
+    return out
+
+
+def batch_problem(shape, device="cpu"):
+    """(A, b) of one problem of ``batch_shapes``."""
+    s = shape
+    A = csr_random_lengths(s["n"], s["d"], s["kmin"], s["kmax"], seed=100003 + s["seed"], device=device)
+    b, _ = rhs(A, 0.1, seed=200003 + s["seed"])
+    return A, b
+
