@@ -155,6 +155,35 @@ int cw_sketch_csr_general(const cw_csr *A, const float *b, int64_t q, int64_t v,
                           uint64_t seed, float *SA, float *Sb, cw_stream stream);
 
 /*
+ * Sketches with given values at the hash positions, and their backward (the
+ * derivative of SA and Sb with respect to the sketch's values).
+ * S(v) has the one entry of column i at row h(i) (the map of Section 2) with
+ * value v_i in place of sigma(i); v = sigma gives the sparse embedding itself.
+ * SA(v)[k, :] = sum_{i: h(i) = k} v_i A_i and Sb(v)[k] = sum_{i: h(i) = k} v_i b_i.
+ * v: n floats (device).  Other arguments, limits and outputs as
+ * cw_sketch_csr / cw_sketch_dense (SA fully overwritten; Sb when b and Sb are
+ * both given).  Sums are float32 in a fixed order.  Asynchronous.
+ */
+int cw_sketch_csr_values(const cw_csr *A, const float *b, int64_t m, uint64_t seed, const float *v,
+                         float *SA, float *Sb, cw_stream stream);
+int cw_sketch_dense_values(const float *A, int64_t n, int64_t d, int64_t lda, const float *b, int64_t m,
+                           uint64_t seed, const float *v, float *SA, float *Sb, cw_stream stream);
+
+/*
+ * cw_sketch_values_backward_* - gv_i = dL/dv_i = <gSA[h(i), :], A_i> + gSb[h(i)] b_i
+ * for a loss L with gradients gSA = dL/dSA (m x d row-major, device) and
+ * gSb = dL/dSb (m, device; NULL, or b NULL, drops the second term).  gv: n
+ * floats (device), fully overwritten.  One pass over the rows of A, each row
+ * reading the gradient row of its bucket (float32 sum in a fixed order per
+ * row; no atomics).  Limits as the forward.  Asynchronous.
+ */
+int cw_sketch_values_backward_csr(const cw_csr *A, const float *b, int64_t m, uint64_t seed, const float *gSA,
+                                  const float *gSb, float *gv, cw_stream stream);
+int cw_sketch_values_backward_dense(const float *A, int64_t n, int64_t d, int64_t lda, const float *b, int64_t m,
+                                    uint64_t seed, const float *gSA, const float *gSb, float *gv,
+                                    cw_stream stream);
+
+/*
  * Batched sketch-and-solve: many independent regressions of uneven size
  * solved by one graph launch.  Problem p gives x'_p = argmin ||S_p A_p x -
  * S_p b_p|| (Theorem "lin reg"), S_p the sparse embedding of Section 2 with
@@ -190,8 +219,9 @@ typedef struct cw_batch cw_batch; /* opaque plan */
  * device memory (scratch, and SA / Sb where NULL), uploads the descriptors and
  * captures the batch in a CUDA graph: the batched sketch (eight launches over
  * all problems) and one persistent cooperative solve kernel.  With
- * CW_BATCH_AUTOTUNE, times slab sizes {512, 1024, 2048, 4096} x {1, 2} CTAs
- * per SM on the batch (running it) and keeps the fastest; the choice is
+ * CW_BATCH_AUTOTUNE, times 16 or 32 lanes per CSR row in the segmented sum,
+ * then slab sizes {512, 1024, 2048, 4096} x {1, 2} CTAs per SM of the solve,
+ * on the batch (running it) and keeps the fastest; the choice is
  * appended to the file named by the CW_TUNE_CACHE environment variable when
  * set, and read back from it for the same shapes.  Synchronises `stream`.
  * Errors: CW_ERR_ARG (NULL pointers), CW_ERR_SHAPE (a problem outside the
@@ -215,9 +245,10 @@ int cw_batch_run(cw_batch *plan, cw_stream stream);
 int cw_batch_finish(cw_batch *plan, cw_stream stream, int32_t *status, int32_t *fallbacks);
 
 /*
- * cw_batch_info - info[0..7] = slab rows, CTAs per SM, solve grid, graph in
+ * cw_batch_info - info[0..8] = slab rows, CTAs per SM, solve grid, graph in
  * use (1) or direct launches (0), work units, tuned (1 timed, 2 from the
- * cache, 0 defaults), plan device bytes, refinement steps.
+ * cache, 0 defaults), plan device bytes, refinement steps at most, lanes per
+ * CSR row of the segmented sum (16 or 32).  `info` holds 9 values.
  */
 int cw_batch_info(const cw_batch *plan, int64_t *info);
 

@@ -18,6 +18,10 @@ Contents, each following the paper passage named in its docstring:
   generalized sparse embedding (Section "Generalized Sparse Embedding
   Matrices": blockdiag(B^(1..q)) P with kappa stacked sketches per block), as a
   row loop in C and as the explicit matrix built block by block.
+* ``sketch_*_values`` / ``sketch_values_backward_*`` / ``dense_S_values``:
+  the sketch with values v_i at the hash positions (S(v)[h(i), i] = v_i) and
+  the gradient of a loss with respect to v, gv_i = <dL/dSA[h(i)], A_i> +
+  dL/dSb[h(i)] b_i (SA and Sb are linear in v).
 * ``qr_r`` / ``solve_sketch``: Householder QR of SA (LAPACK through numpy), R
   normalised to a positive diagonal, then x' = R^-1 Q^T Sb (proof of Theorem
   "renRegAlg": "a QR factorization of SA and then computing R^-1 Q^T SB").
@@ -76,11 +80,14 @@ def _load():
             lib.orc_sketch_csr.argtypes = [_i64, _i64, _p, _p, _p, _p, _i64, _u64, _i64, _p, _p]
             lib.orc_sketch_dense.argtypes = [_i64, _i64, _i64, _p, _p, _i64, _u64, _i64, _p, _p]
             lib.orc_seeds_after_coeffs.argtypes = [_u64, _i64, _p]
+            lib.orc_sketch_csr_values.argtypes = [_i64, _i64, _p, _p, _p, _p, _i64, _u64, _p, _p, _p]
+            lib.orc_sketch_values_backward_csr.argtypes = [_i64, _i64, _p, _p, _p, _p, _i64, _u64, _p, _p, _p]
             lib.orc_sketch_csr_general.argtypes = [_i64, _i64, _p, _p, _p, _p, _i64, _i64, _i64, _u64, _p, _p]
             lib.orc_csr_matvec.argtypes = [_i64, _p, _p, _p, _p, _p]
             lib.orc_csr_rmatvec.argtypes = [_i64, _i64, _p, _p, _p, _p, _p]
             for f in (lib.orc_coeffs, lib.orc_poly_values, lib.orc_hash, lib.orc_sketch_csr,
-                      lib.orc_seeds_after_coeffs, lib.orc_sketch_csr_general,
+                      lib.orc_seeds_after_coeffs, lib.orc_sketch_csr_general, lib.orc_sketch_csr_values,
+                      lib.orc_sketch_values_backward_csr,
                       lib.orc_sketch_dense, lib.orc_csr_matvec, lib.orc_csr_rmatvec):
                 f.restype = None
             _lib = lib
@@ -166,6 +173,70 @@ def sketch_vec(x, m, seed, i0=0):
     x = _np(x, np.float32)
     SA, _ = sketch_dense(x.reshape(-1, 1), None, m, seed, i0)
     return SA[:, 0]
+
+
+# ---------------------------------------------------------------- sketch values and their gradient
+
+def dense_S_values(seed, m, n, v):
+    """The explicit m x n matrix S(v): S[h(i), i] = v_i (tiny n only)."""
+    h, _ = hash(seed, m, 0, n)
+    S = np.zeros((m, n))
+    S[h, np.arange(n)] = _np(v, np.float64)
+    return S
+
+
+def sketch_csr_values(row_ptr, col, val, d, b, m, seed, v):
+    """(SA(v), Sb(v)) in float64: SA[h(i)] += v_i A_i (row loop, C core)."""
+    row_ptr = _np(row_ptr, np.int32)
+    col = _np(col, np.int32)
+    val = _np(val, np.float32)
+    b = _np(b, np.float32)
+    v = _np(v, np.float32)
+    n = row_ptr.shape[0] - 1
+    SA = np.zeros((m, d))
+    Sb = np.zeros(m) if b is not None else None
+    _load().orc_sketch_csr_values(_i64(n), _i64(d), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(b), _i64(m),
+                                  _u64(seed), _ptr(v), _ptr(SA), _ptr(Sb))
+    return SA, Sb
+
+
+def sketch_values_backward_csr(row_ptr, col, val, d, b, m, seed, gSA, gSb=None):
+    """gv_i = <gSA[h(i)], A_i> + gSb[h(i)] b_i in float64 (C core)."""
+    row_ptr = _np(row_ptr, np.int32)
+    col = _np(col, np.int32)
+    val = _np(val, np.float32)
+    b = _np(b, np.float32)
+    gSA = np.ascontiguousarray(gSA, dtype=np.float64)
+    gSb = None if gSb is None else np.ascontiguousarray(gSb, dtype=np.float64)
+    n = row_ptr.shape[0] - 1
+    gv = np.zeros(n)
+    _load().orc_sketch_values_backward_csr(_i64(n), _i64(d), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(b),
+                                           _i64(m), _u64(seed), _ptr(gSA), _ptr(gSb), _ptr(gv))
+    return gv
+
+
+def sketch_dense_values(A, b, m, seed, v):
+    """(SA(v), Sb(v)) for dense A in float64 (scatter-add by bucket, numpy)."""
+    A = _np(A, np.float32).astype(np.float64)
+    v = _np(v, np.float32).astype(np.float64)
+    h, _ = hash(seed, m, 0, A.shape[0])
+    SA = np.zeros((m, A.shape[1]))
+    np.add.at(SA, h, v[:, None] * A)
+    Sb = None
+    if b is not None:
+        Sb = np.zeros(m)
+        np.add.at(Sb, h, v * _np(b, np.float32).astype(np.float64))
+    return SA, Sb
+
+
+def sketch_values_backward_dense(A, b, m, seed, gSA, gSb=None):
+    """gv_i = <gSA[h(i)], A_i> + gSb[h(i)] b_i for dense A in float64 (numpy)."""
+    A = _np(A, np.float32).astype(np.float64)
+    h, _ = hash(seed, m, 0, A.shape[0])
+    gv = (np.asarray(gSA, dtype=np.float64)[h] * A).sum(axis=1)
+    if gSb is not None and b is not None:
+        gv += np.asarray(gSb, dtype=np.float64)[h] * _np(b, np.float32).astype(np.float64)
+    return gv
 
 
 # ---------------------------------------------------------------- generalized sparse embedding

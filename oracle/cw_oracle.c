@@ -202,6 +202,51 @@ void orc_sketch_csr_general(int64_t n, int64_t d, const int32_t *row_ptr, const 
     free(inner);
 }
 
+/*
+ * The sketch with values v_i in place of the signs (S(v)[h(i), i] = v_i):
+ * SA[h(i), :] += v_i A_i and Sb[h(i)] += v_i b_i, rows in ascending order.
+ */
+void orc_sketch_csr_values(int64_t n, int64_t d, const int32_t *row_ptr, const int32_t *col,
+                           const float *val, const float *b, int64_t m, uint64_t seed, const float *v,
+                           double *SA, double *Sb)
+{
+    orc_poly P;
+    int64_t i, k;
+    orc_coefficients(seed, &P);
+    memset(SA, 0, sizeof(double) * (size_t)m * (size_t)d);
+    if (Sb) memset(Sb, 0, sizeof(double) * (size_t)m);
+    for (i = 0; i < n; ++i) {
+        int64_t h;
+        int s;
+        orc_bucket_sign(&P, (uint64_t)i, (uint64_t)m, &h, &s);
+        for (k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+            SA[h * d + col[k]] += (double)v[i] * (double)val[k];
+        if (Sb) Sb[h] += (double)v[i] * (double)b[i];
+    }
+}
+
+/*
+ * Gradient of a loss through SA(v), Sb(v): gv_i = sum_k gSA[h(i), col_k] val_k
+ * + gSb[h(i)] b_i (gSb or b NULL: first term only).
+ */
+void orc_sketch_values_backward_csr(int64_t n, int64_t d, const int32_t *row_ptr, const int32_t *col,
+                                    const float *val, const float *b, int64_t m, uint64_t seed,
+                                    const double *gSA, const double *gSb, double *gv)
+{
+    orc_poly P;
+    int64_t i, k;
+    orc_coefficients(seed, &P);
+    for (i = 0; i < n; ++i) {
+        int64_t h;
+        int s;
+        double acc = 0.0;
+        orc_bucket_sign(&P, (uint64_t)i, (uint64_t)m, &h, &s);
+        for (k = row_ptr[i]; k < row_ptr[i + 1]; ++k) acc += gSA[h * d + col[k]] * (double)val[k];
+        if (gSb && b) acc += gSb[h] * (double)b[i];
+        gv[i] = acc;
+    }
+}
+
 /* Same for dense row-major A (n x d, leading dimension lda). */
 void orc_sketch_dense(int64_t n, int64_t d, int64_t lda, const float *A, const float *b,
                       int64_t m, uint64_t seed, int64_t i0, double *SA, double *Sb)

@@ -20,7 +20,8 @@ __all__ = [
     "CWError", "lib", "load", "status_string", "device_status", "cw_csr_check",
     "cw_hash", "cw_sketch_csr", "cw_sketch_csr_rows", "cw_sketch_csr_general", "cw_sketch_dense", "cw_sketch_vec",
     "cw_qr", "cw_solve_sketch", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
-    "Batch", "EXPORTS", "HEADER",
+    "cw_sketch_csr_values", "cw_sketch_dense_values", "cw_sketch_values_backward_csr",
+    "cw_sketch_values_backward_dense", "SketchValues", "Batch", "EXPORTS", "HEADER",
 ]
 
 HEADER = os.path.join(_build.ROOT, "include", "cw.h")
@@ -28,7 +29,8 @@ EXPORTS = (
     "cw_status_string", "cw_version", "cw_device_status", "cw_csr_check", "cw_hash", "cw_sketch_csr",
     "cw_sketch_csr_rows", "cw_sketch_csr_general", "cw_sketch_csr_noalloc", "cw_sketch_dense", "cw_sketch_vec",
     "cw_qr", "cw_solve_sketch", "cw_batch_create", "cw_batch_run", "cw_batch_finish", "cw_batch_info",
-    "cw_batch_phases", "cw_batch_destroy", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
+    "cw_batch_phases", "cw_batch_destroy", "cw_sketch_csr_values", "cw_sketch_dense_values",
+    "cw_sketch_values_backward_csr", "cw_sketch_values_backward_dense", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
     "cw_launch_count", "cw_profile_enable", "cw_profile_get", "cw_profile_reset",
 )
 
@@ -65,6 +67,10 @@ _SIGS = {
     "cw_sketch_csr": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_csr_rows": ([ctypes.POINTER(_CSR), _i64, _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_csr_noalloc": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
+    "cw_sketch_csr_values": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p, _p], ctypes.c_int),
+    "cw_sketch_dense_values": ([_p, _i64, _i64, _i64, _p, _i64, _u64, _p, _p, _p, _p], ctypes.c_int),
+    "cw_sketch_values_backward_csr": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p, _p], ctypes.c_int),
+    "cw_sketch_values_backward_dense": ([_p, _i64, _i64, _i64, _p, _i64, _u64, _p, _p, _p, _p], ctypes.c_int),
     "cw_batch_create": ([_p, _i32, _i32, _p, _p], ctypes.c_int),
     "cw_batch_run": ([_p, _p], ctypes.c_int),
     "cw_batch_finish": ([_p, _p, _p, _p], ctypes.c_int),
@@ -137,6 +143,15 @@ def _ptr(t, dtype=None, name="tensor"):
     if not t.is_contiguous():
         raise ValueError("%s must be contiguous" % name)
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _ptr_rows(A, name="A"):
+    """Row-major float32 CUDA matrix, possibly a column slice (leading dimension = stride(0))."""
+    if not isinstance(A, torch.Tensor) or A.dtype != torch.float32 or not A.is_cuda:
+        raise TypeError("%s must be a float32 CUDA tensor" % name)
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("%s must be row-major (unit column stride)" % name)
+    return ctypes.c_void_p(A.data_ptr())
 
 
 def _check(st, where):
@@ -258,6 +273,86 @@ def cw_solve_sketch(A, b, m, seed, want_R=False):
     return (x, R) if want_R else x
 
 
+def cw_sketch_csr_values(A, b, m, seed, v, SA=None, Sb=None):
+    dev = A.val.device
+    SA = torch.empty(m, A.d, dtype=torch.float32, device=dev) if SA is None else SA
+    if b is not None and Sb is None:
+        Sb = torch.empty(m, dtype=torch.float32, device=dev)
+    c = _csr(A)
+    _check(load().cw_sketch_csr_values(ctypes.byref(c), _ptr(b, torch.float32, "b"), m, seed,
+                                       _ptr(v, torch.float32, "v"), _ptr(SA, torch.float32, "SA"),
+                                       _ptr(Sb, torch.float32, "Sb"), _stream()), "cw_sketch_csr_values")
+    return SA, Sb
+
+
+def cw_sketch_dense_values(A, b, m, seed, v, SA=None, Sb=None):
+    n, d = A.shape
+    if A.stride(1) != 1:
+        raise ValueError("A must be row-major")
+    SA = torch.empty(m, d, dtype=torch.float32, device=A.device) if SA is None else SA
+    if b is not None and Sb is None:
+        Sb = torch.empty(m, dtype=torch.float32, device=A.device)
+    _check(load().cw_sketch_dense_values(_ptr_rows(A), n, d, A.stride(0),
+                                         _ptr(b, torch.float32, "b"), m, seed, _ptr(v, torch.float32, "v"),
+                                         _ptr(SA, torch.float32, "SA"), _ptr(Sb, torch.float32, "Sb"),
+                                         _stream()), "cw_sketch_dense_values")
+    return SA, Sb
+
+
+def cw_sketch_values_backward_csr(A, b, m, seed, gSA, gSb=None, gv=None):
+    gv = torch.empty(A.n, dtype=torch.float32, device=A.val.device) if gv is None else gv
+    c = _csr(A)
+    _check(load().cw_sketch_values_backward_csr(ctypes.byref(c), _ptr(b, torch.float32, "b"), m, seed,
+                                                _ptr(gSA.contiguous(), torch.float32, "gSA"),
+                                                _ptr(None if gSb is None else gSb.contiguous(), torch.float32,
+                                                     "gSb"),
+                                                _ptr(gv, torch.float32, "gv"), _stream()),
+           "cw_sketch_values_backward_csr")
+    return gv
+
+
+def cw_sketch_values_backward_dense(A, b, m, seed, gSA, gSb=None, gv=None):
+    n, d = A.shape
+    gv = torch.empty(n, dtype=torch.float32, device=A.device) if gv is None else gv
+    _check(load().cw_sketch_values_backward_dense(_ptr_rows(A), n, d, A.stride(0),
+                                                  _ptr(b, torch.float32, "b"), m, seed,
+                                                  _ptr(gSA.contiguous(), torch.float32, "gSA"),
+                                                  _ptr(None if gSb is None else gSb.contiguous(), torch.float32,
+                                                       "gSb"),
+                                                  _ptr(gv, torch.float32, "gv"), _stream()),
+           "cw_sketch_values_backward_dense")
+    return gv
+
+
+class SketchValues(torch.autograd.Function):
+    """(SA, Sb) = (S(v) A, S(v) b) as a differentiable function of the values v.
+
+    ``apply(v, A, b, m, seed)``: v (n,) float32 CUDA tensor; A a CUDA CSR (n,
+    d, row_ptr, col, val) or a row-major float32 CUDA tensor; b (n,) or None.
+    The forward and backward are the library's kernels (cw_sketch_*_values,
+    cw_sketch_values_backward_*); only v receives a gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, v, A, b, m, seed):
+        dense = isinstance(A, torch.Tensor)
+        vv = v.detach().contiguous()
+        if dense:
+            SA, Sb = cw_sketch_dense_values(A, b, m, seed, vv)
+        else:
+            SA, Sb = cw_sketch_csr_values(A, b, m, seed, vv)
+        ctx.A, ctx.b, ctx.m, ctx.seed, ctx.dense = A, b, m, seed, dense
+        if Sb is None:
+            return SA
+        return SA, Sb
+
+    @staticmethod
+    def backward(ctx, gSA, gSb=None):
+        fn = cw_sketch_values_backward_dense if ctx.dense else cw_sketch_values_backward_csr
+        gv = fn(ctx.A, ctx.b, ctx.m, ctx.seed, gSA.float(), None if gSb is None else gSb.float())
+        return gv, None, None, None, None
+
+
 class Batch:
     """A plan for many independent sketch-and-solve problems (cw_batch_*).
 
@@ -307,9 +402,9 @@ class Batch:
         return list(st)
 
     def info(self):
-        v = (ctypes.c_int64 * 8)()
+        v = (ctypes.c_int64 * 9)()
         _check(self._lib.cw_batch_info(self._plan, v), "cw_batch_info")
-        keys = ("slab", "ctas_per_sm", "grid", "graph", "units", "tuned", "device_bytes", "steps")
+        keys = ("slab", "ctas_per_sm", "grid", "graph", "units", "tuned", "device_bytes", "steps", "lanes_per_row")
         return dict(zip(keys, [int(t) for t in v]))
 
     def phases(self):

@@ -13,17 +13,18 @@
 //           products and sums within the slab, float64 across slabs);
 //        B  per problem: sum of its partials (fixed order), float64
 //           Cholesky SA^T SA = L L^T, x0 = L^-T L^-1 SA^T Sb;
-//        C  refinement units: r = Sb - SA x in float64 over the slab's rows,
-//           partial g = SA^T r;
+//        C  refinement units: r = Sb - SA x and the partial g = SA^T r over
+//           the slab's rows in double-word float32 (~48-bit) arithmetic;
 //        D  per problem: g summed in fixed order, delta = L^-T L^-1 g,
-//           x += delta, converged when |delta|_inf <= 1e-14 |x|_inf;
+//           x += delta, converged when |delta|_inf <= 1e-13 |x|_inf or the
+//           contraction over two steps puts the remaining error there;
 //      C and D repeat up to `steps` times.
 // L L^T is the Cholesky factorisation of the Gram matrix, so L^T is the R of a
 // QR factorisation of SA with a positive diagonal (the factorisation of the
-// proof of Theorem "renRegAlg"); the refinement with float64 residuals (the
+// proof of Theorem "renRegAlg"); the refinement with ~48-bit residuals (the
 // corrected semi-normal equations of Bjorck, 1987) removes the float32 error
-// of the Gram products, so x' is the float64 least-squares solution of the
-// float32 SA.  A problem whose Cholesky pivot fails or whose refinement does
+// of the Gram products, so x' is the least-squares solution of the float32 SA
+// to about 1e-12.  A problem whose Cholesky pivot fails or whose refinement does
 // not converge is flagged and re-solved by cw_batch_finish with the float64
 // Householder QR.
 //
@@ -58,6 +59,7 @@ struct SolveProb {
     double* x;            // d (caller's)
     double* L;            // packed lower Cholesky factor, d (d + 1) / 2
     double* dprev;        // |delta|_inf of the previous refinement step
+    int32_t* rowlist;     // m: per unit, its non-empty rows from position r0 (phase A)
     int32_t vec;          // SA rows can be copied in 16-byte pieces
 };
 
@@ -81,6 +83,7 @@ struct SolveArgs {
     unsigned* bar;          // grid barrier words
     unsigned* tflag;        // barrier timeout flag
     unsigned long long* stamps;  // globaltimer (ns) at the start and after each phase, by CTA 0
+    int32_t* ucount;        // per unit: number of non-empty rows (phase A)
 };
 
 __device__ __forceinline__ void stamp(const SolveArgs& S, int k) {
@@ -195,12 +198,15 @@ __device__ __forceinline__ void over_rows(const SolveProb& P, const UnitSmem& u,
 // active threads fill whole warps; float32 sums over the slab.  c_j =
 // sum_i SA_ij Sb_i by threads j < d.  Padding columns of the tiles are zero.
 template <int T>
-__device__ void gram_unit(const SolveArgs& S, const SolveUnit& U, char* smem) {
+__device__ void gram_unit(const SolveArgs& S, int ui, const SolveUnit& U, char* smem) {
     const SolveProb& P = S.probs[U.p];
     const int d = P.d, tid = threadIdx.x;
     const int ldt = 16 * T + 4;
     const UnitSmem u = unit_smem(smem, ldt);
     const int total = compact_rows(P, U.r0, U.r1, u);
+    // keep the list for the refinement passes
+    for (int k = tid; k < total; k += kSolveThreads) P.rowlist[U.r0 + k] = u.rows[k];
+    if (tid == 0) S.ucount[ui] = total;
     // zero the padding columns of both buffers once (copies never touch them)
     for (int e = tid; e < 2 * kChunkRows * (ldt - d); e += kSolveThreads) {
         const int i = e / (ldt - d), j = d + (e - i * (ldt - d));
@@ -335,41 +341,83 @@ __device__ void chol_solve(const SolveArgs& S, int p, double* sm) {
 
 // ---------------------------------------------------------------- phase C
 
-// g = SA_slab^T (Sb_slab - SA_slab x) in float64 over the slab's non-empty
-// rows, staged 32 at a time: eight threads per row form r_i (columns q, q + 8,
-// ...; shuffle sum), then thread t adds column t & 127 of rows (t >> 7) * 16
-// .. + 15 times r_i; the two halves are added at the end.  The tile's row
-// stride is 8 mod 32 words, so the eight-lane row reads hit 32 distinct banks.
-__device__ void refine_unit(const SolveArgs& S, const SolveUnit& U, char* smem) {
+// Double-word float32 arithmetic (float64 issues at 1/64 of the float32 rate
+// on this part, and so do float32 <-> float64 conversions): a value is an
+// unevaluated sum hi + lo of two floats.  dw_mac adds the product of a float
+// a and a double-word y = (yh, yl) to the double-word accumulator (sh, sl):
+// a * yh exactly by TwoProd (the product rounded, its error by a fused
+// multiply-add), a * yl rounded (it is 2^-24 of the product), and the sum by
+// TwoSum (Knuth), so each step keeps about 48 bits.
+// (The _rn intrinsics keep the compiler from fusing the product into the
+// sums, which would break the error terms.)
+__device__ __forceinline__ void dw_mac(float& sh, float& sl, float a, float yh, float yl) {
+    const float p = __fmul_rn(a, yh);
+    const float e = fmaf(a, yh, -p);
+    const float s = __fadd_rn(sh, p);
+    const float bp = __fsub_rn(s, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    sh = s;
+    sl = fmaf(a, yl, __fadd_rn(sl, __fadd_rn(err, e)));
+}
+
+__device__ __forceinline__ void dw_split(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
+// g = SA_slab^T (Sb_slab - SA_slab x) over the slab's non-empty rows, staged
+// 32 at a time, in double-word float32: eight threads per row form r_i
+// (columns q, q + 8, ...; the eight partial sums are added in float64), then
+// thread t accumulates column t & 127 of rows (t >> 7) * 16 .. + 15 times r_i;
+// the two halves are added in float64 at the end.  The tile's row stride is
+// 8 mod 32 words, so the eight-lane row reads hit 32 distinct banks.
+__device__ void refine_unit(const SolveArgs& S, int ui, const SolveUnit& U, char* smem) {
     const SolveProb& P = S.probs[U.p];
     const int d = P.d, tid = threadIdx.x;
     const int ldt = ((d + 31) / 32) * 32 + 8;
     const UnitSmem u = unit_smem(smem, ldt);
-    double* xs = reinterpret_cast<double*>(u.wcnt + 16);  // [kMaxBatchD]
-    double* rr = xs + kMaxBatchD;                         // [kChunkRows]
-    double* red = rr + kChunkRows;                        // [2][kMaxBatchD]
-    for (int j = tid; j < d; j += kSolveThreads) xs[j] = P.x[j];
-    const int total = compact_rows(P, U.r0, U.r1, u);     // (its barriers publish xs)
+    float2* xs = reinterpret_cast<float2*>(u.wcnt + 16);  // [kMaxBatchD] x as (hi, lo)
+    float2* rr = xs + kMaxBatchD;                         // [kChunkRows] r as (hi, lo)
+    double* red = reinterpret_cast<double*>(rr + kChunkRows);  // [2][kMaxBatchD]
+    for (int j = tid; j < d; j += kSolveThreads) {
+        float h, l;
+        dw_split(P.x[j], h, l);
+        xs[j] = make_float2(h, l);
+    }
+    const int total = S.ucount[ui];                       // the list phase A kept
+    for (int k = tid; k < total; k += kSolveThreads) u.rows[k] = P.rowlist[U.r0 + k];
+    __syncthreads();                                      // (publishes xs and rows)
     const int ri = tid >> 3, q = tid & 7;
     const int col = tid & (kMaxBatchD - 1), half = tid >> 7;
-    double g = 0.0;
+    float gh = 0.f, gl = 0.f;
     over_rows(P, u, total, [&](const float* tile, const float* tsb, int nr) {
-        double dot = 0.0;
+        float sh = 0.f, sl = 0.f;
         if (ri < nr) {
             const float* tr = tile + ri * ldt;
-            for (int j = q; j < d; j += 8) dot = fma((double)tr[j], xs[j], dot);
+            for (int j = q; j < d; j += 8) {
+                const float2 x2 = xs[j];
+                dw_mac(sh, sl, tr[j], x2.x, x2.y);
+            }
         }
+        double dot = (double)sh + (double)sl;
         dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 4);
         dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 2);
         dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 1);
-        if (q == 0 && ri < nr) rr[ri] = (double)tsb[ri] - dot;
+        if (q == 0 && ri < nr) {
+            float h, l;
+            dw_split((double)tsb[ri] - dot, h, l);
+            rr[ri] = make_float2(h, l);
+        }
         __syncthreads();
         if (col < d) {
             const int i1 = min(nr, half * 16 + 16);
-            for (int i = half * 16; i < i1; ++i) g = fma((double)tile[i * ldt + col], rr[i], g);
+            for (int i = half * 16; i < i1; ++i) {
+                const float2 r2 = rr[i];
+                dw_mac(gh, gl, tile[i * ldt + col], r2.x, r2.y);
+            }
         }
     });
-    if (col < d) red[half * kMaxBatchD + col] = g;
+    if (col < d) red[half * kMaxBatchD + col] = (double)gh + (double)gl;
     __syncthreads();
     for (int j = tid; j < d; j += kSolveThreads) S.Vp[U.voff + j] = red[j] + red[kMaxBatchD + j];
 }
@@ -450,12 +498,13 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_batch_solve(SolveArgs S) {
     for (;;) {
         const int q = next_item(S.qctr + 0, S.nunits, &item);
         if (q < 0) break;
-        const SolveUnit U = S.units[S.uorder[q]];
+        const int ui = S.uorder[q];
+        const SolveUnit U = S.units[ui];
         const int d = S.probs[U.p].d;
-        if (d <= 16) gram_unit<1>(S, U, reinterpret_cast<char*>(smd));
-        else if (d <= 32) gram_unit<2>(S, U, reinterpret_cast<char*>(smd));
-        else if (d <= 64) gram_unit<4>(S, U, reinterpret_cast<char*>(smd));
-        else gram_unit<8>(S, U, reinterpret_cast<char*>(smd));
+        if (d <= 16) gram_unit<1>(S, ui, U, reinterpret_cast<char*>(smd));
+        else if (d <= 32) gram_unit<2>(S, ui, U, reinterpret_cast<char*>(smd));
+        else if (d <= 64) gram_unit<4>(S, ui, U, reinterpret_cast<char*>(smd));
+        else gram_unit<8>(S, ui, U, reinterpret_cast<char*>(smd));
     }
     if (!grid_barrier(S.bar, G, S.tflag)) return;
     stamp(S, 1);
@@ -472,9 +521,10 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_batch_solve(SolveArgs S) {
         for (;;) {
             const int q = next_item(S.qctr + 2 + 2 * step, S.nunits, &item);
             if (q < 0) break;
-            const SolveUnit U = S.units[S.uorder[q]];
+            const int ui = S.uorder[q];
+            const SolveUnit U = S.units[ui];
             if (*(volatile unsigned*)(S.conv + U.p)) continue;
-            refine_unit(S, U, reinterpret_cast<char*>(smd));
+            refine_unit(S, ui, U, reinterpret_cast<char*>(smd));
         }
         if (!grid_barrier(S.bar, G, S.tflag)) return;
         stamp(S, 3 + 2 * step);
@@ -567,7 +617,7 @@ uint64_t shape_key(const std::vector<BatchSpec>& specs) {
     return h;
 }
 
-bool cache_lookup(uint64_t key, int* slab, int* cps) {
+bool cache_lookup(uint64_t key, int* slab, int* cps, int* lpr) {
     const char* path = std::getenv("CW_TUNE_CACHE");
     if (!path || !*path) return false;
     FILE* f = std::fopen(path, "r");
@@ -576,10 +626,12 @@ bool cache_lookup(uint64_t key, int* slab, int* cps) {
     bool found = false;
     while (std::fgets(line, sizeof line, f)) {
         unsigned long long k = 0;
-        int a = 0, b = 0;
-        if (std::sscanf(line, "batch %llx %d %d", &k, &a, &b) == 3 && k == key && a > 0 && b > 0) {
+        int a = 0, b = 0, c = 0;
+        if (std::sscanf(line, "batch %llx %d %d %d", &k, &a, &b, &c) == 4 && k == key && a > 0 && b > 0 &&
+            (c == 16 || c == 32)) {
             *slab = a;
             *cps = b;
+            *lpr = c;
             found = true;
         }
     }
@@ -587,12 +639,12 @@ bool cache_lookup(uint64_t key, int* slab, int* cps) {
     return found;
 }
 
-void cache_store(uint64_t key, int slab, int cps) {
+void cache_store(uint64_t key, int slab, int cps, int lpr) {
     const char* path = std::getenv("CW_TUNE_CACHE");
     if (!path || !*path) return;
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "batch %llx %d %d\n", (unsigned long long)key, slab, cps);
+    std::fprintf(f, "batch %llx %d %d %d\n", (unsigned long long)key, slab, cps, lpr);
     std::fclose(f);
 }
 
@@ -681,6 +733,8 @@ int build_device(cw_batch* B, int slab) {
     const size_t oConv = L.take(sizeof(unsigned) * B->count);
     const size_t oStamp = L.take(sizeof(unsigned long long) * 64);
     const size_t oDprev = L.take(sizeof(double) * B->count);
+    const size_t oRowl = L.take(sizeof(int32_t) * H.bptr_elems);
+    const size_t oUcnt = L.take(sizeof(int32_t) * std::max<size_t>(1, B->units.size()));
     if (B->mem) {
         cudaFree(B->mem);
         B->mem = nullptr;
@@ -708,6 +762,7 @@ int build_device(cw_batch* B, int slab) {
         P.x = B->xs[(size_t)p];
         P.L = reinterpret_cast<double*>(base + oL) + loff[(size_t)p];
         P.dprev = reinterpret_cast<double*>(base + oDprev) + p;
+        P.rowlist = reinterpret_cast<int32_t*>(base + oRowl) + probs[(size_t)p].bp0;
         P.vec = probs[(size_t)p].vec4;
     }
     auto up = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
@@ -756,6 +811,7 @@ int build_device(cw_batch* B, int slab) {
     A.tflag = ctr + 6;
     A.qctr = ctr + 16;        // [16..16 + 2 + 2 * steps)
     A.stamps = reinterpret_cast<unsigned long long*>(base + oStamp);
+    A.ucount = reinterpret_cast<int32_t*>(base + oUcnt);
     CW_CUDA_TRY(cudaMemset(A.stamps, 0, sizeof(unsigned long long) * 64));
     B->slab = slab;
     return CW_OK;
@@ -920,11 +976,29 @@ extern "C" int cw_batch_create(const cw_batch_problem* probs, int32_t count, int
     int slab = 2048, cps = 1;
     const uint64_t key = shape_key(B->specs);
     bool cached = false;
-    if (flags & CW_BATCH_AUTOTUNE) cached = cache_lookup(key, &slab, &cps);
+    int lpr = B->sk.lpr;
+    if (flags & CW_BATCH_AUTOTUNE) cached = cache_lookup(key, &slab, &cps, &lpr);
+    if (cached && !B->sk.acc_global && batch_sketch_set_lpr(&B->sk, lpr) != CW_OK) cached = false;
     if ((flags & CW_BATCH_AUTOTUNE) && !cached) {
         cudaStream_t s = (cudaStream_t)stream;
         double best = 1e30;
         int bs = slab, bc = cps;
+        // lanes per row of the segmented sum first (with the default solve
+        // shape), then slab x CTAs per SM
+        int best_lpr = B->sk.lpr;
+        if (!B->sk.acc_global) {
+            double bl = 1e30;
+            for (int lp : {16, 32}) {
+                if (batch_sketch_set_lpr(&B->sk, lp) != CW_OK) continue;
+                if (configure(B, slab, cps, use_graph) != CW_OK) continue;
+                const double ms = time_runs(B, s, 2);
+                if (ms < bl) {
+                    bl = ms;
+                    best_lpr = lp;
+                }
+            }
+            batch_sketch_set_lpr(&B->sk, best_lpr);
+        }
         const int slabs[] = {512, 1024, 2048, 4096};
         const int cpss[] = {1, 2};
         for (int cs : cpss) {
@@ -943,7 +1017,7 @@ extern "C" int cw_batch_create(const cw_batch_problem* probs, int32_t count, int
         cps = bc;
         B->tune_ms = best;
         B->tuned = 1;
-        cache_store(key, slab, cps);
+        cache_store(key, slab, cps, B->sk.lpr);
     } else if (cached) {
         B->tuned = 2;
     }
@@ -1021,6 +1095,7 @@ extern "C" int cw_batch_info(const cw_batch* plan, int64_t* info) {
     info[5] = plan->tuned;
     info[6] = (int64_t)plan->mem_bytes;
     info[7] = plan->steps;
+    info[8] = plan->sk.lpr;
     return CW_OK;
 }
 

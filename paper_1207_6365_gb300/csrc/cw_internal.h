@@ -31,7 +31,8 @@ struct SketchLayout {
 int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const int32_t* row_ptr,
                 const int32_t* col, const float* val, const float* A, const float* b, int64_t m,
                 uint64_t seed, float* SA, float* Sb, int32_t* bucket_ptr_out, cudaStream_t stream,
-                double* SA64 = nullptr, const SketchWorkspace* ext = nullptr, const SketchLayout* lay = nullptr);
+                double* SA64 = nullptr, const SketchWorkspace* ext = nullptr, const SketchLayout* lay = nullptr,
+                const float* vals = nullptr);
 int validate_common(int64_t n, int64_t d, int64_t m);
 
 // float64 Householder QR of [SA | Sb]; synchronises.  SA64 (row-major float64)

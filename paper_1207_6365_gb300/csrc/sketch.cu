@@ -187,12 +187,15 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // Per row one 16-byte record {key, a, len, sigma*b}: a = row start (CSR) or
 // the row index (dense); written in coarse-bin order, stable within a bin.
 // Tile `tile` of the rows; Orow = the tile's output offsets per bin.
-template <int MODE, bool HAS_B, bool OUTER>
+// VALS: the sketch's entries are the given values v_i instead of the signs:
+// the record's last word is v_i (times b_i with HAS_B) and the sign is unused.
+template <int MODE, bool HAS_B, bool OUTER, bool VALS = false>
 __device__ __forceinline__ void coarse_scatter_body(const HashParams& hp, int64_t i0, int64_t n, int gshift,
                                                     int nbins, int64_t tile, const uint32_t* __restrict__ Orow,
                                                     const int32_t* __restrict__ row_ptr,
                                                     const float* __restrict__ b, int4* __restrict__ rec,
-                                                    unsigned* status, uint32_t* sm3) {
+                                                    unsigned* status, uint32_t* sm3,
+                                                    const float* __restrict__ vals = nullptr) {
     uint32_t* cnt = sm3;                                // [kTileWarps][nbins]
     uint32_t* skeys = sm3 + kTileWarps * nbins;         // [kTileWarps][kTileRowsPerWarp]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -229,13 +232,14 @@ __device__ __forceinline__ void coarse_scatter_body(const HashParams& hp, int64_
     for (int j0 = 0; j0 < kTileRowsPerLane; j0 += 4) {
         if (r0 - lane + 32 * j0 >= n) break;
         int32_t st[4], ln[4];
-        float bv[4];
+        float bv[4], wv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int64_t r = r0 + 32 * (j0 + u);
             st[u] = 0;
             ln[u] = 0;
             bv[u] = 0.f;
+            wv[u] = 0.f;
             if (r < n) {
                 if (MODE == kModeCSR) {
                     st[u] = __ldg(row_ptr + r);
@@ -244,6 +248,7 @@ __device__ __forceinline__ void coarse_scatter_body(const HashParams& hp, int64_
                     st[u] = (int32_t)r;
                 }
                 if (HAS_B) bv[u] = __ldg(b + r);
+                if (VALS) wv[u] = __ldg(vals + r);
             }
         }
 #pragma unroll
@@ -270,7 +275,8 @@ __device__ __forceinline__ void coarse_scatter_body(const HashParams& hp, int64_
                     flag_error(status, kDevBadRowPtr);
                     L = 0;
                 }
-                const float sb = HAS_B ? ((key >> 31) ? -bv[u] : bv[u]) : 0.f;
+                const float sb = VALS ? (HAS_B ? wv[u] * bv[u] : wv[u])
+                                      : (HAS_B ? ((key >> 31) ? -bv[u] : bv[u]) : 0.f);
                 rec[pos] = make_int4((int)key, st[u], L, __float_as_int(sb));
             }
         }
@@ -286,6 +292,17 @@ __global__ void __launch_bounds__(256) k_coarse_scatter(HashParams hp, int64_t i
     extern __shared__ uint32_t sm3[];
     coarse_scatter_body<MODE, HAS_B, OUTER>(hp, i0, n, gshift, nbins, blockIdx.x, O + (size_t)blockIdx.x * nbins,
                                             row_ptr, b, rec, status, sm3);
+}
+
+template <int MODE, bool HAS_B>
+__global__ void __launch_bounds__(256) k_coarse_scatter_vals(HashParams hp, int64_t i0, int64_t n, int gshift,
+                                                             int nbins, const uint32_t* __restrict__ O,
+                                                             const int32_t* __restrict__ row_ptr,
+                                                             const float* __restrict__ b, int4* __restrict__ rec,
+                                                             unsigned* status, const float* __restrict__ vals) {
+    extern __shared__ uint32_t sm3[];
+    coarse_scatter_body<MODE, HAS_B, false, true>(hp, i0, n, gshift, nbins, blockIdx.x,
+                                                  O + (size_t)blockIdx.x * nbins, row_ptr, b, rec, status, sm3, vals);
 }
 
 // ---------------------------------------------------------------- K4a: fine stable sort per group
@@ -447,7 +464,9 @@ struct CsrApplyArgs {
 // One bucket bk of a.m: its SA row (and Sb entry) from the bucket's records.
 // accw: the warp's COPIES * dpad shared-memory accumulators (unused with
 // acc_global).
-template <int LPR, int U, bool HAS_B>
+// VALS: rb holds each row's value v_i (bucket order); rows are scaled by it
+// instead of their sign, and no Sb is formed.
+template <int LPR, int U, bool HAS_B, bool VALS = false>
 __device__ __forceinline__ void apply_csr_bucket(const CsrApplyArgs& a, unsigned bk, float* accw, int lane, int sub, int sl) {
     constexpr int COPIES = 32 / LPR;
     {
@@ -471,7 +490,7 @@ __device__ __forceinline__ void apply_csr_bucket(const CsrApplyArgs& a, unsigned
             float rbv = 0.f;
             if (k0 + lane < e) {
                 rr = __ldg(&a.rs[k0 + lane]);
-                if (HAS_B) rbv = __ldg(&a.rb[k0 + lane]);
+                if (HAS_B || VALS) rbv = __ldg(&a.rb[k0 + lane]);
             }
             if (HAS_B) {
                 float t = rbv;
@@ -487,11 +506,13 @@ __device__ __forceinline__ void apply_csr_bucket(const CsrApplyArgs& a, unsigned
                 uint32_t ln[U];
                 int cc[U];
                 float vv[U];
+                float wt[VALS ? U : 1];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int t = t0 + u * COPIES + sub;  // row within the 32-row chunk
                     st[u] = __shfl_sync(0xFFFFFFFFu, rr.x, t & 31);
                     ln[u] = (uint32_t)__shfl_sync(0xFFFFFFFFu, rr.y, t & 31);
+                    if (VALS) wt[VALS ? u : 0] = __shfl_sync(0xFFFFFFFFu, rbv, t & 31);
                     if (t >= nrow) ln[u] = 0;
                 }
 #pragma unroll
@@ -509,7 +530,7 @@ __device__ __forceinline__ void apply_csr_bucket(const CsrApplyArgs& a, unsigned
                     const bool neg = (ln[u] >> 31) != 0;
                     if ((uint32_t)sl < L) {
                         const int c = cc[u];
-                        const float v = neg ? -vv[u] : vv[u];
+                        const float v = VALS ? wt[VALS ? u : 0] * vv[u] : (neg ? -vv[u] : vv[u]);
                         if ((unsigned)c < (unsigned)a.d)
                             myacc[c] += v;
                         else
@@ -519,7 +540,7 @@ __device__ __forceinline__ void apply_csr_bucket(const CsrApplyArgs& a, unsigned
                         const int c = __ldg(a.col + st[u] + t);
                         const float v = __ldg(a.val + st[u] + t);
                         if ((unsigned)c < (unsigned)a.d)
-                            myacc[c] += neg ? -v : v;
+                            myacc[c] += VALS ? wt[VALS ? u : 0] * v : (neg ? -v : v);
                         else
                             flag_error(a.status, kDevBadColumn);
                     }
@@ -572,6 +593,22 @@ __global__ void __launch_bounds__(256) k_apply_csr(CsrApplyArgs a) {
     }
 }
 
+template <int LPR, int U>
+__global__ void __launch_bounds__(256) k_apply_csr_vals(CsrApplyArgs a) {
+    constexpr int COPIES = 32 / LPR;
+    extern __shared__ __align__(16) float smacc[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = lane / LPR, sl = lane % LPR;
+    float* accw = a.acc_global ? nullptr : smacc + (size_t)warp * COPIES * a.dpad;
+    for (;;) {
+        unsigned bk = 0;
+        if (lane == 0) bk = atomicAdd(a.counter, 1u);
+        bk = __shfl_sync(0xFFFFFFFFu, bk, 0);
+        if ((int64_t)bk >= a.m) break;
+        apply_csr_bucket<LPR, U, false, true>(a, bk, accw, lane, sub, sl);
+    }
+}
+
 // ---------------------------------------------------------------- K4b: dense apply
 
 struct DenseApplyArgs {
@@ -587,6 +624,7 @@ struct DenseApplyArgs {
     int d;
     int vec4;      // 1 when A rows and d allow 16-byte loads
     double* SA64;  // PRECISE: float64 output of the two-word sums
+    const float* vals;  // VALS: the sketch's entry of row i is vals[i] (not its sign)
 };
 
 // PRECISE: each accumulator is a float32 pair (hi, lo) updated by an exact
@@ -600,7 +638,7 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
 
 // Each warp owns a bucket at a time; lane l holds columns {4l + 128 v .. +3}
 // (vec4) or {l + 32 q + 128 v} in registers; rows are added in ascending order.
-template <int NV, int U, bool HAS_B, bool PRECISE>
+template <int NV, int U, bool HAS_B, bool PRECISE, bool VALS = false>
 __global__ void __launch_bounds__(256) k_apply_dense(DenseApplyArgs a) {
     const int lane = threadIdx.x & 31;
     constexpr int COLS_PER_PASS = NV * 128;
@@ -657,6 +695,17 @@ __global__ void __launch_bounds__(256) k_apply_dense(DenseApplyArgs a) {
                 for (int u = 0; u < U; ++u) {
                     if (rr[u] == 0xFFFFFFFFu) continue;
                     const bool neg = (rr[u] >> 31) != 0;
+                    if (VALS) {
+                        const float w = __ldg(a.vals + (rr[u] & 0x7FFFFFFFu));
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) {
+                            acc[v].x = fmaf(w, x[u][v].x, acc[v].x);
+                            acc[v].y = fmaf(w, x[u][v].y, acc[v].y);
+                            acc[v].z = fmaf(w, x[u][v].z, acc[v].z);
+                            acc[v].w = fmaf(w, x[u][v].w, acc[v].w);
+                        }
+                        continue;
+                    }
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
                         if (PRECISE) {
@@ -785,8 +834,11 @@ __global__ void kb_set_last(BatchSketch B) {
     if (p < B.count) B.bptr[B.probs[p].bp0 + B.probs[p].m] = (int32_t)B.probs[p].n;
 }
 
-constexpr int kBatchApplyChunk = 16;  // buckets per queue grab
+constexpr int kBatchApplyChunk = 16;  // buckets per queue grab (<= 32)
 
+// Warps take kBatchApplyChunk consecutive global buckets at a time; lanes
+// 0..15 look up their bucket's problem and start / end in parallel, so empty
+// buckets (skipped when nobody reads their zero row) cost no dependent loads.
 template <int LPR, int U>
 __global__ void __launch_bounds__(256) kb_apply_csr(BatchSketch B) {
     constexpr int COPIES = 32 / LPR;
@@ -794,47 +846,55 @@ __global__ void __launch_bounds__(256) kb_apply_csr(BatchSketch B) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sub = lane / LPR, sl = lane % LPR;
     float* accw = B.acc_global ? nullptr : smacc + (size_t)warp * COPIES * B.dpad;
-    int64_t lo = 0, hi = 0;  // global bucket range of the cached problem
+    int cur = -1;
     CsrApplyArgs a{};
-    int skip = 0;
     for (;;) {
-      unsigned g0 = 0;
-      if (lane == 0) g0 = atomicAdd(B.counter, (unsigned)kBatchApplyChunk);
-      g0 = __shfl_sync(0xFFFFFFFFu, g0, 0);
-      if ((int64_t)g0 >= B.total_buckets) break;
-      const int64_t ge = (int64_t)g0 + kBatchApplyChunk;
-      const unsigned g1 = (unsigned)(ge < B.total_buckets ? ge : B.total_buckets);
-      for (unsigned gb = g0; gb < g1; ++gb) {
-        if ((int64_t)gb < lo || (int64_t)gb >= hi) {
-            int l = 0, r = B.count - 1;  // last p with bk_base[p] <= gb
+        unsigned g0 = 0;
+        if (lane == 0) g0 = atomicAdd(B.counter, (unsigned)kBatchApplyChunk);
+        g0 = __shfl_sync(0xFFFFFFFFu, g0, 0);
+        if ((int64_t)g0 >= B.total_buckets) break;
+        // lane i: bucket g0 + i -> (problem, local bucket, non-empty)
+        int pi = -1, bki = 0, busy = 0;
+        const int64_t gi = (int64_t)g0 + lane;
+        if (lane < kBatchApplyChunk && gi < B.total_buckets) {
+            int l = 0, r = B.count - 1;  // last p with bk_base[p] <= gi
             while (l < r) {
                 const int mid = (l + r + 1) >> 1;
-                if (B.bk_base[mid] <= (int64_t)gb) l = mid; else r = mid - 1;
+                if (B.bk_base[mid] <= gi) l = mid; else r = mid - 1;
             }
+            pi = l;
+            bki = (int)(gi - B.bk_base[l]);
             const BatchProb& P = B.probs[l];
-            lo = B.bk_base[l];
-            hi = B.bk_base[l + 1];
-            a.rs = B.r2 + P.rec0;
-            a.rb = B.rb + P.rec0;
-            a.bucket_ptr = B.bptr + P.bp0;
-            a.col = P.col;
-            a.val = P.val;
-            a.SA = P.SA;
-            a.Sb = P.Sb;
-            a.status = B.status;
-            a.m = P.m;
-            a.d = P.d;
-            a.dpad = B.acc_global ? B.dpad : (int)((P.d + 31) & ~31) + 4;  // this problem's width (<= B.dpad)
-            a.acc_global = B.acc_global;
-            a.vec4 = P.vec4;
-            a.map_v = 0;
-            a.scale = 1.f;
-            skip = P.skip_empty;
+            const int32_t* bp = B.bptr + P.bp0;
+            busy = (!P.skip_empty || bp[bki] < bp[bki + 1]) ? 1 : 0;
         }
-        const unsigned bk = (unsigned)((int64_t)gb - lo);
-        if (skip && a.bucket_ptr[bk] == a.bucket_ptr[bk + 1]) continue;  // zero row nobody reads
-        apply_csr_bucket<LPR, U, true>(a, bk, accw, lane, sub, sl);
-      }
+        unsigned todo = __ballot_sync(0xFFFFFFFFu, busy != 0);
+        while (todo) {
+            const int i = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int p = __shfl_sync(0xFFFFFFFFu, pi, i);
+            const int bk = __shfl_sync(0xFFFFFFFFu, bki, i);
+            if (p != cur) {
+                const BatchProb& P = B.probs[p];
+                cur = p;
+                a.rs = B.r2 + P.rec0;
+                a.rb = B.rb + P.rec0;
+                a.bucket_ptr = B.bptr + P.bp0;
+                a.col = P.col;
+                a.val = P.val;
+                a.SA = P.SA;
+                a.Sb = P.Sb;
+                a.status = B.status;
+                a.m = P.m;
+                a.d = P.d;
+                a.dpad = B.acc_global ? B.dpad : (int)((P.d + 31) & ~31) + 4;  // this problem's width (<= B.dpad)
+                a.acc_global = B.acc_global;
+                a.vec4 = P.vec4;
+                a.map_v = 0;
+                a.scale = 1.f;
+            }
+            apply_csr_bucket<LPR, U, true>(a, (unsigned)bk, accw, lane, sub, sl);
+        }
     }
 }
 
@@ -919,9 +979,12 @@ static int persistent_grid(F* f, int threads, size_t smem) {
 int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const int32_t* row_ptr,
                 const int32_t* col, const float* val, const float* A, const float* b, int64_t m,
                 uint64_t seed, float* SA, float* Sb, int32_t* bucket_ptr_out, cudaStream_t stream,
-                double* SA64, const SketchWorkspace* ext, const SketchLayout* lay) {
-    const bool has_b = b != nullptr && (mode == kModeVec || Sb != nullptr);
+                double* SA64, const SketchWorkspace* ext, const SketchLayout* lay, const float* vals) {
+    // with vals, the CSR pass forms SA only (its rb carries v_i); Sb comes
+    // from a separate vector pass of the caller
+    const bool has_b = b != nullptr && (mode == kModeVec || Sb != nullptr) && !(vals && mode == kModeCSR);
     if (lay && mode != kModeCSR) return CW_ERR_ARG;
+    if (vals && (lay || SA64)) return CW_ERR_ARG;
     if (n == 0 && lay) return CW_OK;   // the caller zeroed the whole output
     if (n == 0) {
         if (SA && d > 0) CW_CUDA_TRY(cudaMemsetAsync(SA, 0, sizeof(float) * (size_t)m * (size_t)d, stream));
@@ -943,7 +1006,8 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     const size_t oCP = ws.reserve(sizeof(uint32_t) * (size_t)(p.nbins + 1));
     const size_t oRec = ws.reserve(sizeof(int4) * (size_t)n);
     const size_t oR2 = (mode != kModeVec) ? ws.reserve(sizeof(int2) * (size_t)n) : 0;
-    const size_t oRB = has_b ? ws.reserve(sizeof(float) * (size_t)n) : 0;
+    const bool need_rb = has_b || (vals && mode == kModeCSR);
+    const size_t oRB = need_rb ? ws.reserve(sizeof(float) * (size_t)n) : 0;
     const size_t oBP = bucket_ptr_out ? 0 : ws.reserve(sizeof(int32_t) * (size_t)(m + 1));
     const size_t oCnt = ws.reserve(sizeof(unsigned) * 4);
     if (ext && ws.size() > ext->bytes) return CW_ERR_SHAPE;
@@ -953,7 +1017,7 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     uint32_t* CP = ws.at<uint32_t>(oCP);
     int4* rec = ws.at<int4>(oRec);
     int2* r2 = (mode != kModeVec) ? ws.at<int2>(oR2) : nullptr;
-    float* rb = has_b ? ws.at<float>(oRB) : nullptr;
+    float* rb = need_rb ? ws.at<float>(oRB) : nullptr;
     int32_t* bptr = bucket_ptr_out ? bucket_ptr_out : ws.at<int32_t>(oBP);
     unsigned* counter = ws.at<unsigned>(oCnt);
     CW_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned) * 4, stream));
@@ -1000,7 +1064,20 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
         CW_PROF("k_fine_sort", stream);                                                                 \
         kf<<<p.nbins, 512, k4smem, stream>>>(rec, CP, m, p.gshift, fcap, r2, rb, bptr);                 \
     } while (0)
-    if (mode == kModeCSR) {
+#define CW_K3V(MODE, HB)                                                                                   \
+    do {                                                                                                   \
+        auto kf = k_coarse_scatter_vals<MODE, HB>;                                                         \
+        CW_CUDA_TRY(set_smem(kf, k3smem));                                                                 \
+        CW_PROF("k_coarse_scatter", stream);                                                               \
+        kf<<<p.ntiles, 256, k3smem, stream>>>(hp, i0, n, p.gshift, p.nbins, H, row_ptr, b, rec, status, vals); \
+    } while (0)
+    if (vals) {
+        // the record's last word is v_i (CSR), v_i b_i (dense with b, vector)
+        if (mode == kModeCSR) { CW_K3V(kModeCSR, false); CW_K4A(kModeCSR, true); }
+        else if (mode == kModeDense && has_b) { CW_K3V(kModeDense, true); CW_K4A(kModeDense, true); }
+        else if (mode == kModeDense) { CW_K3V(kModeDense, false); CW_K4A(kModeDense, false); }
+        else { CW_K3V(kModeVec, true); CW_K4A(kModeVec, true); }
+    } else if (mode == kModeCSR) {
         if (has_b) { CW_K3(kModeCSR, true); CW_K4A(kModeCSR, true); }
         else { CW_K3(kModeCSR, false); CW_K4A(kModeCSR, false); }
     } else if (mode == kModeDense) {
@@ -1011,6 +1088,7 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
         CW_K4A(kModeVec, true);
     }
 #undef CW_K3
+#undef CW_K3V
 #undef CW_K4A
     CW_LAUNCH_CHECK();
     {
@@ -1032,16 +1110,27 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
         CW_PROF("k_apply_csr", stream);                                   \
         kf<<<grid, 256, p.acc_smem, stream>>>(a);                         \
     } while (0)
-        if (p.lpr == 16) {
+#define CW_K4CV(LPR)                                                      \
+    do {                                                                  \
+        auto kf = k_apply_csr_vals<LPR, 8>;                               \
+        CW_CUDA_TRY(set_smem(kf, p.acc_smem));                            \
+        const int grid = persistent_grid(kf, 256, p.acc_smem);            \
+        CW_PROF("k_apply_csr", stream);                                   \
+        kf<<<grid, 256, p.acc_smem, stream>>>(a);                         \
+    } while (0)
+        if (vals) {
+            if (p.lpr == 16) CW_K4CV(16); else CW_K4CV(32);
+        } else if (p.lpr == 16) {
             if (has_b) CW_K4C(16, true); else CW_K4C(16, false);
         } else {
             if (has_b) CW_K4C(32, true); else CW_K4C(32, false);
         }
 #undef CW_K4C
+#undef CW_K4CV
     } else if (mode == kModeDense) {
         const bool vec4 = (lda % 4 == 0) && (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
                           (SA64 || (reinterpret_cast<uintptr_t>(SA) & 15) == 0);
-        DenseApplyArgs a{r2, rb, bptr, A, lda, SA, Sb, counter, m, (int)d, vec4 ? 1 : 0, SA64};
+        DenseApplyArgs a{r2, rb, bptr, A, lda, SA, Sb, counter, m, (int)d, vec4 ? 1 : 0, SA64, vals};
         const int nv = d <= 128 ? 1 : d <= 256 ? 2 : d <= 512 ? 4 : 8;
 #define CW_K4D(NV, U, HB, PR, NAME)                                       \
     do {                                                                  \
@@ -1050,7 +1139,26 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
         CW_PROF(NAME, stream);                                            \
         kf<<<grid, 256, 0, stream>>>(a);                                  \
     } while (0)
-        if (SA64) {
+#define CW_K4DV(NV, U, HB)                                                \
+    do {                                                                  \
+        auto kf = k_apply_dense<NV, U, HB, false, true>;                  \
+        const int grid = persistent_grid(kf, 256, 0);                     \
+        CW_PROF("k_apply_dense", stream);                                 \
+        kf<<<grid, 256, 0, stream>>>(a);                                  \
+    } while (0)
+        if (vals) {
+            if (has_b) {
+                if (nv == 1) CW_K4DV(1, 8, true);
+                else if (nv == 2) CW_K4DV(2, 4, true);
+                else if (nv == 4) CW_K4DV(4, 4, true);
+                else CW_K4DV(8, 2, true);
+            } else {
+                if (nv == 1) CW_K4DV(1, 8, false);
+                else if (nv == 2) CW_K4DV(2, 4, false);
+                else if (nv == 4) CW_K4DV(4, 4, false);
+                else CW_K4DV(8, 2, false);
+            }
+        } else if (SA64) {
             if (nv == 1) CW_K4D(1, 8, false, true, "k_apply_dense_precise");
             else if (nv == 2) CW_K4D(2, 4, false, true, "k_apply_dense_precise");
             else if (nv == 4) CW_K4D(4, 4, false, true, "k_apply_dense_precise");
@@ -1067,12 +1175,23 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
             else CW_K4D(8, 2, false, false, "k_apply_dense");
         }
 #undef CW_K4D
+#undef CW_K4DV
     } else {
         const int grid = persistent_grid(k_apply_vec, 256, 0);
         CW_PROF("k_apply_vec", stream);
         k_apply_vec<<<grid, 256, 0, stream>>>(rb, bptr, m, Sb, counter);
     }
     CW_LAUNCH_CHECK();
+    return CW_OK;
+}
+
+int batch_sketch_set_lpr(BatchSketch* dev, int lpr) {
+    if (lpr != 16 && lpr != 32) return CW_ERR_ARG;
+    dev->lpr = lpr;
+    dev->acc_smem = dev->acc_global ? 0 : (size_t)8 * (32 / lpr) * dev->dpad * sizeof(float);
+    auto kf = lpr == 16 ? kb_apply_csr<16, 8> : kb_apply_csr<32, 8>;
+    if (set_smem(kf, dev->acc_smem) != cudaSuccess) return CW_ERR_CUDA;
+    dev->apply_grid = persistent_grid(kf, 256, dev->acc_smem);
     return CW_OK;
 }
 
@@ -1085,7 +1204,6 @@ int batch_sketch_plan(const BatchSpec* specs, int count, BatchSketchHost* host, 
     host->H_elems = host->P_elems = host->CP_elems = host->rows = host->bptr_elems = 0;
     int32_t tiles = 0, chunks = 0, bins = 0, max_nbins = 1;
     int lpr = 16, dpad = 0, acc_global = 0;
-    size_t acc_smem = 0;
     for (int p = 0; p < count; ++p) {
         const BatchSpec& s = specs[p];
         SketchPlan sp;
@@ -1144,8 +1262,6 @@ int batch_sketch_plan(const BatchSpec* specs, int count, BatchSketchHost* host, 
         dpad = std::max(dpad, sp.dpad);
         acc_global = std::max(acc_global, sp.acc_global);
     }
-    if (acc_global) acc_smem = 0;
-    else acc_smem = (size_t)8 * (32 / lpr) * dpad * sizeof(float);
     dev->count = count;
     dev->total_tiles = tiles;
     dev->total_chunks = chunks;
@@ -1153,13 +1269,10 @@ int batch_sketch_plan(const BatchSpec* specs, int count, BatchSketchHost* host, 
     dev->max_nbins = max_nbins;
     dev->bin_groups = (max_nbins + 255) / 256;
     dev->total_buckets = host->bk_base[(size_t)count];
-    dev->lpr = lpr;
     dev->dpad = dpad;
     dev->acc_global = acc_global;
-    dev->acc_smem = acc_smem;
-    auto kf = lpr == 16 ? kb_apply_csr<16, 8> : kb_apply_csr<32, 8>;
-    if (set_smem(kf, acc_smem) != cudaSuccess) return CW_ERR_CUDA;
-    dev->apply_grid = persistent_grid(kf, 256, acc_smem);
+    int st = batch_sketch_set_lpr(dev, lpr);
+    if (st != CW_OK) return st;
     const size_t k3smem = sizeof(uint32_t) * (size_t)kTileWarps * (max_nbins + kTileRowsPerWarp);
     if (set_smem(kb_coarse_scatter, k3smem) != cudaSuccess) return CW_ERR_CUDA;
     if (set_smem(kb_fine_sort, sizeof(int4) * (size_t)kBatchFineCap) != cudaSuccess) return CW_ERR_CUDA;
