@@ -89,6 +89,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-step timings of the other rows")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-regression row")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-sketch row")
     ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -479,6 +480,47 @@ def batch_timings(cw, stream, count=512):
     return out
 
 
+def learned_rows(cw, n_train=64, n_test=16, epochs=20, n=1 << 20, d=128, m=2048):
+    """The learned-sketch workload: a family A = U diag(j^-1.5) V_fam^T + 1e-3 N(0,1)
+    (n = 2^20, d = 128, V_fam fixed by seed 7, U Haar per matrix), b = A x0 + 0.05
+    noise; m = 2048 = 1024 learned rows (values at fixed hash positions) + 1024
+    random CountSketch rows; Adam lr 1e-3 on rho^2 - 1 through the backward kernel.
+    Fewer matrices than the 2000 / 200 of the recipe (all kept in HBM); the test
+    residual ratios of the plain CountSketch (m = 2048) and of the learned + random
+    sketch (the float64 oracle re-judges the trained sketch in the GPU tests)."""
+    import time
+    import torch
+    import workloads as W
+    from paper_1207_6365_gb300 import learned as L
+    t0 = time.time()
+    V, sig = W.family_basis(d, seed=7, device="cuda")
+    sk = L.LearnedSketch(n, m, seed_L=11, seed_R=12)
+
+    def member(k):
+        A, b = W.family_matrix(k, n, V, sig, device="cuda")
+        return A, b, L.MatrixStats(A, b), sk.random_half(A, b)
+    train_set = [member(k) for k in range(n_train)]
+    test_set = [member(100000 + k) for k in range(n_test)]
+    torch.cuda.synchronize()
+    t_gen = time.time() - t0
+    p0, l0 = L.evaluate(sk, test_set, m, seed_P=13)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    hist = L.train(sk, train_set, epochs, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.time() - t1
+    p1, l1 = L.evaluate(sk, test_set, m, seed_P=13)
+    out = {"N3_workload": "family n=2^20 x d=128, %d train / %d test matrices (recipe: 2000 / 200), m=2048 = "
+                          "1024 learned + 1024 random rows, Adam lr 1e-3, %d epochs" % (n_train, n_test, epochs),
+           "N3_test_ratio_plain_countsketch": p1, "N3_test_ratio_learned_random_init": l0,
+           "N3_test_ratio_learned_random_trained": l1, "N3_selected": "learned" if l1 < p1 else "plain",
+           "N3_train_loss_first_last_epoch": [hist[0], hist[-1]],
+           "N3_train_ms_per_step": t_train * 1000.0 / (epochs * n_train), "N3_generate_s": t_gen}
+    del train_set, test_set
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_cw(args):
     import torch
     import paper_1207_6365_gb300 as cw
@@ -615,6 +657,8 @@ def run_cw(args):
         rows = row_timings(cw, A, b, stream, peak)
         if not args.no_batch:
             rows.update(batch_timings(cw, stream))
+        if not args.no_learned:
+            rows.update(learned_rows(cw))
 
     cpu_baseline = None
     if rank == 0 and not args.no_cpu_baseline:

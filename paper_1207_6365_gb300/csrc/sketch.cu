@@ -898,6 +898,140 @@ __global__ void __launch_bounds__(256) kb_apply_csr(BatchSketch B) {
     }
 }
 
+// Range variant for batches of sparse buckets: a warp takes the buckets
+// bk0 .. bk0 + nb - 1 of one problem (nb <= kBatchApplyChunk) and walks all
+// their records together, a full warp per row and U = 8 rows' gathers in
+// flight whatever the bucket boundaries, each row adding into its bucket's
+// own shared-memory row (nb x dpad floats per warp).  Rows are added in
+// ascending record order within each bucket, as in apply_csr_bucket with one
+// accumulator copy; Sb entries are summed per bucket in record order.
+__device__ __forceinline__ void apply_csr_range(const CsrApplyArgs& a, int bk0, int nb, int skip, float* acc,
+                                                int lane) {
+    constexpr int U = 8;
+    // lane j < nb: start of bucket bk0 + j; lane nb: the end of the range
+    const int bs = (lane <= nb) ? a.bucket_ptr[bk0 + lane] : 0;
+    const int s = __shfl_sync(0xFFFFFFFFu, bs, 0), e = __shfl_sync(0xFFFFFFFFu, bs, nb);
+    const int dp = a.dpad;
+    for (int c = lane * 4; c < nb * dp; c += 128) *reinterpret_cast<float4*>(acc + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    for (int k0 = s; k0 < e; k0 += 32) {
+        const int k = k0 + lane;
+        int2 rr = make_int2(0, 0);
+        int bid = 0;
+        if (k < e) {
+            rr = __ldg(&a.rs[k]);
+            // bucket of record k: the last j with start_j <= k
+#pragma unroll
+            for (int j = 1; j < kBatchApplyChunk; ++j) {
+                const int sj = __shfl_sync(0xFFFFFFFFu, bs, j);
+                if (j < nb && sj <= k) bid = j;
+            }
+        } else {
+#pragma unroll
+            for (int j = 1; j < kBatchApplyChunk; ++j) (void)__shfl_sync(0xFFFFFFFFu, bs, j);
+        }
+        const int nrow = min(32, e - k0);
+        for (int t0 = 0; t0 < nrow; t0 += U) {
+            int st[U], bq[U];
+            uint32_t ln[U];
+            int cc[U];
+            float vv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int t = (t0 + u) & 31;
+                st[u] = __shfl_sync(0xFFFFFFFFu, rr.x, t);
+                ln[u] = (uint32_t)__shfl_sync(0xFFFFFFFFu, rr.y, t);
+                bq[u] = __shfl_sync(0xFFFFFFFFu, bid, t);
+                if (t0 + u >= nrow) ln[u] = 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                cc[u] = 0;
+                vv[u] = 0.f;
+                if ((uint32_t)lane < (ln[u] & 0x7FFFFFFFu)) {
+                    cc[u] = __ldg(a.col + st[u] + lane);
+                    vv[u] = __ldg(a.val + st[u] + lane);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t L = ln[u] & 0x7FFFFFFFu;
+                const bool neg = (ln[u] >> 31) != 0;
+                float* row = acc + bq[u] * dp;
+                if ((uint32_t)lane < L) {
+                    const int c = cc[u];
+                    if ((unsigned)c < (unsigned)a.d) row[c] += neg ? -vv[u] : vv[u];
+                    else flag_error(a.status, kDevBadColumn);
+                }
+                for (uint32_t t = lane + 32; t < L; t += 32) {  // rows longer than 32
+                    const int c = __ldg(a.col + st[u] + t);
+                    const float v = __ldg(a.val + st[u] + t);
+                    if ((unsigned)c < (unsigned)a.d) row[c] += neg ? -v : v;
+                    else flag_error(a.status, kDevBadColumn);
+                }
+                __syncwarp();
+            }
+        }
+    }
+    // Sb: lane j < nb sums bucket j's sigma * b in record order
+    const int nxt = __shfl_sync(0xFFFFFFFFu, bs, (lane + 1) & 31);
+    float sb = 0.f;
+    if (lane < nb && a.Sb)
+        for (int k = bs; k < nxt; ++k) sb += __ldg(&a.rb[k]);
+    for (int j = 0; j < nb; ++j) {
+        const int sj = __shfl_sync(0xFFFFFFFFu, bs, j), ej = __shfl_sync(0xFFFFFFFFu, bs, j + 1);
+        if (skip && sj == ej) continue;
+        float* SArow = a.SA + (size_t)(bk0 + j) * a.d;
+        const float* row = acc + j * dp;
+        if (a.vec4) {
+            for (int c = lane * 4; c < a.d; c += 128) *reinterpret_cast<float4*>(SArow + c) = *reinterpret_cast<const float4*>(row + c);
+        } else {
+            for (int c = lane; c < a.d; c += 32) SArow[c] = row[c];
+        }
+        if (a.Sb && lane == j) a.Sb[bk0 + j] = sb;
+    }
+    __syncwarp();
+}
+
+// Batched segmented sum over ranges of up to kBatchApplyChunk buckets (one
+// problem each; a grab that crosses a problem boundary is split).
+__global__ void __launch_bounds__(256) kb_apply_csr_range(BatchSketch B) {
+    extern __shared__ __align__(16) float smacc[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* acc = smacc + (size_t)warp * kBatchApplyChunk * B.dpad;
+    CsrApplyArgs a{};
+    for (;;) {
+        unsigned g0 = 0;
+        if (lane == 0) g0 = atomicAdd(B.counter, (unsigned)kBatchApplyChunk);
+        g0 = __shfl_sync(0xFFFFFFFFu, g0, 0);
+        if ((int64_t)g0 >= B.total_buckets) break;
+        const int64_t g1 = min((int64_t)g0 + kBatchApplyChunk, B.total_buckets);
+        for (int64_t gs = g0; gs < g1;) {
+            int l = 0, r = B.count - 1;  // last p with bk_base[p] <= gs
+            while (l < r) {
+                const int mid = (l + r + 1) >> 1;
+                if (B.bk_base[mid] <= gs) l = mid; else r = mid - 1;
+            }
+            const BatchProb& P = B.probs[l];
+            const int64_t pe = min(g1, B.bk_base[l + 1]);
+            a.rs = B.r2 + P.rec0;
+            a.rb = B.rb + P.rec0;
+            a.bucket_ptr = B.bptr + P.bp0;
+            a.col = P.col;
+            a.val = P.val;
+            a.SA = P.SA;
+            a.Sb = P.Sb;
+            a.status = B.status;
+            a.m = P.m;
+            a.d = P.d;
+            a.dpad = (int)((P.d + 31) & ~31) + 4;
+            a.vec4 = P.vec4;
+            apply_csr_range(a, (int)(gs - B.bk_base[l]), (int)(pe - gs), P.skip_empty, acc, lane);
+            gs = pe;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- host driver
 
 struct SketchPlan {
@@ -1186,8 +1320,15 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
 }
 
 int batch_sketch_set_lpr(BatchSketch* dev, int lpr) {
-    if (lpr != 16 && lpr != 32) return CW_ERR_ARG;
+    if (lpr != 16 && lpr != 32 && lpr != 0) return CW_ERR_ARG;
+    if (lpr == 0 && dev->acc_global) return CW_ERR_ARG;
     dev->lpr = lpr;
+    if (lpr == 0) {
+        dev->acc_smem = (size_t)8 * kBatchApplyChunk * dev->dpad * sizeof(float);
+        if (set_smem(kb_apply_csr_range, dev->acc_smem) != cudaSuccess) return CW_ERR_CUDA;
+        dev->apply_grid = persistent_grid(kb_apply_csr_range, 256, dev->acc_smem);
+        return CW_OK;
+    }
     dev->acc_smem = dev->acc_global ? 0 : (size_t)8 * (32 / lpr) * dev->dpad * sizeof(float);
     auto kf = lpr == 16 ? kb_apply_csr<16, 8> : kb_apply_csr<32, 8>;
     if (set_smem(kf, dev->acc_smem) != cudaSuccess) return CW_ERR_CUDA;
@@ -1322,8 +1463,10 @@ int batch_sketch_enqueue(const BatchSketch& B, cudaStream_t stream) {
         CW_PROF("kb_apply_csr", stream);
         if (B.lpr == 16)
             kb_apply_csr<16, 8><<<B.apply_grid, 256, B.acc_smem, stream>>>(B);
-        else
+        else if (B.lpr == 32)
             kb_apply_csr<32, 8><<<B.apply_grid, 256, B.acc_smem, stream>>>(B);
+        else
+            kb_apply_csr_range<<<B.apply_grid, 256, B.acc_smem, stream>>>(B);
     }
     CW_LAUNCH_CHECK();
     return CW_OK;

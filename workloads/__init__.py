@@ -25,6 +25,11 @@ Section 6 of the paper):
   sign-fixed Q factors of Gaussian matrices (Haar distributed), float32.
 * ``rhs``: b = A x0 + noise * N(0,1), x0 ~ N(0,1)^d, float32.
 * ``gaussian``: G ~ N(0,1)^{d x k}, float64.
+* ``family_basis`` / ``family_matrix``: the learned-sketch workload, a family of
+  matrices A = U diag(sigma) V^T + 1e-3 N(0,1) (n x d) with V (d x d) Haar and
+  fixed for the family (seed 7), U (n x d) Haar per matrix (sign-fixed Q of a
+  float32 Gaussian's QR), sigma_j = j^-1.5, b = A x0 + 0.05 N(0,1); matrix k of
+  the family is drawn from seed 1000003 + k.
 * ``batch_shapes`` / ``batch_problem``: the batched regression workload, many
   independent problems with n log-uniform in [2^lo, 2^hi] (n = floor(2^U),
   U uniform), d drawn uniformly from a set, row lengths uniform in
@@ -52,6 +57,8 @@ __all__ = [
     "zipf_probs",
     "batch_shapes",
     "batch_problem",
+    "family_basis",
+    "family_matrix",
 ]
 
 _CHUNK = 1 << 18
@@ -251,4 +258,29 @@ def batch_problem(shape, device="cpu"):
     A = csr_random_lengths(s["n"], s["d"], s["kmin"], s["kmax"], seed=100003 + s["seed"], device=device)
     b, _ = rhs(A, 0.1, seed=200003 + s["seed"])
     return A, b
+
+
+def family_basis(d=128, seed=7, device="cpu"):
+    """(V, sigma) of the matrix family: V (d x d) Haar float64, sigma_j = j^-1.5."""
+    g = _gen(seed, device)
+    V = _haar(d, d, g, device)
+    sigma = torch.arange(1, d + 1, dtype=torch.float64, device=device) ** -1.5
+    return V, sigma
+
+
+def family_matrix(k, n, V, sigma, device="cpu"):
+    """(A float32 (n, d) row-major, b float32 (n,)) of member k of the family."""
+    d = V.shape[0]
+    g = _gen(1000003 + k, device)
+    q, r = torch.linalg.qr(torch.randn(n, d, dtype=torch.float32, device=device, generator=g))
+    sg = torch.sign(torch.diagonal(r))
+    sg[sg == 0] = 1.0
+    U = q * sg
+    A = (U * sigma.to(device=device, dtype=torch.float32)) @ V.to(device=device, dtype=torch.float32).T
+    A += 1e-3 * torch.randn(n, d, dtype=torch.float32, device=device, generator=g)
+    x0 = torch.randn(d, dtype=torch.float64, device=device, generator=g)
+    y = (A.double() @ x0) if n * d <= (1 << 24) else torch.cat(
+        [A[s:s + _CHUNK].double() @ x0 for s in range(0, n, _CHUNK)])
+    b = y + 0.05 * torch.randn(n, dtype=torch.float64, device=device, generator=g)
+    return A.contiguous(), b.to(torch.float32)
 
