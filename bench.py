@@ -225,7 +225,8 @@ def measured_peak_hbm():
 
 
 # the sources each profiled kernel is built from: a capture stays valid until they change
-KERNEL_SOURCES = {"k_lsqr_pass": ("lsqr.cu", "cw_common.cuh"), "k_apply_csr": ("sketch.cu", "cw_common.cuh")}
+KERNEL_SOURCES = {"k_lsqr_pass": ("lsqr.cu", "cw_common.cuh"),
+                  "k_apply_csr": ("sketch.cu", "sketch_body.cuh", "cw_common.cuh")}
 
 
 def source_hash(kernel=None):
@@ -443,6 +444,13 @@ def batch_timings(cw, stream, count=512):
                           "{16, 32, 64, 128}, 4-32 distinct uniform columns per row, N(0,1) values, "
                           "b = A x0 + 0.1 noise, m = 4 d^2, seeds 1..%d"
                           % (count, sum(p[0].n for p in probs), sum(int(p[0].col.numel()) for p in probs), count)}
+    # the tuned shape goes to a cache file so that the direct-launch plan below
+    # (per-kernel times) runs the same configuration
+    import tempfile
+    tune = tempfile.NamedTemporaryFile(prefix="cw_tune_", suffix=".txt", delete=False)
+    tune.close()
+    old_env = os.environ.get("CW_TUNE_CACHE")
+    os.environ["CW_TUNE_CACHE"] = tune.name
     B = cw.Batch(probs, autotune=True)
     out["N1_plan"] = B.info()
     B.run()
@@ -456,7 +464,13 @@ def batch_timings(cw, stream, count=512):
     out["N1_solve_phases_ms"] = B.phases()
     B.close()
     # per-stage times from a direct-launch plan (the graph hides its kernels)
-    E = cw.Batch(probs, eager=True)
+    E = cw.Batch(probs, eager=True, autotune=True)
+    out["N1_stages_plan"] = E.info()
+    if old_env is None:
+        del os.environ["CW_TUNE_CACHE"]
+    else:
+        os.environ["CW_TUNE_CACHE"] = old_env
+    os.unlink(tune.name)
     E.run()
     E.finish()
     torch.cuda.synchronize()
@@ -466,7 +480,7 @@ def batch_timings(cw, stream, count=512):
     torch.cuda.synchronize()
     cw.profile_enable(False)
     names = ("kb_tile_hist", "kb_scan_chunk_sums", "kb_scan_bins", "kb_scan_tiles", "kb_coarse_scatter",
-             "kb_fine_sort", "kb_set_last", "kb_apply_csr", "k_batch_solve")
+             "kb_fine_sort", "kb_set_last", "kb_apply_csr", "k_batch_solve")  # (kb_apply_csr: any variant)
     out["N1_stages_ms"] = _stage_ms(cw, names, 1)
     E.close()
     # one problem at a time through the single-problem API
