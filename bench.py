@@ -71,7 +71,7 @@ def _moved_bytes(kernel, n, d, nnz, m):
 
 TIMED_KERNELS = ("k_lsqr_pass", "k_apply_csr", "k_coarse_scatter", "k_fine_sort", "k_tile_hist", "k_lsqr_post",
                  "k_chol_small", "k_chol_panel", "k_chol_update", "k_tri_inv_f32", "k_gram_to_f32", "k_chol_finish",
-                 "k_copy_f32", "k_gram_tile", "k_gram_gemv", "k_qr_householder", "k_scan_tiles", "k_scan_bins",
+                 "k_copy_f32", "k_gram_tile", "k_gram_gemv", "k_qr_householder", "k_qr_blocked", "k_scan_tiles", "k_scan_bins",
                  "k_scan_chunk_sums", "k_trsm_upper", "k_trsv_upper", "k_gram_reduce", "k_tri_inverse",
                  "k_transpose64", "k_upper_matvec", "k_to_f32_transposed", "k_set_last", "k_pack_upper_f32",
                  "k_tri_diag_inv", "k_tri_inv_blk")
@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--no-rows", action="store_true", help="skip the per-step timings of the other rows")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-regression row")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-sketch row")
+    ap.add_argument("--only-batch", type=int, default=0,
+                    help="only plan and run the first N problems of the batched workload (profiling)")
     ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -400,8 +402,8 @@ def row_timings(cw, A, b, stream, peak):
     rows["A3_sketch_dense_GBps"] = ab / (ms / 1000.0) / 1e9
     rows["A3_sketch_dense_frac"] = rows["A3_sketch_dense_GBps"] / peak
     del SA3
-    lev_k = ("k_apply_dense_precise", "k_qr_householder", "k_qr_finalize", "k_trsm_upper", "k_m_digits",
-             "k_leverage_tc", "k_leverage")
+    lev_k = ("k_apply_dense_precise", "k_qr_blocked", "k_qr_householder", "k_qr_finalize", "k_trsm_upper",
+             "k_m_digits", "k_leverage_tc", "k_leverage")
     cw.cw_leverage(A3, M, SEED, G3)
     torch.cuda.synchronize()
     cw.profile_reset()
@@ -706,8 +708,31 @@ def run_cw(args):
     return 0
 
 
+def run_batch_only(count):
+    """--only-batch N: the first N problems of the batched workload, planned
+    with the autotuner and direct launches (one line of JSON; for profiler
+    captures of the batch kernels on a smaller case)."""
+    import torch
+    import paper_1207_6365_gb300 as cw
+    import workloads as W
+    cw.load()
+    probs = []
+    for sh in W.batch_shapes(512, seed=1)[:count]:
+        A, b = W.batch_problem(sh, device="cuda")
+        probs.append((A, b, sh["m"], sh["seed"]))
+    B = cw.Batch(probs, autotune=True, eager=True)
+    B.run()
+    st = B.finish()
+    print(json.dumps({"problems": count, "plan": B.info(), "status": {str(k): st.count(k) for k in set(st)},
+                      "phases_ms": B.phases()}), flush=True)
+    B.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.only_batch:
+        return run_batch_only(args.only_batch)
     if args.oracle_worker:
         oracle_worker(args.oracle_worker, args.oracle_steps)
         return 0

@@ -48,6 +48,7 @@ constexpr int kSolveThreads = 256;
 constexpr int kMaxBatchD = 128;
 constexpr int kMaxSlab = 4096;
 constexpr int kChunkRows = 32;
+constexpr int kStages = 4;      // row chunks in flight per work unit
 constexpr int kMaxSteps = 4;  // refinement steps at most
 
 struct SolveProb {
@@ -113,8 +114,8 @@ __device__ __forceinline__ int next_item(unsigned* ctr, int total, int* sh) {
 // order), two buffers of 32 staged SA rows with their Sb, warp counts.
 struct UnitSmem {
     int* rows;   // [kMaxSlab]
-    float* tile; // [2][kChunkRows][ldt]
-    float* tsb;  // [2][kChunkRows]
+    float* tile; // [kStages][kChunkRows][ldt]
+    float* tsb;  // [kStages][kChunkRows]
     int* wcnt;   // [16]
     int ldt;
 };
@@ -123,8 +124,8 @@ __device__ __forceinline__ UnitSmem unit_smem(char* smem, int ldt) {
     UnitSmem u;
     u.rows = reinterpret_cast<int*>(smem);
     u.tile = reinterpret_cast<float*>(u.rows + kMaxSlab);
-    u.tsb = u.tile + 2 * kChunkRows * ldt;
-    u.wcnt = reinterpret_cast<int*>(u.tsb + 2 * kChunkRows);
+    u.tsb = u.tile + kStages * kChunkRows * ldt;
+    u.wcnt = reinterpret_cast<int*>(u.tsb + kStages * kChunkRows);
     u.ldt = ldt;
     return u;
 }
@@ -169,26 +170,31 @@ __device__ __forceinline__ void stage_rows(const SolveProb& P, const UnitSmem& u
         }
     }
     if (tid < nr) cp_async4(u.tsb + buf * kChunkRows + tid, P.Sb + u.rows[c0 + tid]);
-    cp_async_commit();
 }
 
-// Runs body(tile, tsb, nr) over the unit's non-empty rows, 32 at a time, the
-// next chunk's copy in flight while the current one is used.
+// Runs body(tile, tsb, nr) over the unit's non-empty rows, 32 at a time, with
+// the copies of the next kStages - 1 chunks in flight while one is used (one
+// commit group per chunk, empty past the end, so the wait count is fixed).
 template <class F>
 __device__ __forceinline__ void over_rows(const SolveProb& P, const UnitSmem& u, int total, F&& body) {
     const int nch = (total + kChunkRows - 1) / kChunkRows;
-    if (nch > 0) stage_rows(P, u, 0, min(kChunkRows, total), 0);
+    if (nch == 0) return;
+#pragma unroll
+    for (int c = 0; c < kStages - 1; ++c) {
+        if (c < nch) stage_rows(P, u, c * kChunkRows, min(kChunkRows, total - c * kChunkRows), c);
+        cp_async_commit();
+    }
     for (int c = 0; c < nch; ++c) {
-        if (c + 1 < nch) {
-            stage_rows(P, u, (c + 1) * kChunkRows, min(kChunkRows, total - (c + 1) * kChunkRows), (c + 1) & 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
+        const int cn = c + kStages - 1;
+        if (cn < nch) stage_rows(P, u, cn * kChunkRows, min(kChunkRows, total - cn * kChunkRows), cn % kStages);
+        cp_async_commit();
+        cp_async_wait<kStages - 1>();
         __syncthreads();
-        body(u.tile + (c & 1) * kChunkRows * u.ldt, u.tsb + (c & 1) * kChunkRows, min(kChunkRows, total - c * kChunkRows));
+        const int b = c % kStages;
+        body(u.tile + b * kChunkRows * u.ldt, u.tsb + b * kChunkRows, min(kChunkRows, total - c * kChunkRows));
         __syncthreads();
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------- phase A
@@ -207,8 +213,8 @@ __device__ void gram_unit(const SolveArgs& S, int ui, const SolveUnit& U, char* 
     // keep the list for the refinement passes
     for (int k = tid; k < total; k += kSolveThreads) P.rowlist[U.r0 + k] = u.rows[k];
     if (tid == 0) S.ucount[ui] = total;
-    // zero the padding columns of both buffers once (copies never touch them)
-    for (int e = tid; e < 2 * kChunkRows * (ldt - d); e += kSolveThreads) {
+    // zero the padding columns of all buffers once (copies never touch them)
+    for (int e = tid; e < kStages * kChunkRows * (ldt - d); e += kSolveThreads) {
         const int i = e / (ldt - d), j = d + (e - i * (ldt - d));
         u.tile[i * ldt + j] = 0.f;
     }
@@ -365,9 +371,18 @@ __device__ __forceinline__ void dw_split(double v, float& h, float& l) {
     l = (float)(v - (double)h);
 }
 
+// (sh, sl) += (oh, ol) for double-word values (TwoSum of the high parts).
+__device__ __forceinline__ void dw_add(float& sh, float& sl, float oh, float ol) {
+    const float s = __fadd_rn(sh, oh);
+    const float bp = __fsub_rn(s, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bp)), __fsub_rn(oh, bp));
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(ol, err));
+}
+
 // g = SA_slab^T (Sb_slab - SA_slab x) over the slab's non-empty rows, staged
 // 32 at a time, in double-word float32: eight threads per row form r_i
-// (columns q, q + 8, ...; the eight partial sums are added in float64), then
+// (columns q, q + 8, ...; the eight partial sums combined by TwoSum), then
 // thread t accumulates column t & 127 of rows (t >> 7) * 16 .. + 15 times r_i;
 // the two halves are added in float64 at the end.  The tile's row stride is
 // 8 mod 32 words, so the eight-lane row reads hit 32 distinct banks.
@@ -399,14 +414,23 @@ __device__ void refine_unit(const SolveArgs& S, int ui, const SolveUnit& U, char
                 dw_mac(sh, sl, tr[j], x2.x, x2.y);
             }
         }
-        double dot = (double)sh + (double)sl;
-        dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 4);
-        dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 2);
-        dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 1);
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xFFFFFFFFu, sh, o);
+            const float ol = __shfl_xor_sync(0xFFFFFFFFu, sl, o);
+            dw_add(sh, sl, oh, ol);
+        }
         if (q == 0 && ri < nr) {
-            float h, l;
-            dw_split((double)tsb[ri] - dot, h, l);
-            rr[ri] = make_float2(h, l);
+            // r_i = Sb_i - dot as a double-word value
+            float rh = tsb[ri], rl = 0.f;
+            dw_add(rh, rl, -sh, -sl);
+            {   // renormalise (TwoSum of the two parts): |rl| <= ulp(rh) / 2 for dw_mac
+                const float t = __fadd_rn(rh, rl);
+                const float bp = __fsub_rn(t, rh);
+                rl = __fadd_rn(__fsub_rn(rh, __fsub_rn(t, bp)), __fsub_rn(rl, bp));
+                rh = t;
+            }
+            rr[ri] = make_float2(rh, rl);
         }
         __syncthreads();
         if (col < d) {
@@ -543,8 +567,8 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_batch_solve(SolveArgs S) {
 
 size_t solve_smem_bytes() {
     const int ldt = std::max(16 * 8 + 4, kMaxBatchD + 8);
-    const size_t unit = sizeof(int) * kMaxSlab + sizeof(float) * 2 * kChunkRows * (ldt + 1) + sizeof(int) * 16 +
-                        sizeof(double) * (3 * kMaxBatchD + kChunkRows);
+    const size_t unit = sizeof(int) * kMaxSlab + sizeof(float) * kStages * kChunkRows * (ldt + 1) +
+                        sizeof(int) * 16 + sizeof(double) * (3 * kMaxBatchD + kChunkRows);
     const size_t chol = sizeof(double) * ((size_t)kMaxBatchD * (kMaxBatchD + 1) / 2 + kMaxBatchD + 16);
     return std::max(unit, chol);
 }

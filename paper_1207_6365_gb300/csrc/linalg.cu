@@ -186,6 +186,252 @@ __global__ void __launch_bounds__(1024) k_qr_householder(QrArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- blocked Householder QR (float64)
+//
+// The same reflectors in panels of kQrB columns (compact WY form, as in
+// LAPACK's dgeqrf / dlarft / dlarfb): the panel's columns are factored one at
+// a time as above, but each reflector is applied only to the rest of the
+// panel; then the panel's product Q_p = I - V T V^T is applied to all trailing
+// columns at once, W_t <- W_t - V (T^T (V^T W_t)).  Each CTA keeps the
+// reflectors' entries for its own rows in shared memory (V, rows x kQrB), so
+// the trailing matrix is read and written once per panel instead of once per
+// column.  Reductions over CTAs are in a fixed order (deterministic).
+constexpr int kQrB = 32;         // panel width
+constexpr int kQrVs = kQrB + 1;  // row stride of V in shared memory (doubles)
+
+struct QrbArgs {
+    double* W;        // column-major m x nc
+    int64_t m;
+    int d, nc;
+    double* normp;    // [2][grid] partial squared norms (double-buffered by column parity)
+    double* dotp;     // [2][grid][kQrB] partial raw dots inside a panel
+    double* rowv;     // [2][kQrB] row j of the panel, published by its owner block
+    double* Pp;       // [grid][nc][kQrB] partial V^T W_t
+    double* VtVp;     // [grid][kQrB][kQrB] partial V^T V
+    double* P;        // [nc][kQrB] V^T W_t
+    double* T;        // [kQrB][kQrB] the panel's T
+    double* Y;        // [nc][kQrB] T^T V^T W_t
+    unsigned* bar;
+    unsigned* tflag;
+};
+
+__global__ void __launch_bounds__(1024) k_qr_blocked(QrbArgs a) {
+    extern __shared__ double V[];  // [rows][kQrVs]: this block's rows of the panel's reflectors
+    __shared__ double s_red[32];
+    __shared__ double stau[kQrB];
+    __shared__ double swv[kQrB];
+    __shared__ double sT[kQrB][kQrB + 1];
+    __shared__ double sVV[kQrB][kQrB + 1];
+    const unsigned G = gridDim.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+    const int64_t per = (a.m + G - 1) / G;
+    const int64_t r0 = (per * blockIdx.x < a.m) ? per * blockIdx.x : a.m;
+    const int64_t r1 = (r0 + per < a.m) ? r0 + per : a.m;
+    const int rows = (int)(r1 - r0);
+
+    // Partials of column j for its reflector, over this block's rows, into
+    // buffer (j & 1): ||W[i >= j, j]||^2 and, for k in (j, kend), the raw dots
+    // sum_{i > j} W[i][j] W[i][k].  With v = (1 at j, W[i][j] * vscale below),
+    // v^T W[:, k] = W[j][k] + vscale * (raw dot), so the dots are formed before
+    // the column's scale is known and one grid barrier per column suffices.
+    auto column_partials = [&](int j, int kend) {
+        const int buf = j & 1;
+        const double* colj = a.W + (int64_t)j * a.m + r0;
+        double s = 0.0;
+        for (int q = tid; q < rows; q += blockDim.x) {
+            const int64_t i = r0 + q;
+            if (i >= j) s = fma(colj[q], colj[q], s);
+        }
+        s = warp_sum(s);
+        if (lane == 0) s_red[warp] = s;
+        for (int k = j + 1 + warp; k < kend; k += nwarps) {
+            const double* colk = a.W + (int64_t)k * a.m + r0;
+            double t0 = 0.0, t1 = 0.0;
+            for (int q = lane; q < rows; q += 64) {
+                if (r0 + q > j) t0 = fma(colj[q], colk[q], t0);
+                if (q + 32 < rows && r0 + q + 32 > j) t1 = fma(colj[q + 32], colk[q + 32], t1);
+            }
+            const double t = warp_sum(t0 + t1);
+            if (lane == 0) a.dotp[((size_t)buf * G + blockIdx.x) * kQrB + (k - (j / kQrB) * kQrB)] = t;
+        }
+        // the block owning row j publishes W[j][j .. kend): every block reads
+        // them after the barrier while the owner goes on to overwrite row j
+        if (j >= r0 && j < r1)
+            for (int k = j + tid; k < kend; k += blockDim.x)
+                a.rowv[buf * kQrB + (k - (j / kQrB) * kQrB)] = a.W[(int64_t)k * a.m + j];
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nwarps; ++w) t += s_red[w];
+            a.normp[buf * G + blockIdx.x] = t;
+        }
+    };
+
+    column_partials(0, min(kQrB, a.d));
+    if (!grid_barrier(a.bar, G, a.tflag)) return;
+
+    for (int j0 = 0; j0 < a.d; j0 += kQrB) {
+        const int bb = min(kQrB, a.d - j0);
+        const int jend = j0 + bb;
+        // ---- the panel, one column (one grid barrier) at a time
+        for (int j = j0; j < jend; ++j) {
+            const int jl = j - j0, buf = j & 1;
+            // ||column j||^2: lanes over blocks, then the warp's tree (the same
+            // fixed order in every block)
+            if (warp == 0) {
+                double t = 0.0;
+                for (unsigned c = lane; c < G; c += 32) t += a.normp[buf * G + c];
+                t = warp_sum(t);
+                if (lane == 0) s_red[0] = t;
+            }
+            __syncthreads();
+            const double sig2 = s_red[0];
+            const double ajj = a.rowv[buf * kQrB + jl];
+            double beta, tau, vscale;
+            if (sig2 == 0.0) {
+                beta = 0.0;
+                tau = 0.0;
+                vscale = 0.0;
+            } else {
+                const double sig = sqrt(sig2);
+                beta = ajj >= 0.0 ? -sig : sig;
+                tau = (beta - ajj) / beta;
+                vscale = 1.0 / (ajj - beta);
+            }
+            if (tid == 0) stau[jl] = tau;
+            const double* colj = a.W + (int64_t)j * a.m;
+            for (int q = tid; q < rows; q += blockDim.x) {
+                const int64_t i = r0 + q;
+                V[q * kQrVs + jl] = (i < j) ? 0.0 : (i == j ? 1.0 : colj[i] * vscale);
+            }
+            // tau * v^T W[:, k] for k in (j, jend), the same in every block
+            for (int k = j + 1 + warp; k < jend; k += nwarps) {
+                double t = 0.0;
+                for (unsigned c = lane; c < G; c += 32) t += a.dotp[((size_t)buf * G + c) * kQrB + (k - j0)];
+                t = warp_sum(t);
+                if (lane == 0) swv[k - j0] = tau * (a.rowv[buf * kQrB + (k - j0)] + vscale * t);
+            }
+            __syncthreads();
+            // apply the reflector to the rest of the panel (this block's rows i >= j)
+            for (int k = j + 1 + warp; k < jend; k += nwarps) {
+                double* colk = a.W + (int64_t)k * a.m + r0;
+                const double wk = swv[k - j0];
+                for (int q = lane; q < rows; q += 32)
+                    if (r0 + q >= j) colk[q] = fma(-V[q * kQrVs + jl], wk, colk[q]);
+            }
+            if (tid == 0 && j >= r0 && j < r1) a.W[(int64_t)j * a.m + j] = beta;  // R_jj
+            __syncthreads();
+            if (j + 1 < jend) {
+                column_partials(j + 1, jend);
+                if (!grid_barrier(a.bar, G, a.tflag)) return;
+            }
+        }
+        const int ntr = a.nc - jend;  // trailing columns (with the carried Sb)
+        if (ntr <= 0) break;
+        __syncthreads();
+        // ---- partial V^T V and V^T W_t over this block's rows
+        for (int ap = warp; ap < bb; ap += nwarps) {
+            double acc = 0.0;
+            if (lane < bb)
+                for (int q = 0; q < rows; ++q) acc = fma(V[q * kQrVs + lane], V[q * kQrVs + ap], acc);
+            a.VtVp[((size_t)blockIdx.x * kQrB + ap) * kQrB + lane] = acc;
+        }
+        for (int t = warp; t < ntr; t += nwarps) {
+            const int k = jend + t;
+            const double* colk = a.W + (int64_t)k * a.m + r0;
+            double acc = 0.0;
+            for (int q0 = 0; q0 < rows; q0 += 32) {
+                const double w = (q0 + lane < rows) ? colk[q0 + lane] : 0.0;
+                const int nq = min(32, rows - q0);
+                for (int u = 0; u < nq; ++u) {
+                    const double wu = __shfl_sync(0xFFFFFFFFu, w, u);
+                    if (lane < bb) acc = fma(V[(q0 + u) * kQrVs + lane], wu, acc);
+                }
+            }
+            a.Pp[((size_t)blockIdx.x * a.nc + k) * kQrB + lane] = acc;
+        }
+        if (!grid_barrier(a.bar, G, a.tflag)) return;
+        // ---- reductions over blocks; block 0 also forms T
+        for (int t = blockIdx.x * nwarps + warp; t < ntr; t += G * nwarps) {
+            const int k = jend + t;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;  // four chains, fixed order
+            unsigned c = 0;
+            for (; c + 3 < G; c += 4) {
+                s0 += a.Pp[((size_t)c * a.nc + k) * kQrB + lane];
+                s1 += a.Pp[((size_t)(c + 1) * a.nc + k) * kQrB + lane];
+                s2 += a.Pp[((size_t)(c + 2) * a.nc + k) * kQrB + lane];
+                s3 += a.Pp[((size_t)(c + 3) * a.nc + k) * kQrB + lane];
+            }
+            for (; c < G; ++c) s0 += a.Pp[((size_t)c * a.nc + k) * kQrB + lane];
+            a.P[(size_t)k * kQrB + lane] = (s0 + s1) + (s2 + s3);
+        }
+        if (blockIdx.x == 0) {
+            __syncthreads();
+            for (int ap = warp; ap < bb; ap += nwarps) {
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                unsigned c = 0;
+                for (; c + 3 < G; c += 4) {
+                    s0 += a.VtVp[((size_t)c * kQrB + ap) * kQrB + lane];
+                    s1 += a.VtVp[((size_t)(c + 1) * kQrB + ap) * kQrB + lane];
+                    s2 += a.VtVp[((size_t)(c + 2) * kQrB + ap) * kQrB + lane];
+                    s3 += a.VtVp[((size_t)(c + 3) * kQrB + ap) * kQrB + lane];
+                }
+                for (; c < G; ++c) s0 += a.VtVp[((size_t)c * kQrB + ap) * kQrB + lane];
+                sVV[ap][lane] = (s0 + s1) + (s2 + s3);
+            }
+            __syncthreads();
+            if (warp == 0) {
+                // T upper triangular: T_aa = tau_a, T[0:a, a] = -tau_a T[0:a, 0:a] (V^T v_a)[0:a]
+                for (int c2 = 0; c2 < bb; ++c2) {
+                    double z = 0.0;
+                    if (lane < c2)
+                        for (int x = lane; x < c2; ++x) z = fma(sT[lane][x], sVV[x][c2], z);
+                    __syncwarp();
+                    if (lane < c2) sT[lane][c2] = -stau[c2] * z;
+                    else if (lane == c2) sT[c2][c2] = stau[c2];
+                    else sT[lane][c2] = 0.0;
+                    __syncwarp();
+                }
+                for (int x = 0; x < kQrB; ++x) a.T[x * kQrB + lane] = (x < bb && lane < bb) ? sT[x][lane] : 0.0;
+            }
+        }
+        if (!grid_barrier(a.bar, G, a.tflag)) return;
+        // ---- Y = T^T P for the trailing columns (distributed)
+        for (int e = tid; e < kQrB * kQrB; e += blockDim.x) sT[e / kQrB][e % kQrB] = a.T[e];
+        __syncthreads();
+        for (int t = blockIdx.x * nwarps + warp; t < ntr; t += G * nwarps) {
+            const int k = jend + t;
+            const double p = a.P[(size_t)k * kQrB + lane];
+            double y = 0.0;
+            for (int x = 0; x < bb; ++x) {
+                const double px = __shfl_sync(0xFFFFFFFFu, p, x);
+                if (x <= lane) y = fma(sT[x][lane], px, y);
+            }
+            a.Y[(size_t)k * kQrB + lane] = (lane < bb) ? y : 0.0;
+        }
+        if (!grid_barrier(a.bar, G, a.tflag)) return;
+        // ---- W_t -= V Y over this block's rows, then the next panel's first
+        // column partials
+        for (int t = warp; t < ntr; t += nwarps) {
+            const int k = jend + t;
+            const double yl = a.Y[(size_t)k * kQrB + lane];
+            double* colk = a.W + (int64_t)k * a.m + r0;
+            for (int q0 = 0; q0 < rows; q0 += 32) {
+                const int q = q0 + lane;
+                double acc = 0.0;
+                for (int x = 0; x < bb; ++x) {
+                    const double yx = __shfl_sync(0xFFFFFFFFu, yl, x);
+                    if (q < rows) acc = fma(V[q * kQrVs + x], yx, acc);
+                }
+                if (q < rows) colk[q] -= acc;
+            }
+        }
+        __syncthreads();
+        if (jend < a.d) column_partials(jend, min(jend + kQrB, a.d));
+        if (!grid_barrier(a.bar, G, a.tflag)) return;
+    }
+}
+
 // R (row-major d x d, positive diagonal) and c = Q^T Sb from the factored W;
 // flags rank deficiency |R_jj| <= d * 2^-52 * max |R_ii|.
 __global__ void k_qr_finalize(const double* __restrict__ W, int64_t m, int d, int nc, double* __restrict__ R,
@@ -975,11 +1221,34 @@ int qr64(const float* SA, int64_t m, int d, const float* Sb, double* R, double* 
     int G = qr_grid(m, threads, 48 * 1024);
     const size_t smem = sizeof(double) * (size_t)((m + G - 1) / G);
     if (smem > 200 * 1024) return CW_ERR_SHAPE;  // m too large for the resident-grid design
+    // the blocked kernel when this block's rows of a panel fit in shared memory
+    // (one CTA of 1024 threads per SM)
+    int Gb = num_sms();
+    if ((int64_t)Gb > (m + 63) / 64) Gb = (int)std::max<int64_t>(1, (m + 63) / 64);
+    const size_t bsmem = sizeof(double) * (size_t)((m + Gb - 1) / Gb) * kQrVs;
+    bool blocked = bsmem <= 180 * 1024;
+    if (blocked) {
+        int per_sm = 0;
+        if (cudaFuncSetAttribute(k_qr_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr_blocked, threads, bsmem) != cudaSuccess ||
+            per_sm < 1) {
+            (void)cudaGetLastError();
+            blocked = false;
+        }
+    }
+    const int Gn = blocked ? Gb : G;
     Scratch ws(stream);
     const size_t oW = ws.reserve(sizeof(double) * (size_t)m * nc);
-    const size_t oN = ws.reserve(sizeof(double) * (size_t)G);
-    const size_t oD = ws.reserve(sizeof(double) * (size_t)G * nc);
-    const size_t oV = ws.reserve(sizeof(double) * (size_t)nc);
+    const size_t oN = ws.reserve(sizeof(double) * (size_t)Gn * 2);
+    const size_t oD = blocked ? 0 : ws.reserve(sizeof(double) * (size_t)G * nc);
+    const size_t oV = blocked ? 0 : ws.reserve(sizeof(double) * (size_t)nc);
+    const size_t oBd = blocked ? ws.reserve(sizeof(double) * (size_t)Gb * kQrB * 2) : 0;
+    const size_t oBw = blocked ? ws.reserve(sizeof(double) * kQrB * 2) : 0;
+    const size_t oPp = blocked ? ws.reserve(sizeof(double) * (size_t)Gb * nc * kQrB) : 0;
+    const size_t oVV = blocked ? ws.reserve(sizeof(double) * (size_t)Gb * kQrB * kQrB) : 0;
+    const size_t oP = blocked ? ws.reserve(sizeof(double) * (size_t)nc * kQrB) : 0;
+    const size_t oT = blocked ? ws.reserve(sizeof(double) * kQrB * kQrB) : 0;
+    const size_t oY = blocked ? ws.reserve(sizeof(double) * (size_t)nc * kQrB) : 0;
     const size_t oB = ws.reserve(sizeof(unsigned) * 4);
     CW_CUDA_TRY(ws.alloc());
     double* W = ws.at<double>(oW);
@@ -997,6 +1266,16 @@ int qr64(const float* SA, int64_t m, int d, const float* Sb, double* R, double* 
             k_to_colmajor64<float><<<tg, tb, 0, stream>>>(SA, Sb, m, d, nc, W);
         }
     CW_LAUNCH_CHECK();
+    if (blocked) {
+        QrbArgs b{W, m, d, nc, ws.at<double>(oN), ws.at<double>(oBd), ws.at<double>(oBw), ws.at<double>(oPp),
+                  ws.at<double>(oVV), ws.at<double>(oP), ws.at<double>(oT), ws.at<double>(oY), bar, bar + 2};
+        CW_CUDA_TRY(cudaFuncSetAttribute(k_qr_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
+        void* args[] = {&b};
+        {
+            CW_PROF("k_qr_blocked", stream);
+            CW_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_qr_blocked, dim3(Gb), dim3(threads), args, bsmem, stream));
+        }
+    } else {
     QrArgs a{W, m, d, nc, ws.at<double>(oN), ws.at<double>(oD), ws.at<double>(oV), bar, bar + 2};
     CW_CUDA_TRY(cudaFuncSetAttribute(k_qr_householder, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -1007,6 +1286,7 @@ int qr64(const float* SA, int64_t m, int d, const float* Sb, double* R, double* 
     {
         CW_PROF("k_qr_householder", stream);
         CW_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_qr_householder, dim3(G), dim3(threads), args, smem, stream));
+    }
     }
     {
         CW_PROF("k_qr_finalize", stream);
