@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--no-rows", action="store_true", help="skip the per-step timings of the other rows")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-regression row")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-sketch row")
+    ap.add_argument("--only-qr", type=int, nargs=2, default=None, metavar=("M", "D"),
+                    help="only time the float64 QR of an M x D Gaussian SA (profiling)")
     ap.add_argument("--only-batch", type=int, default=0,
                     help="only plan and run the first N problems of the batched workload (profiling)")
     ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
@@ -729,10 +731,29 @@ def run_batch_only(count):
     return 0
 
 
+def run_qr_only(m, d):
+    """--only-qr M D: the float64 QR (cw_qr) of an M x D Gaussian SA with a
+    right-hand side, one warm-up and three timed calls (CUDA events); one line
+    of JSON (for profiler captures of the QR kernel on its own)."""
+    import torch
+    import paper_1207_6365_gb300 as cw
+    cw.load()
+    g = torch.Generator(device="cuda").manual_seed(5)
+    SA = torch.randn(m, d, device="cuda", generator=g)
+    Sb = torch.randn(m, device="cuda", generator=g)
+    stream = torch.cuda.current_stream()
+    ms = _timed(lambda: cw.cw_qr(SA, Sb), stream, reps=3, warm=1)
+    flops = 2.0 * m * d * d - 2.0 * d ** 3 / 3.0
+    print(json.dumps({"m": m, "d": d, "qr_ms": ms, "fp64_tflops": flops / (ms / 1000.0) / 1e12}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.only_batch:
         return run_batch_only(args.only_batch)
+    if args.only_qr:
+        return run_qr_only(args.only_qr[0], args.only_qr[1])
     if args.oracle_worker:
         oracle_worker(args.oracle_worker, args.oracle_steps)
         return 0
