@@ -62,7 +62,26 @@ struct SolveProb {
     double* dprev;        // |delta|_inf of the previous refinement step
     int32_t* rowlist;     // m: per unit, its non-empty rows from position r0 (phase A)
     int32_t vec;          // SA rows can be copied in 16-byte pieces
+    int64_t g0, gstride;  // partial Gram of unit unit0 + u at Gp + g0 + u * gstride
+    int64_t v0, vstride;  // partial vector of unit unit0 + u at Vp + v0 + u * vstride
 };
+
+// sum over the problem's units of part[base + u * stride + e], four chains in a
+// fixed order
+__device__ __forceinline__ double sum_units(const double* __restrict__ part, int64_t base, int64_t stride, int n,
+                                            int64_t e) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    const double* p = part + base + e;
+    int u = 0;
+    for (; u + 3 < n; u += 4) {
+        s0 += __ldg(p + (int64_t)u * stride);
+        s1 += __ldg(p + (int64_t)(u + 1) * stride);
+        s2 += __ldg(p + (int64_t)(u + 2) * stride);
+        s3 += __ldg(p + (int64_t)(u + 3) * stride);
+    }
+    for (; u < n; ++u) s0 += __ldg(p + (int64_t)u * stride);
+    return (s0 + s1) + (s2 + s3);
+}
 
 struct SolveUnit {
     int32_t p, r0, r1;
@@ -287,16 +306,8 @@ __device__ void chol_solve(const SolveArgs& S, int p, double* sm) {
     double* G = sm;         // packed lower [nt]
     double* v = sm + nt;    // [d]
     __shared__ int ok;
-    for (int64_t e = tid; e < nt; e += kSolveThreads) {
-        double s = 0.0;
-        for (int u = 0; u < P.nunits; ++u) s += S.Gp[S.units[P.unit0 + u].goff + e];
-        G[e] = s;
-    }
-    for (int j = tid; j < d; j += kSolveThreads) {
-        double s = 0.0;
-        for (int u = 0; u < P.nunits; ++u) s += S.Vp[S.units[P.unit0 + u].voff + j];
-        v[j] = s;
-    }
+    for (int64_t e = tid; e < nt; e += kSolveThreads) G[e] = sum_units(S.Gp, P.g0, P.gstride, P.nunits, e);
+    for (int j = tid; j < d; j += kSolveThreads) v[j] = sum_units(S.Vp, P.v0, P.vstride, P.nunits, j);
     if (tid == 0) ok = 1;
     __syncthreads();
     for (int j = 0; j < d; ++j) {
@@ -456,11 +467,7 @@ __device__ void refine_update(const SolveArgs& S, int p, bool first, bool last, 
     double* v = sm + nt;
     double* red = v + kMaxBatchD;  // [2 * 8]
     for (int64_t e = tid; e < nt; e += kSolveThreads) G[e] = P.L[e];
-    for (int j = tid; j < d; j += kSolveThreads) {
-        double s = 0.0;
-        for (int u = 0; u < P.nunits; ++u) s += S.Vp[S.units[P.unit0 + u].voff + j];
-        v[j] = s;
-    }
+    for (int j = tid; j < d; j += kSolveThreads) v[j] = sum_units(S.Vp, P.v0, P.vstride, P.nunits, j);
     __syncthreads();
     for (int j = 0; j < d; ++j) {
         if (tid == 0) v[j] /= G[tri(j) + j];
@@ -698,6 +705,10 @@ void build_units(cw_batch* B, int slab) {
             cost.push_back((double)(U.r1 - U.r0) * fill * (double)(s.d * s.d + 64));
         }
         P.nunits = (int32_t)B->units.size() - P.unit0;
+        P.gstride = (s.d * (s.d + 1) / 2 + 31) & ~31ll;
+        P.vstride = (s.d + 31) & ~31ll;
+        P.g0 = P.nunits ? B->units[(size_t)P.unit0].goff : 0;
+        P.v0 = P.nunits ? B->units[(size_t)P.unit0].voff : 0;
     }
     B->uorder.resize(B->units.size());
     for (size_t u = 0; u < B->units.size(); ++u) B->uorder[u] = (int32_t)u;
