@@ -218,12 +218,17 @@ __device__ __forceinline__ void over_rows(const SolveProb& P, const UnitSmem& u,
 
 // ---------------------------------------------------------------- phase A
 
-// Partial Gram of the unit's non-empty rows: T x T blocks (jb, kb), jb >= kb,
-// of the lower triangle, one per thread (136 blocks for 16 x 16), so the
-// active threads fill whole warps; float32 sums over the slab.  c_j =
-// sum_i SA_ij Sb_i by threads j < d.  Padding columns of the tiles are zero.
+// Partial Gram of the unit's non-empty rows in T x T blocks of the lower
+// triangle (16 block rows at most), spread over the warps so that no
+// scheduler issues much more than one off-diagonal block's multiply-adds per
+// row (warp w runs on scheduler w % 4): threads 0..119 take the off-diagonal
+// blocks (jb > kb, T*T FMAs per row), threads 128..143 the lower triangles of
+// the diagonal blocks (T(T+1)/2 FMAs), threads 160..255 form c = SA^T Sb
+// (thread 160 + j for column j, then j + 96).  float32 sums over the slab;
+// padding columns of the tiles are zero.
 template <int T>
-__device__ void gram_unit(const SolveArgs& S, int ui, const SolveUnit& U, char* smem) {
+__device__ __noinline__ void gram_unit(const SolveArgs& S, int ui, const SolveUnit& U, char* smem) {
+    constexpr int NT = T * T;  // accumulators: T*T (off-diagonal) or T(T+1)/2 (diagonal)
     const SolveProb& P = S.probs[U.p];
     const int d = P.d, tid = threadIdx.x;
     const int ldt = 16 * T + 4;
@@ -238,21 +243,26 @@ __device__ void gram_unit(const SolveArgs& S, int ui, const SolveUnit& U, char* 
         u.tile[i * ldt + j] = 0.f;
     }
     const int nbd = (d + T - 1) / T;
-    const int nblk = nbd * (nbd + 1) / 2;
-    int jb = 0, kb = 0;
-    if (tid < nblk) {
-        while ((jb + 1) * (jb + 2) / 2 <= tid) ++jb;
-        kb = tid - jb * (jb + 1) / 2;
+    const int nod = nbd * (nbd - 1) / 2;
+    // role: 1 off-diagonal block (jb, kb), 2 diagonal blocks db, db + 1, 0 none
+    int role = 0, jb = 0, kb = 0;
+    if (tid < nod) {
+        role = 1;
+        jb = 1;
+        while (jb * (jb + 1) / 2 <= tid) ++jb;  // tid in [jb (jb - 1) / 2, jb (jb + 1) / 2)
+        kb = tid - jb * (jb - 1) / 2;
+    } else if (tid >= 128 && tid < 128 + nbd) {
+        role = 2;
+        jb = tid - 128;
     }
-    const bool active = tid < nblk;
-    float acc[T][T];
+    float acc[NT];
 #pragma unroll
-    for (int a = 0; a < T; ++a)
-#pragma unroll
-        for (int b = 0; b < T; ++b) acc[a][b] = 0.f;
-    float cacc = 0.f;
+    for (int e = 0; e < NT; ++e) acc[e] = 0.f;
+    float cacc = 0.f, cacc2 = 0.f;
+    const int cj = tid - 160;  // columns cj and cj + 96
     over_rows(P, u, total, [&](const float* tile, const float* tsb, int nr) {
-        if (active) {
+        if (role == 1) {
+#pragma unroll 1
             for (int i = 0; i < nr; ++i) {
                 const float* tr = tile + i * ldt;
                 float aj[T], ak[T];
@@ -274,23 +284,56 @@ __device__ void gram_unit(const SolveArgs& S, int ui, const SolveUnit& U, char* 
 #pragma unroll
                 for (int a = 0; a < T; ++a)
 #pragma unroll
-                    for (int b = 0; b < T; ++b) acc[a][b] = fmaf(aj[a], ak[b], acc[a][b]);
+                    for (int b = 0; b < T; ++b) acc[a * T + b] = fmaf(aj[a], ak[b], acc[a * T + b]);
+            }
+        } else if (role == 2) {
+#pragma unroll 1
+            for (int i = 0; i < nr; ++i) {
+                const float* tr = tile + i * ldt;
+                float x[T];
+                if constexpr (T >= 4) {
+#pragma unroll
+                    for (int a = 0; a < T; a += 4) {
+                        const float4 v = *reinterpret_cast<const float4*>(tr + jb * T + a);
+                        x[a] = v.x; x[a + 1] = v.y; x[a + 2] = v.z; x[a + 3] = v.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int a = 0; a < T; ++a) x[a] = tr[jb * T + a];
+                }
+#pragma unroll
+                for (int a = 0; a < T; ++a)
+#pragma unroll
+                    for (int b = 0; b <= a; ++b) acc[a * (a + 1) / 2 + b] = fmaf(x[a], x[b], acc[a * (a + 1) / 2 + b]);
             }
         }
-        if (tid < d)
-            for (int i = 0; i < nr; ++i) cacc = fmaf(tile[i * ldt + tid], tsb[i], cacc);
+        if (cj >= 0 && cj < d)
+            for (int i = 0; i < nr; ++i) cacc = fmaf(tile[i * ldt + cj], tsb[i], cacc);
+        if (cj >= 0 && cj + 96 < d)
+            for (int i = 0; i < nr; ++i) cacc2 = fmaf(tile[i * ldt + cj + 96], tsb[i], cacc2);
     });
     double* G = S.Gp + U.goff;
-    if (active) {
+    if (role == 1) {
+#pragma unroll
+        for (int a = 0; a < T; ++a) {
+            const int j = jb * T + a;
+            if (j < d) {
+                double* g = G + (j * (j + 1) / 2 + kb * T);
+#pragma unroll
+                for (int b = 0; b < T; ++b) g[b] = (double)acc[a * T + b];
+            }
+        }
+    } else if (role == 2) {
 #pragma unroll
         for (int a = 0; a < T; ++a)
 #pragma unroll
-            for (int b = 0; b < T; ++b) {
-                const int j = jb * T + a, k = kb * T + b;
-                if (j < d && k <= j) G[tri(j) + k] = (double)acc[a][b];
+            for (int b = 0; b <= a; ++b) {
+                const int j = jb * T + a, k = jb * T + b;
+                if (j < d) G[tri(j) + k] = (double)acc[a * (a + 1) / 2 + b];
             }
     }
-    if (tid < d) S.Vp[U.voff + tid] = (double)cacc;
+    if (cj >= 0 && cj < d) S.Vp[U.voff + cj] = (double)cacc;
+    if (cj >= 0 && cj + 96 < d) S.Vp[U.voff + cj + 96] = (double)cacc2;
 }
 
 // ---------------------------------------------------------------- phase B
