@@ -403,7 +403,19 @@ def row_timings(cw, A, b, stream, peak):
     rows["A3_sketch_dense_ms"] = ms
     rows["A3_sketch_dense_GBps"] = ab / (ms / 1000.0) / 1e9
     rows["A3_sketch_dense_frac"] = rows["A3_sketch_dense_GBps"] / peak
-    del SA3
+    # NEXT-2: sketch with values and its backward on the same dense A (one pass over A each)
+    vals = torch.randn(n3, device=A.row_ptr.device, generator=g)
+    gS = torch.randn(M, d3, device=A.row_ptr.device, generator=g)
+    ms = _timed(lambda: cw.cw_sketch_dense_values(A3, None, M, SEED, vals, SA3), stream, reps=reps)
+    rows["N2_values_forward_dense_ms"] = ms
+    rows["N2_values_forward_dense_frac"] = (ab + n3 * 4) / (ms / 1000.0) / 1e9 / peak
+    gv = torch.empty(n3, device=A.row_ptr.device)
+    ms = _timed(lambda: cw.cw_sketch_values_backward_dense(A3, None, M, SEED, gS, None, gv), stream, reps=reps)
+    bb = n3 * d3 * 4 + M * d3 * 4 + n3 * 4
+    rows["N2_values_backward_dense_ms"] = ms
+    rows["N2_values_backward_dense_GBps"] = bb / (ms / 1000.0) / 1e9
+    rows["N2_values_backward_dense_frac"] = rows["N2_values_backward_dense_GBps"] / peak
+    del SA3, vals, gS, gv
     lev_k = ("k_apply_dense_precise", "k_qr_blocked", "k_qr_householder", "k_qr_finalize", "k_trsm_upper",
              "k_m_digits", "k_leverage_tc", "k_leverage")
     cw.cw_leverage(A3, M, SEED, G3)
