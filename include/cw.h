@@ -219,8 +219,8 @@ typedef struct cw_batch cw_batch; /* opaque plan */
  * device memory (scratch, and SA / Sb where NULL), uploads the descriptors and
  * captures the batch in a CUDA graph: the batched sketch (eight launches over
  * all problems) and one persistent cooperative solve kernel.  With
- * CW_BATCH_AUTOTUNE, times three segmented-sum variants (16 or 32 lanes per
- * CSR row, or 16-bucket ranges per warp),
+ * CW_BATCH_AUTOTUNE, times four segmented-sum variants (16 or 32 lanes per
+ * CSR row, or 16- or 8-bucket ranges per warp),
  * then slab sizes {512, 1024, 2048, 4096} x {1, 2} CTAs per SM of the solve,
  * on the batch (running it) and keeps the fastest; the choice is
  * appended to the file named by the CW_TUNE_CACHE environment variable when
@@ -249,7 +249,7 @@ int cw_batch_finish(cw_batch *plan, cw_stream stream, int32_t *status, int32_t *
  * cw_batch_info - info[0..8] = slab rows, CTAs per SM, solve grid, graph in
  * use (1) or direct launches (0), work units, tuned (1 timed, 2 from the
  * cache, 0 defaults), plan device bytes, refinement steps at most, lanes per
- * CSR row of the segmented sum (16 or 32; 0: the 16-bucket range variant).
+ * CSR row of the segmented sum (16 or 32; 0 / -8: the 16- / 8-bucket range variants).
  * `info` holds 9 values.
  */
 int cw_batch_info(const cw_batch *plan, int64_t *info);

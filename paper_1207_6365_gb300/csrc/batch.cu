@@ -702,7 +702,7 @@ bool cache_lookup(uint64_t key, int* slab, int* cps, int* lpr) {
         unsigned long long k = 0;
         int a = 0, b = 0, c = 0;
         if (std::sscanf(line, "batch %llx %d %d %d", &k, &a, &b, &c) == 4 && k == key && a > 0 && b > 0 &&
-            (c == 16 || c == 32 || c == 0)) {
+            (c == 16 || c == 32 || c == 0 || c == -8)) {
             *slab = a;
             *cps = b;
             *lpr = c;
@@ -1066,7 +1066,7 @@ extern "C" int cw_batch_create(const cw_batch_problem* probs, int32_t count, int
         int best_lpr = B->sk.lpr;
         if (!B->sk.acc_global) {
             double bl = 1e30;
-            for (int lp : {16, 32, 0}) {
+            for (int lp : {16, 32, 0, -8}) {
                 if (batch_sketch_set_lpr(&B->sk, lp) != CW_OK) continue;
                 if (configure(B, slab, cps, use_graph) != CW_OK) continue;
                 const double ms = time_runs(B, s, 2);

@@ -81,8 +81,8 @@ struct BatchSketchHost {
 // for the given problems; pointers of `dev` are set by the caller.
 int batch_sketch_plan(const BatchSpec* specs, int count, BatchSketchHost* host, BatchSketch* dev);
 // Segmented-sum variant: lanes per CSR row (16: two rows at a time and two
-// accumulator copies; 32: one row, one copy), or 0: whole 16-bucket ranges at
-// a time (one accumulator row per bucket); sets the launch shape.
+// accumulator copies; 32: one row, one copy), or 0 / -8: whole 16- / 8-bucket
+// ranges at a time (one accumulator row per bucket); sets the launch shape.
 int batch_sketch_set_lpr(BatchSketch* dev, int lpr);
 // Enqueues the batched sketch (8 launches; capturable).
 int batch_sketch_enqueue(const BatchSketch& B, cudaStream_t stream);

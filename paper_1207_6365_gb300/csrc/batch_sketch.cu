@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(256) kb_apply_csr(BatchSketch B) {
 // own shared-memory row (nb x dpad floats per warp).  Rows are added in
 // ascending record order within each bucket, as in apply_csr_bucket with one
 // accumulator copy; Sb entries are summed per bucket in record order.
+template <int NB>
 __device__ __forceinline__ void apply_csr_range(const CsrApplyArgs& a, int bk0, int nb, int skip, float* acc,
                                                 int lane) {
     constexpr int U = 8;
@@ -155,13 +156,13 @@ __device__ __forceinline__ void apply_csr_range(const CsrApplyArgs& a, int bk0, 
             rr = __ldg(&a.rs[k]);
             // bucket of record k: the last j with start_j <= k
 #pragma unroll
-            for (int j = 1; j < kBatchApplyChunk; ++j) {
+            for (int j = 1; j < NB; ++j) {
                 const int sj = __shfl_sync(0xFFFFFFFFu, bs, j);
                 if (j < nb && sj <= k) bid = j;
             }
         } else {
 #pragma unroll
-            for (int j = 1; j < kBatchApplyChunk; ++j) (void)__shfl_sync(0xFFFFFFFFu, bs, j);
+            for (int j = 1; j < NB; ++j) (void)__shfl_sync(0xFFFFFFFFu, bs, j);
         }
         const int nrow = min(32, e - k0);
         for (int t0 = 0; t0 < nrow; t0 += U) {
@@ -226,19 +227,21 @@ __device__ __forceinline__ void apply_csr_range(const CsrApplyArgs& a, int bk0, 
     __syncwarp();
 }
 
-// Batched segmented sum over ranges of up to kBatchApplyChunk buckets (one
-// problem each; a grab that crosses a problem boundary is split).
-__global__ void __launch_bounds__(256) kb_apply_csr_range(BatchSketch B) {
+// Batched segmented sum over ranges of up to NB buckets (one problem each; a
+// grab that crosses a problem boundary is split).  NB = 8 halves the shared
+// accumulator rows per warp and is built for four CTAs per SM.
+template <int NB>
+__global__ void __launch_bounds__(256, NB == 8 ? 4 : 3) kb_apply_csr_range(BatchSketch B) {
     extern __shared__ __align__(16) float smacc[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* acc = smacc + (size_t)warp * kBatchApplyChunk * B.dpad;
+    float* acc = smacc + (size_t)warp * NB * B.dpad;
     CsrApplyArgs a{};
     for (;;) {
         unsigned g0 = 0;
-        if (lane == 0) g0 = atomicAdd(B.counter, (unsigned)kBatchApplyChunk);
+        if (lane == 0) g0 = atomicAdd(B.counter, (unsigned)NB);
         g0 = __shfl_sync(0xFFFFFFFFu, g0, 0);
         if ((int64_t)g0 >= B.total_buckets) break;
-        const int64_t g1 = min((int64_t)g0 + kBatchApplyChunk, B.total_buckets);
+        const int64_t g1 = min((int64_t)g0 + NB, B.total_buckets);
         for (int64_t gs = g0; gs < g1;) {
             int l = 0, r = B.count - 1;  // last p with bk_base[p] <= gs
             while (l < r) {
@@ -259,7 +262,7 @@ __global__ void __launch_bounds__(256) kb_apply_csr_range(BatchSketch B) {
             a.d = P.d;
             a.dpad = (int)((P.d + 31) & ~31) + 4;
             a.vec4 = P.vec4;
-            apply_csr_range(a, (int)(gs - B.bk_base[l]), (int)(pe - gs), P.skip_empty, acc, lane);
+            apply_csr_range<NB>(a, (int)(gs - B.bk_base[l]), (int)(pe - gs), P.skip_empty, acc, lane);
             gs = pe;
         }
     }
@@ -267,13 +270,15 @@ __global__ void __launch_bounds__(256) kb_apply_csr_range(BatchSketch B) {
 
 
 int batch_sketch_set_lpr(BatchSketch* dev, int lpr) {
-    if (lpr != 16 && lpr != 32 && lpr != 0) return CW_ERR_ARG;
-    if (lpr == 0 && dev->acc_global) return CW_ERR_ARG;
+    if (lpr != 16 && lpr != 32 && lpr != 0 && lpr != -8) return CW_ERR_ARG;
+    if (lpr <= 0 && dev->acc_global) return CW_ERR_ARG;
     dev->lpr = lpr;
-    if (lpr == 0) {
-        dev->acc_smem = (size_t)8 * kBatchApplyChunk * dev->dpad * sizeof(float);
-        if (set_smem(kb_apply_csr_range, dev->acc_smem) != cudaSuccess) return CW_ERR_CUDA;
-        dev->apply_grid = persistent_grid(kb_apply_csr_range, 256, dev->acc_smem);
+    if (lpr <= 0) {
+        const int nb = lpr == 0 ? 16 : 8;
+        dev->acc_smem = (size_t)8 * nb * dev->dpad * sizeof(float);
+        auto kf = lpr == 0 ? kb_apply_csr_range<16> : kb_apply_csr_range<8>;
+        if (set_smem(kf, dev->acc_smem) != cudaSuccess) return CW_ERR_CUDA;
+        dev->apply_grid = persistent_grid(kf, 256, dev->acc_smem);
         return CW_OK;
     }
     dev->acc_smem = dev->acc_global ? 0 : (size_t)8 * (32 / lpr) * dev->dpad * sizeof(float);
@@ -413,7 +418,10 @@ int batch_sketch_enqueue(const BatchSketch& B, cudaStream_t stream) {
         else if (B.lpr == 32)
             kb_apply_csr<32, 8><<<B.apply_grid, 256, B.acc_smem, stream>>>(B);
         else
-            kb_apply_csr_range<<<B.apply_grid, 256, B.acc_smem, stream>>>(B);
+            if (B.lpr == 0)
+                kb_apply_csr_range<16><<<B.apply_grid, 256, B.acc_smem, stream>>>(B);
+            else
+                kb_apply_csr_range<8><<<B.apply_grid, 256, B.acc_smem, stream>>>(B);
     }
     CW_LAUNCH_CHECK();
     return CW_OK;
