@@ -95,9 +95,17 @@ __global__ void __launch_bounds__(1024) k_qr_householder(QrArgs a) {
     if (!grid_barrier(a.bar, G, a.tflag)) return;
 
     for (int j = 0; j < a.d; ++j) {
-        // reflector for column j: every block forms the same scalars
-        double sig2 = 0.0;
-        for (unsigned c = 0; c < G; ++c) sig2 += a.normp[c];  // fixed order
+        // reflector for column j: every block forms the same scalars (lanes
+        // over blocks, then the warp's tree: the same fixed order everywhere)
+        if (warp == 0) {
+            double t = 0.0;
+            for (unsigned c = lane; c < G; c += 32) t += a.normp[c];
+            t = warp_sum(t);
+            if (lane == 0) s_red[0] = t;
+        }
+        __syncthreads();
+        const double sig2 = s_red[0];
+        __syncthreads();
         const double ajj = a.W[(int64_t)j * a.m + j];
         double beta, tau, vscale;
         if (sig2 == 0.0) {

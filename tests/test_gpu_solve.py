@@ -34,7 +34,11 @@ def _rho(A, b, x, rn):
     return oracle.residual_ratio_csr(A.row_ptr, A.col, A.val, b, x, rn)
 
 
-@pytest.mark.parametrize("m,d", [(4096, 32), (1000, 17), (300, 300)])
+# blocked kernel: one panel, several panels with a ragged last one, d = 1,
+# d = 33, d = m; unblocked fallback: 131075 rows do not fit one CTA's panel rows
+# in shared memory
+@pytest.mark.parametrize("m,d", [(4096, 32), (1000, 17), (300, 300), (20000, 100), (5000, 1), (70001, 33),
+                                 (131075, 40)])
 def test_qr_matches_oracle_on_same_matrix(cw, m, d):
     SA = W.dense_gaussian(m, d, seed=m + d).cuda()
     SA[:, 0] *= 1e3  # uneven column scales
