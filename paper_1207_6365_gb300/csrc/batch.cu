@@ -361,8 +361,8 @@ __device__ void chol_solve(const SolveArgs& S, int p, double* sm) {
         }
         __syncthreads();
         if (!ok) break;
-        const double ljj = G[tri(j) + j];
-        for (int i = j + 1 + tid; i < d; i += kSolveThreads) G[tri(i) + j] /= ljj;
+        const double rl = 1.0 / G[tri(j) + j];  // one division per column (float64 divides are long)
+        for (int i = j + 1 + tid; i < d; i += kSolveThreads) G[tri(i) + j] *= rl;
         __syncthreads();
         for (int i = j + 1 + warp; i < d; i += kSolveThreads / 32) {
             const double lij = G[tri(i) + j];
