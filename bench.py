@@ -684,11 +684,20 @@ def run_cw(args):
 
     rows = None
     if rank == 0 and not args.no_rows:
-        rows = row_timings(cw, A, b, stream, peak)
-        if not args.no_batch:
-            rows.update(batch_timings(cw, stream))
-        if not args.no_learned:
-            rows.update(learned_rows(cw))
+        # the other rows are reported, not required: a failure in one of them is
+        # recorded in the line instead of losing the line
+        rows = {}
+        for name, fn, skip in (("rows", lambda: row_timings(cw, A, b, stream, peak), False),
+                               ("N1", lambda: batch_timings(cw, stream), args.no_batch),
+                               ("N3", lambda: learned_rows(cw), args.no_learned)):
+            if skip:
+                continue
+            try:
+                rows.update(fn())
+            except Exception as exc:  # noqa: BLE001
+                rows[name + "_error"] = ("%s: %s" % (type(exc).__name__, exc))[-400:]
+                torch.cuda.synchronize()
+                torch.cuda.empty_cache()
 
     cpu_baseline = None
     if rank == 0 and not args.no_cpu_baseline:
