@@ -304,6 +304,19 @@ int cw_sketch_vec(const float *x, int64_t n, int64_t m, uint64_t seed, float *Sx
                   cw_stream stream);
 
 /*
+ * cw_gram - G = [SA | Sb]^T [SA | Sb], the Gram matrix whose Cholesky factor
+ * is the R of Section 7.6's preconditioner (R^T R = (SA)^T SA).
+ * SA: m x d float32 row-major (device); Sb: m float32 (device) or NULL.
+ * G: (d+1) x (d+1) float64 row-major (device, caller-owned), symmetric; d x d
+ * when Sb is NULL.  For d <= 256 on the tensor cores with three TF32 products
+ * per pair (hi*hi + hi*lo + lo*hi), accumulated in float32 within a CTA's rows
+ * and in float64 across CTAs (fixed order: deterministic); larger d on the CUDA
+ * cores (float32 tiles, float64 partials).  Requires 1 <= d <= 1024, m >= 1.
+ * CW_ERR_TIMEOUT if a bounded tensor-core wait gave up.  Synchronises.
+ */
+int cw_gram(const float *SA, int64_t m, int64_t d, const float *Sb, double *G, cw_stream stream);
+
+/*
  * cw_qr - Householder QR of the m x d float32 matrix SA in float64 (the
  * factorisation used in the proof of Theorem "renRegAlg").
  * R: d x d row-major float64, upper triangular with a positive diagonal.

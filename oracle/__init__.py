@@ -331,6 +331,19 @@ def qr_r(SA, Sb=None):
     return R, c
 
 
+def gram(SA, Sb=None):
+    """[SA | Sb]^T [SA | Sb] in float64 (d x d without Sb).
+
+    Section 7.6 preconditions with any R for which SA R^-1 has orthonormal
+    columns up to scale; the Cholesky factor of this Gram matrix is such an R
+    (R^T R = (SA)^T SA).
+    """
+    X = np.asarray(SA, dtype=np.float64)
+    if Sb is not None:
+        X = np.concatenate([X, np.asarray(Sb, dtype=np.float64)[:, None]], axis=1)
+    return X.T @ X
+
+
 def solve_sketch(SA, Sb):
     """x' = argmin ||SA x - Sb|| = R^-1 Q^T Sb (proof of Theorem "renRegAlg")."""
     R, c = qr_r(SA, Sb)

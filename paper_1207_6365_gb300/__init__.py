@@ -19,7 +19,7 @@ from . import _build
 __all__ = [
     "CWError", "lib", "load", "status_string", "device_status", "cw_csr_check",
     "cw_hash", "cw_sketch_csr", "cw_sketch_csr_rows", "cw_sketch_csr_general", "cw_sketch_dense", "cw_sketch_vec",
-    "cw_qr", "cw_solve_sketch", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
+    "cw_gram", "cw_qr", "cw_solve_sketch", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
     "cw_sketch_csr_values", "cw_sketch_dense_values", "cw_sketch_values_backward_csr",
     "cw_sketch_values_backward_dense", "SketchValues", "Batch", "EXPORTS", "HEADER",
 ]
@@ -28,7 +28,7 @@ HEADER = os.path.join(_build.ROOT, "include", "cw.h")
 EXPORTS = (
     "cw_status_string", "cw_version", "cw_device_status", "cw_csr_check", "cw_hash", "cw_sketch_csr",
     "cw_sketch_csr_rows", "cw_sketch_csr_general", "cw_sketch_csr_noalloc", "cw_sketch_dense", "cw_sketch_vec",
-    "cw_qr", "cw_solve_sketch", "cw_batch_create", "cw_batch_run", "cw_batch_finish", "cw_batch_info",
+    "cw_gram", "cw_qr", "cw_solve_sketch", "cw_batch_create", "cw_batch_run", "cw_batch_finish", "cw_batch_info",
     "cw_batch_phases", "cw_batch_destroy", "cw_sketch_csr_values", "cw_sketch_dense_values",
     "cw_sketch_values_backward_csr", "cw_sketch_values_backward_dense", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
     "cw_launch_count", "cw_profile_enable", "cw_profile_get", "cw_profile_reset",
@@ -86,6 +86,7 @@ _SIGS = {
     "cw_lsqr_precond": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _f64, _i32, _p,
                          ctypes.POINTER(_i32), ctypes.POINTER(_f64), _p], ctypes.c_int),
     "cw_leverage": ([_p, _i64, _i64, _i64, _i64, _u64, _i32, _p, _p, _p], ctypes.c_int),
+    "cw_gram": ([_p, _i64, _i64, _p, _p, _p], ctypes.c_int),
     "cw_launch_count": ([], ctypes.c_longlong),
     "cw_profile_enable": ([ctypes.c_int], ctypes.c_int),
     "cw_profile_get": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_f64)], ctypes.c_int),
@@ -250,6 +251,16 @@ def cw_sketch_vec(x, m, seed, Sx=None):
     _check(load().cw_sketch_vec(_ptr(x, torch.float32, "x"), x.numel(), m, seed,
                                 _ptr(Sx, torch.float32, "Sx"), _stream()), "cw_sketch_vec")
     return Sx
+
+
+def cw_gram(SA, Sb=None):
+    """[SA | Sb]^T [SA | Sb] (float64, (d+1) x (d+1); d x d without Sb)."""
+    m, d = SA.shape
+    nc = d + (1 if Sb is not None else 0)
+    G = torch.empty(nc, nc, dtype=torch.float64, device=SA.device)
+    _check(load().cw_gram(_ptr(SA, torch.float32, "SA"), m, d, _ptr(Sb, torch.float32, "Sb"),
+                          _ptr(G, torch.float64, "G"), _stream()), "cw_gram")
+    return G
 
 
 def cw_qr(SA, Sb=None):

@@ -42,6 +42,12 @@ int qr64(const float* SA, int64_t m, int d, const float* Sb, double* R, double* 
 int trsv_upper(const double* R, int d, const double* rhs, double* x, cudaStream_t stream);
 int trsm_upper(const double* R, int d, const double* B, int k, double* X, cudaStream_t stream);
 int tri_inverse(const double* R, int d, double* M, cudaStream_t stream);
+// [SA | Sb]^T [SA | Sb] (float64, symmetric, nc = d + (Sb != NULL)) on the
+// tensor cores (3xTF32); CW_ERR_SHAPE when d > 256.
+int gram_tc(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsigned* tflag, cudaStream_t stream);
+// The same Gram matrix for any d <= 1024: tensor cores when d <= 256, float32
+// CUDA-core tiles with float64 partials otherwise.
+int gram_f64(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsigned* tflag, cudaStream_t stream);
 // Gram + Cholesky + explicit inverse in shared memory (LSQR preconditioner).
 int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double* M, float* M32T, double* c,
                       float* kappa_lb_host, cudaStream_t stream);

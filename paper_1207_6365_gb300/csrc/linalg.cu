@@ -1309,14 +1309,12 @@ int qr64(const float* SA, int64_t m, int d, const float* Sb, double* R, double* 
     return CW_OK;
 }
 
-// Gram + Cholesky + inverse for the LSQR preconditioner.  M (float64 d x d,
-// float32 values), M32T (float32, column-major) and c = R^-T SA^T Sb; *kappa_lb
-// receives the diagonal ratio of R.  Returns CW_ERR_RANK on a non-positive
-// pivot.  Synchronises (the caller needs the ratio on the host).
-int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double* M, float* M32T, double* c,
-                      float* kappa_lb_host, cudaStream_t stream) {
+// [SA | Sb]^T [SA | Sb] (float64, nc x nc, nc = d + (Sb != NULL)).  Does not
+// synchronise; an MMA wait of the tensor-core kernel that gave up sets *tflag.
+int gram_f64(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsigned* tflag, cudaStream_t stream) {
+    if (d < 1 || d > 1024) return CW_ERR_SHAPE;
+    if (d <= 256) return gram_tc(SA, m, d, Sb, Gm, tflag, stream);
     const int nc = d + (Sb ? 1 : 0);
-    if (d > 1024) return CW_ERR_SHAPE;
     const int ntile = (d + kGT - 1) / kGT;
     const int ntl = ntile * (ntile + 1) / 2;
     // rows per chunk: about one CTA per SM in one wave (146 registers a thread)
@@ -1327,27 +1325,48 @@ int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double
     Scratch ws(stream);
     const size_t oP = ws.reserve(sizeof(double) * (size_t)nchunk * ntl * kGT * kGT);
     const size_t oV = ws.reserve(sizeof(double) * (size_t)nchunk * (d + 1));
-    const size_t oG = ws.reserve(sizeof(double) * (size_t)nc * nc);
-    const size_t oW = ws.reserve(sizeof(float) * (size_t)nc * nc);
-    const size_t oF = ws.reserve(sizeof(unsigned) * 2 + sizeof(float) * 2);
     CW_CUDA_TRY(ws.alloc());
     double* part = ws.at<double>(oP);
     double* vpart = ws.at<double>(oV);
-    double* Gm = ws.at<double>(oG);
-    float* W = ws.at<float>(oW);
-    unsigned* bad = ws.at<unsigned>(oF);
-    float* klb = reinterpret_cast<float*>(bad + 2);
-    CW_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned) * 2 + sizeof(float) * 2, stream));
+    const int64_t tot = (int64_t)nc * nc;
     {
         CW_PROF("k_gram_tile", stream);
         k_gram_tile<<<dim3((unsigned)ntl, (unsigned)nchunk), 256, 0, stream>>>(SA, Sb, m, d, ntile, (int)rows, part,
                                                                              vpart);
     }
-    const int64_t tot = (int64_t)nc * nc;
     {
         CW_PROF("k_gram_reduce", stream);
         k_gram_reduce2<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(part, vpart, nchunk, ntile, d, nc, Gm);
     }
+    CW_LAUNCH_CHECK();
+    return CW_OK;
+}
+
+// Gram + Cholesky + inverse for the LSQR preconditioner.  M (float64 d x d,
+// float32 values), M32T (float32, column-major) and c = R^-T SA^T Sb; *kappa_lb
+// receives the diagonal ratio of R.  Returns CW_ERR_RANK on a non-positive
+// pivot.  Synchronises (the caller needs the ratio on the host).
+int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double* M, float* M32T, double* c,
+                      float* kappa_lb_host, cudaStream_t stream) {
+    const int nc = d + (Sb ? 1 : 0);
+    if (d > 1024) return CW_ERR_SHAPE;
+    Scratch ws(stream);
+    const size_t oG = ws.reserve(sizeof(double) * (size_t)nc * nc);
+    const size_t oW = ws.reserve(sizeof(float) * (size_t)nc * nc);
+    const size_t oF = ws.reserve(sizeof(unsigned) * 2 + sizeof(float) * 2);
+    const int nb = (d + kCholB - 1) / kCholB;
+    const size_t oD = ws.reserve(sizeof(float) * (size_t)nb * kCholB * kCholB);   // diagonal block inverses
+    CW_CUDA_TRY(ws.alloc());
+    double* Gm = ws.at<double>(oG);
+    float* W = ws.at<float>(oW);
+    float* Dinv = ws.at<float>(oD);
+    unsigned* bad = ws.at<unsigned>(oF);
+    float* klb = reinterpret_cast<float*>(bad + 2);
+    CW_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned) * 2 + sizeof(float) * 2, stream));
+    const int64_t tot = (int64_t)nc * nc;
+    // bad[1]: an MMA wait of the tensor-core Gram gave up
+    int gst = gram_f64(SA, m, d, Sb, Gm, bad + 1, stream);
+    if (gst != CW_OK) return gst;
     {
         CW_PROF("k_gram_to_f32", stream);
         k_gram_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(Gm, tot, W);
@@ -1382,8 +1401,6 @@ int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double
     }
     // M = R^-1: diagonal block inverses, then one CTA per block column
     {
-        const int nb = (d + kCholB - 1) / kCholB;
-        float* Dinv = reinterpret_cast<float*>(Gm);   // Gram no longer needed; nb * 32 * 32 floats fit
         {
             CW_PROF("k_tri_diag_inv", stream);
             k_tri_diag_inv<<<nb, 32, 0, stream>>>(W, d, nc, Dinv);
@@ -1408,6 +1425,7 @@ int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double
     CW_CUDA_TRY(cudaMemcpyAsync(kl, klb, sizeof(float) * 2, cudaMemcpyDeviceToHost, stream));
     CW_CUDA_TRY(cudaStreamSynchronize(stream));
     if (kappa_lb_host) *kappa_lb_host = kl[0];
+    if (h[1]) return CW_ERR_TIMEOUT;
     return h[0] ? CW_ERR_RANK : CW_OK;
 }
 
@@ -1452,6 +1470,25 @@ int trsm_upper(const double* R, int d, const double* B, int k, double* X, cudaSt
 }  // namespace cw
 
 using namespace cw;
+
+extern "C" int cw_gram(const float* SA, int64_t m, int64_t d, const float* Sb, double* G, cw_stream stream) {
+    if (!SA || !G) return CW_ERR_ARG;
+    if (d < 1 || d > 1024 || m < 1) return CW_ERR_SHAPE;
+    if (m > 0x7FFFFFFFll) return CW_ERR_OVERFLOW;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned* flag = nullptr;
+    CW_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&flag), sizeof(unsigned), s));
+    int st = CW_OK;
+    unsigned h = 0;
+    if (cudaMemsetAsync(flag, 0, sizeof(unsigned), s) != cudaSuccess) st = CW_ERR_CUDA;
+    if (st == CW_OK) st = gram_f64(SA, m, (int)d, Sb, G, flag, s);
+    if (st == CW_OK && cudaMemcpyAsync(&h, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        st = CW_ERR_CUDA;
+    cudaFreeAsync(flag, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == CW_OK) st = CW_ERR_CUDA;
+    if (st == CW_OK && h) st = CW_ERR_TIMEOUT;
+    return st;
+}
 
 extern "C" int cw_qr(const float* SA, int64_t m, int64_t d, const float* Sb, double* R, double* c,
                      cw_stream stream) {

@@ -23,7 +23,7 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for n in ("cw_sketch_csr", "cw_sketch_dense", "cw_sketch_vec", "cw_solve_sketch", "cw_lsqr_precond",
-              "cw_leverage", "cw_hash", "cw_qr", "cw_sketch_csr_general"):
+              "cw_leverage", "cw_hash", "cw_qr", "cw_gram", "cw_sketch_csr_general"):
         assert n in names
 
 
@@ -66,6 +66,11 @@ def test_host_side_validation_rejects_bad_arguments():
     assert lib.cw_sketch_dense(null, 10, 4, 2, null, 8, 1, ctypes.c_void_p(16), null, null) == -1
     assert lib.cw_sketch_dense(ctypes.c_void_p(16), 10, 4, 2, null, 8, 1, ctypes.c_void_p(16), null, null) == -2
     assert lib.cw_qr(ctypes.c_void_p(16), 4, 8, null, null, null, null) == -2
+    assert lib.cw_gram(null, 4, 8, null, ctypes.c_void_p(16), null) == -1
+    assert lib.cw_gram(ctypes.c_void_p(16), 4, 8, null, null, null) == -1
+    assert lib.cw_gram(ctypes.c_void_p(16), 4, 0, null, ctypes.c_void_p(16), null) == -2
+    assert lib.cw_gram(ctypes.c_void_p(16), 4, 1025, null, ctypes.c_void_p(16), null) == -2
+    assert lib.cw_gram(ctypes.c_void_p(16), 0, 8, null, ctypes.c_void_p(16), null) == -2
     it = ctypes.c_int32(0)
     ft = ctypes.c_double(0)
     c.nnz = 10

@@ -134,7 +134,8 @@ def test_lsqr_ragged_rows(cw):
     (150000, 300, 8, 4096, 7),    # one-CTA Cholesky, last panel 12 columns wide
     (80000, 400, 6, 8192, 8),     # packed triangle too large for one CTA: panel kernels
     (30000, 1, 1, 64, 9),         # a single column
-    (50000, 33, 5, 512, 10)])     # two panels, the second one column wide
+    (50000, 33, 5, 512, 10),      # two panels, the second one column wide
+    (60000, 150, 6, 2048, 11)])   # tensor-core Gram with two accumulator blocks, element loads
 def test_lsqr_shapes(cw, n, d, k, m, seed):
     A = W.csr_uniform(n, d, k, seed=seed + 40)
     b, _ = W.rhs(A, 0.1, seed=seed + 50)

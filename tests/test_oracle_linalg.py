@@ -43,6 +43,33 @@ def test_qr_r_is_cholesky_factor_and_orthogonal():
     np.testing.assert_allclose(c, Q.T @ Sb, atol=1e-9 * np.linalg.norm(Sb))
 
 
+def test_gram_against_qr_and_brute_force():
+    """The Gram matrix pinned two ways: R^T R from the Householder QR (LAPACK,
+    another algorithm), with the Sb column R^T c and corner ||Sb||^2, and a
+    plain triple loop on a tiny case."""
+    A, b, SA, Sb = _problem(d=9, m=96)
+    G = oracle.gram(SA, Sb)
+    R, c = oracle.qr_r(SA, Sb)
+    d = SA.shape[1]
+    scale = np.abs(G).max()
+    np.testing.assert_allclose(G[:d, :d], R.T @ R, atol=1e-12 * scale)
+    np.testing.assert_allclose(G[:d, d], R.T @ c, atol=1e-12 * scale)
+    np.testing.assert_allclose(G[d, :d], G[:d, d], rtol=0, atol=0)
+    assert abs(G[d, d] - float(np.dot(Sb.astype(np.float64), Sb.astype(np.float64)))) <= 1e-12 * scale
+    np.testing.assert_array_equal(oracle.gram(SA), G[:d, :d])
+    X = np.random.default_rng(3).standard_normal((5, 3))
+    y = np.random.default_rng(4).standard_normal(5)
+    Gt = oracle.gram(X, y)
+    for i in range(4):
+        for j in range(4):
+            s = 0.0
+            for r in range(5):
+                u = X[r, i] if i < 3 else y[r]
+                v = X[r, j] if j < 3 else y[r]
+                s += u * v
+            assert abs(Gt[i, j] - s) <= 1e-12
+
+
 def test_solve_sketch_matches_svd_lstsq():
     A, b, SA, Sb = _problem()
     x, R = oracle.solve_sketch(SA, Sb)
