@@ -310,7 +310,8 @@ int cw_sketch_vec(const float *x, int64_t n, int64_t m, uint64_t seed, float *Sx
  * G: (d+1) x (d+1) float64 row-major (device, caller-owned), symmetric; d x d
  * when Sb is NULL.  For d <= 256 on the tensor cores with three TF32 products
  * per pair (hi*hi + hi*lo + lo*hi), accumulated in float32 within a CTA's rows
- * and in float64 across CTAs (fixed order: deterministic); larger d on the CUDA
+ * and as float32 two-word sums across CTAs (fixed order: deterministic);
+ * larger d on the CUDA
  * cores (float32 tiles, float64 partials).  Requires 1 <= d <= 1024, m >= 1.
  * CW_ERR_TIMEOUT if a bounded tensor-core wait gave up.  Synchronises.
  */

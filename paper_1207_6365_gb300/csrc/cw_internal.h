@@ -49,7 +49,11 @@ int gram_tc(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsi
 // CUDA-core tiles with float64 partials otherwise.
 int gram_f64(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsigned* tflag, cudaStream_t stream);
 // Gram + Cholesky + explicit inverse in shared memory (LSQR preconditioner).
+// With flags_dev NULL it synchronises and returns CW_ERR_RANK (non-positive
+// pivot) or CW_ERR_TIMEOUT, *kappa_lb_host receiving R's diagonal ratio.
+// With flags_dev (device, 16 bytes) it does not synchronise: flags_dev[0] =
+// failed pivot, [1] = tensor-core wait gave up, float at [2] = diagonal ratio.
 int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double* M, float* M32T, double* c,
-                      float* kappa_lb_host, cudaStream_t stream);
+                      float* kappa_lb_host, cudaStream_t stream, unsigned* flags_dev = nullptr);
 
 }  // namespace cw

@@ -18,7 +18,7 @@
 // 128..dp-1 (the lower-left block is the transpose of the upper-right), three
 // products per K-step of 8.  Operands and staging are double-buffered; the
 // stage's MMAs are tracked by an mbarrier (bounded waits).  Per-CTA partials
-// are reduced over CTAs in float64 in a fixed order.
+// are reduced over CTAs in a fixed order (float32 two-word sums).
 #include <cstdint>
 
 #include "cw_common.cuh"
@@ -46,6 +46,11 @@ __device__ __forceinline__ uint64_t gt_desc(uint32_t saddr) {
            ((uint64_t)((kGtSBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
+// floats between two CTAs' partial Gram matrices: dp^2 plus one 128-byte line,
+// so that the reduction's loads of one entry over all CTAs (a power-of-two
+// stride otherwise) spread over the memory partitions
+__host__ __device__ __forceinline__ size_t gt_pstride(int dp) { return (size_t)dp * dp + 32; }
+
 // byte offset of (operand row r, K index k) in a tile
 __device__ __forceinline__ int gt_off(int r, int k) { return (r >> 3) * kGtSBO + (k >> 2) * kGtLBO + (r & 7) * 16; }
 
@@ -60,7 +65,8 @@ struct GramTcArgs {
     int64_t m;
     int d, dp;          // columns, padded to a multiple of 16
     int64_t rows_per;   // rows per CTA (a multiple of kGtKC)
-    float* part;        // [grid][dp][dp] partial Gram (rows 0..127: all columns; rows >= 128: columns >= 128)
+    float* part;        // [grid] partial Gram matrices dp x dp, gt_pstride(dp) floats apart (rows 0..127: all
+                        // columns; rows >= 128: columns >= 128)
     float* vpart;       // [grid][d + 1] partial SA^T Sb and Sb^T Sb
     unsigned* tflag;    // set when an MMA wait gave up
 };
@@ -224,7 +230,7 @@ __global__ void __launch_bounds__(kGtThreads, 1) k_gram_tc(GramTcArgs a) {
         // drain: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (Gram rows), half w / 4 of the columns
         const int quarter = warp & 3, half = warp >> 2;
         const int row = 32 * quarter + lane;
-        float* prow = a.part + (size_t)blockIdx.x * dp * dp;
+        float* prow = a.part + (size_t)blockIdx.x * gt_pstride(dp);
         for (int blk = 0; blk < (dp > 128 ? 2 : 1); ++blk) {
             // whole 16-column chunks (one tcgen05.ld each) split between the two halves
             const int nch = (blk ? dp - 128 : dp) / 16, h0 = (nch + 1) / 2;
@@ -265,32 +271,63 @@ __global__ void __launch_bounds__(kGtThreads, 1) k_gram_tc(GramTcArgs a) {
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
 }
 
-// Gm (nc x nc, symmetric, float64) = sum over CTAs of the partials, fixed order.
-__global__ void k_gram_tc_reduce(const float* __restrict__ part, const float* __restrict__ vpart, int grid, int d,
-                                 int dp, int nc, double* __restrict__ Gm) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)nc * nc) return;
-    const int ci = (int)(idx / nc), cj = (int)(idx % nc);
-    if (ci > cj) return;
-    double s0 = 0.0, s1 = 0.0;
-    int c = 0;
-    if (cj < d) {
-        const size_t off = (size_t)ci * dp + cj, stride = (size_t)dp * dp;
-        for (; c + 1 < grid; c += 2) {
-            s0 += (double)part[(size_t)c * stride + off];
-            s1 += (double)part[(size_t)(c + 1) * stride + off];
+// float32 two-word sum (hi, lo) += (xh, xl): TwoSum of the high parts, the
+// low parts and the rounding error carried in lo
+__device__ __forceinline__ void gt_two_add(float& hi, float& lo, float xh, float xl) {
+    const float t = __fadd_rn(hi, xh);
+    const float bp = __fsub_rn(t, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(xh, bp)), xl));
+    hi = t;
+}
+
+// Gm (nc x nc, symmetric, float64) = sum over CTAs of the partials.  Block
+// (x, y) covers entries (ci = y, cj = 32 x + lane) with cj >= ci; warp w adds
+// the partials of CTAs [w * cpw, (w + 1) * cpw) as float32 two-word sums
+// (float64 arithmetic issues at 1/64 of the float32 rate on this part; two
+// words carry ~44 bits, far below the 3xTF32 product error), eight loads
+// issued before their adds, and warp 0 adds the eight warp sums in order:
+// the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) k_gram_tc_reduce(const float* __restrict__ part,
+                                                        const float* __restrict__ vpart, int grid, int d, int dp,
+                                                        int nc, double* __restrict__ Gm) {
+    const int ci = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if ((int)blockIdx.x * 32 + 31 < ci) return;   // the whole block below the diagonal
+    __shared__ float2 sp[8][32];
+    const int cj = blockIdx.x * 32 + lane;
+    const bool act = cj < nc && cj >= ci;
+    const float* src = nullptr;
+    size_t stride = 0;
+    if (act) {
+        if (cj < d) {
+            src = part + (size_t)ci * dp + cj;
+            stride = gt_pstride(dp);
+        } else {
+            src = vpart + ci;
+            stride = (size_t)d + 1;
         }
-        if (c < grid) s0 += (double)part[(size_t)c * stride + off];
-    } else {
-        for (; c + 1 < grid; c += 2) {
-            s0 += (double)vpart[(size_t)c * (d + 1) + ci];
-            s1 += (double)vpart[(size_t)(c + 1) * (d + 1) + ci];
-        }
-        if (c < grid) s0 += (double)vpart[(size_t)c * (d + 1) + ci];
     }
-    const double s = s0 + s1;
-    Gm[(int64_t)ci * nc + cj] = s;
-    Gm[(int64_t)cj * nc + ci] = s;
+    const int cpw = (grid + 7) / 8, c0 = warp * cpw, c1 = min(grid, c0 + cpw);
+    float hi = 0.f, lo = 0.f;
+    if (act) {
+        for (int c = c0; c < c1; c += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = c + u < c1 ? __ldg(src + (size_t)(c + u) * stride) : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (c + u < c1) gt_two_add(hi, lo, v[u], 0.f);
+        }
+    }
+    sp[warp][lane] = make_float2(hi, lo);
+    __syncthreads();
+    if (warp == 0 && act) {
+        float th = sp[0][lane].x, tl = sp[0][lane].y;
+#pragma unroll
+        for (int w = 1; w < 8; ++w) gt_two_add(th, tl, sp[w][lane].x, sp[w][lane].y);
+        const double t = (double)th + (double)tl;
+        Gm[(int64_t)ci * nc + cj] = t;
+        Gm[(int64_t)cj * nc + ci] = t;
+    }
 }
 
 }  // namespace
@@ -313,7 +350,7 @@ int gram_tc(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsi
     grid = (int)((m + rows_per - 1) / rows_per);
     const int nc = d + (Sb ? 1 : 0);
     Scratch ws(stream);
-    const size_t oP = ws.reserve(sizeof(float) * (size_t)grid * dp * dp);
+    const size_t oP = ws.reserve(sizeof(float) * (size_t)grid * gt_pstride(dp));
     const size_t oV = ws.reserve(sizeof(float) * (size_t)grid * (d + 1));
     const size_t oF = ws.reserve(sizeof(unsigned) * 2);
     CW_CUDA_TRY(ws.alloc());
@@ -326,10 +363,10 @@ int gram_tc(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsi
         k_gram_tc<<<grid, kGtThreads, kGtSmem, stream>>>(a);
     }
     CW_LAUNCH_CHECK();
-    const int64_t tot = (int64_t)nc * nc;
     {
         CW_PROF("k_gram_tc_reduce", stream);
-        k_gram_tc_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(a.part, a.vpart, grid, d, dp, nc, Gm);
+        k_gram_tc_reduce<<<dim3((unsigned)((nc + 31) / 32), (unsigned)nc), 256, 0, stream>>>(a.part, a.vpart, grid, d,
+                                                                                            dp, nc, Gm);
     }
     CW_LAUNCH_CHECK();
     if (tflag_ext) return CW_OK;

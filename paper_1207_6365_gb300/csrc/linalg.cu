@@ -1347,7 +1347,7 @@ int gram_f64(const float* SA, int64_t m, int d, const float* Sb, double* Gm, uns
 // receives the diagonal ratio of R.  Returns CW_ERR_RANK on a non-positive
 // pivot.  Synchronises (the caller needs the ratio on the host).
 int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double* M, float* M32T, double* c,
-                      float* kappa_lb_host, cudaStream_t stream) {
+                      float* kappa_lb_host, cudaStream_t stream, unsigned* flags_dev) {
     const int nc = d + (Sb ? 1 : 0);
     if (d > 1024) return CW_ERR_SHAPE;
     Scratch ws(stream);
@@ -1419,6 +1419,11 @@ int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double
         }
     }
     CW_LAUNCH_CHECK();
+    if (flags_dev) {   // the caller reads the flags later
+        CW_CUDA_TRY(cudaMemcpyAsync(flags_dev, bad, sizeof(unsigned) * 2 + sizeof(float) * 2, cudaMemcpyDeviceToDevice,
+                                    stream));
+        return CW_OK;
+    }
     unsigned h[2] = {0, 0};
     float kl[2] = {0.f, 0.f};
     CW_CUDA_TRY(cudaMemcpyAsync(h, bad, sizeof(unsigned) * 2, cudaMemcpyDeviceToHost, stream));

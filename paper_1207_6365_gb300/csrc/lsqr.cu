@@ -299,12 +299,11 @@ struct PostArgs {
     int nblk;
     int d;
     const float* M32T;    // M = R^-1 (float32 values), column-major: M32T[j * d + i] = M_ij
-    const float* M32P;    // the same, packed by columns: M_ij (i <= j) at j (j + 1) / 2 + i
+    const double* M;      // the same values, float64 row-major
     const double* y0;     // R x0
     double* v;
     double* w;
     double* dy;
-    double* g;            // scratch d
     float* vhat;          // out: M v (float32)
     LsqrState* st;
     double rtol;
@@ -312,268 +311,246 @@ struct PostArgs {
     int first;
 };
 
-// Sum over the block, the same on every thread and in every run: a shuffle
-// tree in each warp (skipped by warps whose values are all zero), then warp 0
-// adds the per-warp sums the same way.  float64 issues slowly on this part,
-// so only these few warp instructions use it.  red: 33 doubles.
-__device__ double block_sum(double v, double* red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (__any_sync(0xFFFFFFFFu, v != 0.0))
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        double t = lane < nw ? red[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
-        if (lane == 0) red[32] = t;
-    }
-    __syncthreads();
-    return red[32];
+// One LSQR step on P CTAs (one cooperative launch, three bounded grid
+// barriers), CTA c owning the columns [c * per, (c + 1) * per) of every
+// length-d vector:
+//   1. g_j = sum over pass blocks of the two-word partials (A^T z)_j;
+//   2. t_j = (M^T g)_j (two-word products and sums), gv_j = s t_j - beta v_j,
+//      and the CTA's share of ||gv||^2;
+//   3. alpha from the shares (every CTA adds them in the same order), the
+//      plane rotation from the state (every CTA alike), v, w, dy, and the
+//      share of ||y0 + dy||^2;
+//   4. CTA 0 updates the state; vhat_i = (M v)_i in float32 for the CTA's rows.
+// Every sum has a fixed order, so the results are the same in every run.
+struct PostMcArgs {
+    PostArgs p;
+    float2* gsum;       // d: g as (hi, lo)
+    double* tv;         // d: gv
+    double* share;      // [2][P]: shares of ||gv||^2 and ||y||^2
+    unsigned* bar;      // grid barrier words (zero at the first launch)
+    unsigned* tflag;    // set when a barrier wait gave up
+};
+
+__device__ __forceinline__ void two_add(float& hi, float& lo, float xh, float xl) {
+    const float t = __fadd_rn(hi, xh);
+    const float bp = __fsub_rn(t, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(xh, bp)), xl));
+    hi = t;
 }
 
-// SMEM_M: the packed triangle of M is copied to shared memory at the start
-// (one round of 16-byte copies, overlapped with the partial-sum reduction),
-// and both products with M read it from there.
-template <bool SMEM_M>
-__global__ void __launch_bounds__(1024) k_lsqr_post(PostArgs a) {
-    extern __shared__ __align__(16) float Ms[];
-    __shared__ double red[33];
-    __shared__ double sg[1024];
-    __shared__ double sv[1024];
-    LsqrState* st = a.st;
-    if (st->done) return;
-    const int d = a.d;
-    if (SMEM_M) {
-        const int nq = (d * (d + 1) / 2 + 3) / 4;
-        for (int q = threadIdx.x; q < nq; q += blockDim.x) cp_async16(Ms + 4 * q, a.M32P + 4 * q);
-        cp_async_commit();
-    }
-    // reduce the pass partials (two-word sums) -> g = A^T z as float32 (hi, lo)
-    // pairs in shared memory: `gp` threads per column, thread g taking blocks
-    // g, g + gp, ... in order, eight independent loads in flight (the next
-    // eight issued before the current ones are added); the gp sums combined in order
-    __shared__ float ghi[1024], glo[1024];
-    {
-        __shared__ float2 gstripe[1024];
-        const int gp = blockDim.x / d >= 4 ? 4 : (blockDim.x / d >= 2 ? 2 : 1);
-        constexpr int U = 8;
-        for (int tq = threadIdx.x; tq < d * gp; tq += blockDim.x) {
-            const int j = tq % d, g = tq / d;
-            const int nb = (a.nblk - g + gp - 1) / gp;   // blocks g + gp * t, t < nb
-            float hi = 0.f, lo = 0.f;
-            float2 cur[U], nxt[U];
+// sum of x[0..cnt) in float64 in a fixed order, the same value on every lane
+__device__ __forceinline__ double warp_sum_fixed(const double* x, int cnt, int lane) {
+    double v = 0.0;
+    for (int k = lane; k < cnt; k += 32) v += __ldcg(x + k);
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                cur[u] = u < nb ? a.gpart[(size_t)(g + gp * u) * d + j] : make_float2(0.f, 0.f);
-            for (int t0 = 0; t0 < nb; t0 += U) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_lsqr_post_mc(PostMcArgs a) {
+    const PostArgs& q = a.p;
+    LsqrState* st = q.st;
+    if (st->done || *reinterpret_cast<volatile unsigned*>(a.tflag)) return;
+    const int d = q.d, P = gridDim.x, cta = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int per = (d + P - 1) / P, j0 = cta * per, j1 = min(d, j0 + per);
+    __shared__ double s_sc[8], s_a2;
+    __shared__ double s_col[32];
+    __shared__ float vf[1024];
+
+    // 1. g for the CTA's columns (warp per column, lanes over the pass blocks)
+    for (int j = j0 + warp; j < j1; j += nwarp) {
+        float hi = 0.f, lo = 0.f;
+        for (int b0 = lane; b0 < q.nblk; b0 += 32 * 8) {   // blocks b0, b0 + 32, ... (loads ahead of the adds)
+            float2 x[8];
 #pragma unroll
-                for (int u = 0; u < U; ++u)
-                    nxt[u] = t0 + U + u < nb ? a.gpart[(size_t)(g + gp * (t0 + U + u)) * d + j] : make_float2(0.f, 0.f);
+            for (int u = 0; u < 8; ++u)
+                x[u] = b0 + 32 * u < q.nblk ? __ldg(q.gpart + (size_t)(b0 + 32 * u) * d + j) : make_float2(0.f, 0.f);
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (t0 + u < nb) {
-                        const float t = hi + cur[u].x;
-                        const float bp = t - hi;
-                        lo += (hi - (t - bp)) + (cur[u].x - bp) + cur[u].y;
-                        hi = t;
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) cur[u] = nxt[u];
-            }
-            gstripe[g * d + j] = make_float2(hi, lo);
+            for (int u = 0; u < 8; ++u)
+                if (b0 + 32 * u < q.nblk) two_add(hi, lo, x[u].x, x[u].y);
         }
-        __syncthreads();
-        for (int j = threadIdx.x; j < d; j += blockDim.x) {
-            float hi = 0.f, lo = 0.f;
-            for (int g = 0; g < gp; ++g) {
-                const float2 x = gstripe[g * d + j];
-                const float t = hi + x.x;
-                const float bp = t - hi;
-                lo += (hi - (t - bp)) + (x.x - bp) + x.y;
-                hi = t;
-            }
-            ghi[j] = hi;
-            glo[j] = lo;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+            const float ol = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+            two_add(hi, lo, oh, ol);
         }
-        if (SMEM_M) cp_async_wait_all();
-        __syncthreads();
+        if (lane == 0) a.gsum[j] = make_float2(hi, lo);
     }
-    double zz = 0.0, bb = 0.0;
-    for (int b = threadIdx.x; b < a.nblk; b += blockDim.x) {
-        zz += a.zpart[b];
-        if (a.first) bb += a.bpart[b];
+    // ||z||^2 (and ||b||^2 on the first step): every CTA the same sums
+    if (warp == 0) {
+        const double zz = warp_sum_fixed(q.zpart, q.nblk, lane);
+        const double bb = q.first ? warp_sum_fixed(q.bpart, q.nblk, lane) : 0.0;
+        if (lane == 0) {
+            s_sc[6] = zz;
+            s_sc[7] = bb;
+        }
     }
-    zz = block_sum(zz, red);
-    if (a.first) bb = block_sum(bb, red);
+    if (!grid_barrier(a.bar, (unsigned)P, a.tflag)) return;
+    const double beta = sqrt(s_sc[6]);
+    const double s_new = beta > 0.0 ? (q.first ? -1.0 / beta : 1.0 / beta) : 0.0;
+
+    // 2. t = M^T g for the CTA's columns (warp per column, lanes over rows i <= j)
+    for (int j = j0 + warp; j < j1; j += nwarp) {
+        const float* mcol = q.M32T + (size_t)j * d;
+        float sh = 0.f, sl = 0.f;
+        for (int i0 = lane; i0 <= j; i0 += 32 * 4) {   // rows i0, i0 + 32, ... (loads ahead of the adds)
+            float m[4];
+            float2 g[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = i0 + 32 * u <= j;
+                m[u] = ok ? __ldg(mcol + i0 + 32 * u) : 0.f;
+                g[u] = ok ? __ldcg(a.gsum + i0 + 32 * u) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (i0 + 32 * u > j) break;
+                const float p = __fmul_rn(m[u], g[u].x);
+                float e = fmaf(m[u], g[u].x, -p);
+                e = fmaf(m[u], g[u].y, e);
+                two_add(sh, sl, p, e);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xFFFFFFFFu, sh, o);
+            const float ol = __shfl_xor_sync(0xFFFFFFFFu, sl, o);
+            two_add(sh, sl, oh, ol);
+        }
+        if (lane == 0) {
+            double gv = s_new * ((double)sh + (double)sl);
+            if (!q.first) gv -= beta * q.v[j];
+            a.tv[j] = gv;
+            s_col[j - j0] = gv * gv;
+        }
+    }
     __syncthreads();
-    const double beta = sqrt(zz);
-    // scale of u = z * s_new: z = A x0 - b = -r0 on the first step
-    const double s_new = beta > 0.0 ? (a.first ? -1.0 / beta : 1.0 / beta) : 0.0;
-    // t = M^T (A^T z): exact float32 products (fma two-product) and two-word
-    // sums; one warp per column (columns w, w + 32, ...), lane l taking rows
-    // l, l + 32, ... in order, then a fixed shuffle tree of two-word sums
-    {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-        for (int j = warp; j < d; j += nwarp) {
-            const float* mcol = SMEM_M ? Ms + j * (j + 1) / 2 : a.M32T + (size_t)j * d;
-            float sh = 0.f, sl2 = 0.f;
-            for (int i = lane; i <= j; i += 32) {
-                const float m = mcol[i];
-                const float p = m * ghi[i];
-                float e = fmaf(m, ghi[i], -p);
-                e = fmaf(m, glo[i], e);
-                const float t = sh + p;
-                const float bp = t - sh;
-                sl2 += (sh - (t - bp)) + (p - bp) + e;
-                sh = t;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float oh = __shfl_xor_sync(0xFFFFFFFFu, sh, o);
-                const float ol = __shfl_xor_sync(0xFFFFFFFFu, sl2, o);
-                const float t = sh + oh;
-                const float bp = t - sh;
-                sl2 += (sh - (t - bp)) + (oh - bp) + ol;
-                sh = t;
-            }
-            if (lane == 0) sv[j] = (double)sh + (double)sl2;
-        }
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        double loc = 0.0;
+        for (int j = j0; j < j1; ++j) loc += s_col[j - j0];
+        a.share[cta] = loc;
     }
-    double loc = 0.0;
-    for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        double gv = s_new * sv[j];
-        if (!a.first) gv -= beta * a.v[j];
-        sv[j] = gv;
-        loc += gv * gv;
+    if (!grid_barrier(a.bar, (unsigned)P, a.tflag)) return;
+
+    // 3. alpha, the rotation, the vector updates for the CTA's columns
+    if (warp == 0) {
+        const double t = warp_sum_fixed(a.share, P, lane);
+        if (lane == 0) s_a2 = t;
     }
-    const double alpha = sqrt(block_sum(loc, red));
     __syncthreads();
-    if (a.first) {
-        for (int j = threadIdx.x; j < d; j += blockDim.x) {
-            const double vj = alpha > 0.0 ? sv[j] / alpha : 0.0;
-            a.v[j] = vj;
-            a.w[j] = vj;
-            a.dy[j] = 0.0;
-            sv[j] = vj;
-        }
-        if (threadIdx.x == 0) {
-            st->bnorm = sqrt(bb);
-            st->beta = beta;
-            st->alpha = alpha;
-            st->phibar = beta;
-            st->rhobar = alpha;
-            st->anorm2 = 0.0;
-            st->iters = 0;
-            st->rnorm = beta;
-            st->s = s_new;
-            st->coef = alpha * s_new;
-            st->test2 = 1.0;
-            if (alpha * beta == 0.0) {
-                st->done = 1;
-                st->converged = 1;
-                st->test2 = 0.0;
-            } else if (a.max_iter <= 0) {
-                st->done = 1;
-            }
+    const double alpha = sqrt(s_a2);
+    if (q.first) {
+        for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+            const double vj = alpha > 0.0 ? a.tv[j] / alpha : 0.0;
+            q.v[j] = vj;
+            q.w[j] = vj;
+            q.dy[j] = 0.0;
         }
     } else {
-        // the plane rotation and its scalars once (thread 0), then the vector updates
-        __shared__ double sc[8];
         if (threadIdx.x == 0) {
             const double alpha_old = st->alpha;
             const double anorm2 = st->anorm2 + alpha_old * alpha_old + beta * beta;
             const double rho = hypot(st->rhobar, beta);
             const double c = st->rhobar / rho, sn = beta / rho;
             const double rinv = 1.0 / rho;
-            sc[0] = c * st->phibar * rinv;     // phi / rho
-            sc[1] = sn * alpha * rinv;         // theta / rho
-            sc[2] = alpha > 0.0 ? 1.0 / alpha : 0.0;
-            sc[3] = anorm2;
-            sc[4] = c;
-            sc[5] = sn * st->phibar;           // phibar
+            s_sc[0] = c * st->phibar * rinv;   // phi / rho
+            s_sc[1] = sn * alpha * rinv;       // theta / rho
+            s_sc[2] = alpha > 0.0 ? 1.0 / alpha : 0.0;
+            s_sc[3] = anorm2;
+            s_sc[4] = c;
+            s_sc[5] = sn * st->phibar;         // phibar
         }
         __syncthreads();
-        const double k_dy = sc[0], k_w = sc[1], ainv = sc[2];
-        double yl = 0.0;
-        for (int j = threadIdx.x; j < d; j += blockDim.x) {
-            const double vj = sv[j] * ainv;
-            const double wj = a.w[j];
-            const double dyj = fma(k_dy, wj, a.dy[j]);
-            a.dy[j] = dyj;
-            a.w[j] = fma(-k_w, wj, vj);
-            a.v[j] = vj;
-            sv[j] = vj;
-            const double yj = a.y0[j] + dyj;
-            yl = fma(yj, yj, yl);
+        const double k_dy = s_sc[0], k_w = s_sc[1], ainv = s_sc[2];
+        for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+            const double vj = a.tv[j] * ainv;
+            const double wj = q.w[j];
+            const double dyj = fma(k_dy, wj, q.dy[j]);
+            q.dy[j] = dyj;
+            q.w[j] = fma(-k_w, wj, vj);
+            q.v[j] = vj;
+            const double yj = q.y0[j] + dyj;
+            s_col[j - j0] = yj * yj;
         }
-        const double ynorm = sqrt(block_sum(yl, red));
+        __syncthreads();
         if (threadIdx.x == 0) {
-            const double anorm2 = sc[3], c = sc[4], phibar = sc[5];
-            const double anorm = sqrt(anorm2);
-            const double rnorm = phibar;
-            const double arnorm = phibar * alpha * fabs(c);
-            const double test2 = rnorm > 0.0 ? arnorm / (anorm * rnorm) : 0.0;
-            st->anorm2 = anorm2;
-            st->rhobar = -c * alpha;
-            st->phibar = phibar;
-            st->alpha = alpha;
-            st->beta = beta;
-            st->s = s_new;
-            st->coef = alpha * s_new;
-            st->rnorm = rnorm;
-            st->test2 = test2;
-            st->iters += 1;
-            const bool conv = test2 <= a.rtol || rnorm <= a.rtol * (st->bnorm + anorm * ynorm) || beta == 0.0 ||
-                              alpha == 0.0;
-            if (conv) {
-                st->converged = 1;
-                st->done = 1;
-            } else if (st->iters >= a.max_iter) {
-                st->done = 1;
+            double yl = 0.0;
+            for (int j = j0; j < j1; ++j) yl += s_col[j - j0];
+            a.share[P + cta] = yl;
+        }
+    }
+    if (!grid_barrier(a.bar, (unsigned)P, a.tflag)) return;
+
+    // 4. the state (CTA 0) and vhat = M v for the CTA's rows
+    if (cta == 0 && warp == 0) {
+        const double ynorm = q.first ? 0.0 : sqrt(warp_sum_fixed(a.share + P, P, lane));
+        if (lane == 0) {
+            if (q.first) {
+                st->bnorm = sqrt(s_sc[7]);
+                st->beta = beta;
+                st->alpha = alpha;
+                st->phibar = beta;
+                st->rhobar = alpha;
+                st->anorm2 = 0.0;
+                st->iters = 0;
+                st->rnorm = beta;
+                st->s = s_new;
+                st->coef = alpha * s_new;
+                st->test2 = 1.0;
+                if (alpha * beta == 0.0) {
+                    st->done = 1;
+                    st->converged = 1;
+                    st->test2 = 0.0;
+                } else if (q.max_iter <= 0) {
+                    st->done = 1;
+                }
+            } else {
+                const double anorm2 = s_sc[3], c = s_sc[4], phibar = s_sc[5];
+                const double anorm = sqrt(anorm2);
+                const double rnorm = phibar;
+                const double arnorm = phibar * alpha * fabs(c);
+                const double test2 = rnorm > 0.0 ? arnorm / (anorm * rnorm) : 0.0;
+                st->anorm2 = anorm2;
+                st->rhobar = -c * alpha;
+                st->phibar = phibar;
+                st->alpha = alpha;
+                st->beta = beta;
+                st->s = s_new;
+                st->coef = alpha * s_new;
+                st->rnorm = rnorm;
+                st->test2 = test2;
+                st->iters += 1;
+                const bool conv = test2 <= q.rtol || rnorm <= q.rtol * (st->bnorm + anorm * ynorm) || beta == 0.0 ||
+                                  alpha == 0.0;
+                if (conv) {
+                    st->converged = 1;
+                    st->done = 1;
+                } else if (st->iters >= q.max_iter) {
+                    st->done = 1;
+                }
             }
         }
     }
+    if (j0 >= j1) return;
+    for (int j = j0 + threadIdx.x; j < d; j += blockDim.x) vf[j] = (float)__ldcg(q.v + j);
     __syncthreads();
-    // next vhat = M v (float32; it feeds the float32 pass)
-    {
-        // vhat = M v in float32, `gper` threads per row (fixed slices, fixed combine order)
-        __shared__ float vf[1024];
-        for (int j = threadIdx.x; j < d; j += blockDim.x) vf[j] = (float)sv[j];
-        __syncthreads();
-        const int gper = blockDim.x / d >= 4 ? 4 : (blockDim.x / d >= 2 ? 2 : 1);
-        float* vpart = reinterpret_cast<float*>(sg);  // sg no longer needed
-        for (int tq = threadIdx.x; tq < d * gper; tq += blockDim.x) {
-            const int i = tq % d, g = tq / d;
-            const int len = d - i, lo = i + (int)((int64_t)len * g / gper), hi = i + (int)((int64_t)len * (g + 1) / gper);
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-            int j = lo;
-            if (SMEM_M) {
-                for (; j + 3 < hi; j += 4) {
-                    s0 = fmaf(Ms[j * (j + 1) / 2 + i], vf[j], s0);
-                    s1 = fmaf(Ms[(j + 1) * (j + 2) / 2 + i], vf[j + 1], s1);
-                    s2 = fmaf(Ms[(j + 2) * (j + 3) / 2 + i], vf[j + 2], s2);
-                    s3 = fmaf(Ms[(j + 3) * (j + 4) / 2 + i], vf[j + 3], s3);
-                }
-                for (; j < hi; ++j) s0 = fmaf(Ms[j * (j + 1) / 2 + i], vf[j], s0);
-            } else {
-                for (; j + 3 < hi; j += 4) {
-                    s0 = fmaf(a.M32T[(size_t)j * d + i], vf[j], s0);
-                    s1 = fmaf(a.M32T[(size_t)(j + 1) * d + i], vf[j + 1], s1);
-                    s2 = fmaf(a.M32T[(size_t)(j + 2) * d + i], vf[j + 2], s2);
-                    s3 = fmaf(a.M32T[(size_t)(j + 3) * d + i], vf[j + 3], s3);
-                }
-                for (; j < hi; ++j) s0 = fmaf(a.M32T[(size_t)j * d + i], vf[j], s0);
-            }
-            vpart[g * d + i] = (s0 + s1) + (s2 + s3);
+    // row i: lanes over j >= i (M row-major float64 holds the float32 values), fixed tree
+    for (int i = j0 + warp; i < j1; i += nwarp) {
+        const double* mrow = q.M + (size_t)i * d;
+        float s0 = 0.f;
+        for (int jb = i + lane; jb < d; jb += 32 * 4) {   // columns jb, jb + 32, ... (loads ahead of the FMAs)
+            double mv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) mv[u] = jb + 32 * u < d ? __ldg(mrow + jb + 32 * u) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (jb + 32 * u < d) s0 = fmaf((float)mv[u], vf[jb + 32 * u], s0);
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < d; i += blockDim.x) {
-            float t = 0.f;
-            for (int g = 0; g < gper; ++g) t += vpart[g * d + i];
-            a.vhat[i] = t;
-        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xFFFFFFFFu, s0, o);
+        if (lane == 0) q.vhat[i] = s0;
     }
 }
 
@@ -589,13 +566,6 @@ __global__ void k_to_f32_transposed(double* __restrict__ M, int d, float* __rest
     }
 }
 
-// M32P = the upper triangle of M (float32, column-major M32T) packed by columns.
-__global__ void k_pack_upper_f32(const float* __restrict__ M32T, int d, float* __restrict__ M32P) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (int64_t)d * d) return;
-    const int j = (int)(q / d), i = (int)(q % d);
-    if (i <= j) M32P[(int64_t)j * (j + 1) / 2 + i] = M32T[q];
-}
 
 // y = float32 copy of x (n entries).
 __global__ void k_copy_f32(const double* __restrict__ x, int n, float* __restrict__ y) {
@@ -658,21 +628,23 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     const size_t oR = ws.reserve(sizeof(double) * (size_t)d * d);
     const size_t oM = ws.reserve(sizeof(double) * (size_t)d * d);
     const size_t oM32 = ws.reserve(sizeof(float) * (size_t)d * d);
-    const size_t packed_floats = ((size_t)d * (d + 1) / 2 + 3) & ~size_t(3);
-    const size_t oM32P = ws.reserve(sizeof(float) * packed_floats);
     const size_t oc = ws.reserve(sizeof(double) * (size_t)d);
     const size_t ox0 = ws.reserve(sizeof(double) * (size_t)d);
     const size_t oy0 = ws.reserve(sizeof(double) * (size_t)d);
     const size_t ov = ws.reserve(sizeof(double) * (size_t)d);
     const size_t ow = ws.reserve(sizeof(double) * (size_t)d);
     const size_t ody = ws.reserve(sizeof(double) * (size_t)d);
-    const size_t og = ws.reserve(sizeof(double) * (size_t)d);
     const size_t ovh = ws.reserve(sizeof(float) * (size_t)d);
     const size_t oz = ws.reserve(sizeof(float) * (size_t)(n > 0 ? n : 1));
     const size_t ogp = ws.reserve(sizeof(float2) * (size_t)grid * d);
     const size_t ozp = ws.reserve(sizeof(double) * (size_t)grid);
     const size_t obp = ws.reserve(sizeof(double) * (size_t)grid);
     const size_t ost = ws.reserve(sizeof(LsqrState));
+    const size_t ogf = ws.reserve(16);   // the Cholesky route's flags
+    const size_t opb = ws.reserve(16);   // the LSQR step's grid barrier and its timeout flag
+    const size_t ogs = ws.reserve(sizeof(float2) * (size_t)d);
+    const size_t otv = ws.reserve(sizeof(double) * (size_t)d);
+    const size_t osh = ws.reserve(sizeof(double) * 2 * (size_t)(nsm > 0 ? nsm : 1));
     CW_CUDA_TRY(ws.alloc());
     float* SA = ws.at<float>(oSA);
     float* Sb = ws.at<float>(oSb);
@@ -685,7 +657,6 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     float* vhat = ws.at<float>(ovh);
     float* z = ws.at<float>(oz);
     LsqrState* state = ws.at<LsqrState>(ost);
-    CW_CUDA_TRY(cudaMemsetAsync(state, 0, sizeof(LsqrState), stream));
 
     st = sketch_impl(kSketchCSR, n, d, 0, 0, A->row_ptr, A->col, A->val, nullptr, b, m, seed, SA, Sb, nullptr,
                      stream);
@@ -693,95 +664,135 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     // preconditioner M = R^-1: R from the Cholesky factor of the Gram matrix of
     // SA (one shared-memory kernel), or from the float64 Householder QR of SA
     // when the Cholesky route is not safe (large diagonal ratio, a failed
-    // pivot, or d too large for the shared-memory kernel).  c = Q^T Sb.
+    // pivot, or d too large for the shared-memory kernel).  c = Q^T Sb.  The
+    // Cholesky route's flags are read back with the first LSQR state, after
+    // the first batch of iterations has been queued; if they reject it, the
+    // iterations are redone from the QR preconditioner.
+    unsigned* gflags = ws.at<unsigned>(ogf);
+    CW_CUDA_TRY(cudaMemsetAsync(gflags, 0, 16, stream));
     float klb = 0.f;
-    st = gram_chol_inverse(SA, m, d, Sb, M, M32T, c, &klb, stream);
-    const bool fast_ok = (st == CW_OK) && klb <= 300.f;
-    if (st != CW_OK && st != CW_ERR_RANK && st != CW_ERR_SHAPE) return st;
-    if (!fast_ok) {
-        st = qr64(SA, m, d, Sb, R, c, stream);
-        if (st != CW_OK) return st;
-        st = tri_inverse(R, d, M, stream);
-        if (st != CW_OK) return st;
+    st = gram_chol_inverse(SA, m, d, Sb, M, M32T, c, &klb, stream, gflags);
+    if (st != CW_OK && st != CW_ERR_SHAPE) return st;
+    bool precond_checked = st != CW_OK;   // CW_ERR_SHAPE: straight to the QR route
+    auto qr_precond = [&]() -> int {
+        int r = qr64(SA, m, d, Sb, R, c, stream);
+        if (r != CW_OK) return r;
+        r = tri_inverse(R, d, M, stream);
+        if (r != CW_OK) return r;
         const int64_t dd0 = (int64_t)d * d;
         {
             CW_PROF("k_to_f32_transposed", stream);
             k_to_f32_transposed<<<(unsigned)((dd0 + 255) / 256), 256, 0, stream>>>(M, d, M32T);
         }
         CW_LAUNCH_CHECK();
+        return CW_OK;
+    };
+    if (precond_checked) {
+        st = qr_precond();
+        if (st != CW_OK) return st;
     }
-    float* M32P = ws.at<float>(oM32P);
-    {
-        const int64_t dd1 = (int64_t)d * d;
-        CW_PROF("k_pack_upper_f32", stream);
-        k_pack_upper_f32<<<(unsigned)((dd1 + 255) / 256), 256, 0, stream>>>(M32T, d, M32P);
-    }
-    {
-        CW_PROF("k_upper_matvec", stream);  // x0 = M c: the sketch-and-solve start
-        k_upper_matvec<<<(d + 7) / 8, 256, 0, stream>>>(M, d, c, x0, nullptr);
-    }
-    CW_LAUNCH_CHECK();
-    // first pass input: vhat = x0 (float32); y0 = R x0 = c
-    {
-        CW_PROF("k_copy_f32", stream);
-        k_copy_f32<<<(d + 255) / 256, 256, 0, stream>>>(x0, d, vhat);
-    }
-    CW_CUDA_TRY(cudaMemcpyAsync(y0, c, sizeof(double) * d, cudaMemcpyDeviceToDevice, stream));
-    CW_LAUNCH_CHECK();
-
     auto pk = pass_warps == 24   ? k_lsqr_pass<24>
               : pass_warps == 16 ? k_lsqr_pass<16>
               : pass_warps == 12 ? k_lsqr_pass<12>
               : pass_warps == 8  ? k_lsqr_pass<8>
                                  : k_lsqr_pass<4>;
     CW_CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem));
-    PassArgs pa{A->row_ptr, A->col, A->val, vhat, b, z, ws.at<float2>(ogp), ws.at<double>(ozp), ws.at<double>(obp),
-                nullptr, status, n, d, dpad, 1.0f};
-    {
-        CW_PROF("k_lsqr_pass", stream);
-        pk<<<grid, threads, pass_smem, stream>>>(pa);  // z = A x0 - b
-    }
-    CW_LAUNCH_CHECK();
-    // the post kernel keeps the packed triangle of M in shared memory when it fits
-    const size_t post_smem = sizeof(float) * packed_floats;
-    const bool post_sm = post_smem <= 160 * 1024;
-    auto postk = post_sm ? k_lsqr_post<true> : k_lsqr_post<false>;
-    if (post_sm)
-        CW_CUDA_TRY(cudaFuncSetAttribute(postk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)post_smem));
-    const size_t post_dyn = post_sm ? post_smem : 0;
-    PostArgs qa{ws.at<float2>(ogp), ws.at<double>(ozp), ws.at<double>(obp), grid, d, M32T, M32P, y0,
-                ws.at<double>(ov), ws.at<double>(ow), ws.at<double>(ody), ws.at<double>(og), vhat, state, rtol,
-                max_iter, 1};
-    {
-        CW_PROF("k_lsqr_post", stream);
-        postk<<<1, 1024, post_dyn, stream>>>(qa);
-    }
-    CW_LAUNCH_CHECK();
-    pa.zin = z;
-    pa.st = state;
-    pa.bpart = nullptr;
-    qa.first = 0;
-    qa.bpart = nullptr;
+    PassArgs pa{};
+    PostArgs qa{};
+    // the LSQR step on P CTAs (cooperative), each owning at most 32 columns
+    const int post_P = std::min(nsm, (d + 7) / 8);
+    if ((d + post_P - 1) / post_P > 32) return CW_ERR_SHAPE;
+    unsigned* pbar = ws.at<unsigned>(opb);   // [0, 1] barrier, [2] barrier wait gave up
+    auto post = [&]() -> int {
+        PostMcArgs qm{qa, ws.at<float2>(ogs), ws.at<double>(otv), ws.at<double>(osh), pbar, pbar + 2};
+        void* args[] = {&qm};
+        CW_PROF("k_lsqr_post_mc", stream);
+        CW_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_lsqr_post_mc, dim3((unsigned)post_P), dim3(256), args, 0,
+                                                stream));
+        CW_LAUNCH_CHECK();
+        return CW_OK;
+    };
+    // from M and c: the start x0 = M c, the first pass (z = A x0 - b) and the
+    // first post step (LSQR's initial bidiagonalisation)
+    auto start = [&]() -> int {
+        CW_CUDA_TRY(cudaMemsetAsync(state, 0, sizeof(LsqrState), stream));
+        {
+            CW_PROF("k_upper_matvec", stream);  // x0 = M c: the sketch-and-solve start
+            k_upper_matvec<<<(d + 7) / 8, 256, 0, stream>>>(M, d, c, x0, nullptr);
+        }
+        CW_LAUNCH_CHECK();
+        // first pass input: vhat = x0 (float32); y0 = R x0 = c
+        {
+            CW_PROF("k_copy_f32", stream);
+            k_copy_f32<<<(d + 255) / 256, 256, 0, stream>>>(x0, d, vhat);
+        }
+        CW_CUDA_TRY(cudaMemcpyAsync(y0, c, sizeof(double) * d, cudaMemcpyDeviceToDevice, stream));
+        CW_LAUNCH_CHECK();
+        pa = PassArgs{A->row_ptr, A->col, A->val, vhat, b, z, ws.at<float2>(ogp), ws.at<double>(ozp),
+                      ws.at<double>(obp), nullptr, status, n, d, dpad, 1.0f};
+        {
+            CW_PROF("k_lsqr_pass", stream);
+            pk<<<grid, threads, pass_smem, stream>>>(pa);  // z = A x0 - b
+        }
+        CW_LAUNCH_CHECK();
+        qa = PostArgs{ws.at<float2>(ogp), ws.at<double>(ozp), ws.at<double>(obp), grid, d, M32T, M, y0,
+                      ws.at<double>(ov), ws.at<double>(ow), ws.at<double>(ody), vhat, state, rtol,
+                      max_iter, 1};
+        CW_CUDA_TRY(cudaMemsetAsync(pbar, 0, 16, stream));
+        int r = post();
+        if (r != CW_OK) return r;
+        pa.zin = z;
+        pa.st = state;
+        pa.bpart = nullptr;
+        qa.first = 0;
+        qa.bpart = nullptr;
+        return CW_OK;
+    };
+    st = start();
+    if (st != CW_OK) return st;
+    // iterations in batches of four: each pass and post step returns at once
+    // when the state says done, so a batch may run past convergence at the
+    // cost of a few empty launches; the host reads the state between batches
+    struct Flags {
+        unsigned rank, timeout;
+        float klb, pad;
+    };
     LsqrState hs{};
+    Flags hf{};
     int launched = 0;
     const int batch = 4;
     for (;;) {
-        CW_CUDA_TRY(cudaMemcpyAsync(&hs, state, sizeof(LsqrState), cudaMemcpyDeviceToHost, stream));
-        CW_CUDA_TRY(cudaStreamSynchronize(stream));
-        if (hs.done || launched >= max_iter) break;
         const int nb = (max_iter - launched) < batch ? (max_iter - launched) : batch;
         for (int q = 0; q < nb; ++q) {
             {
                 CW_PROF("k_lsqr_pass", stream);
                 pk<<<grid, threads, pass_smem, stream>>>(pa);
             }
-            {
-                CW_PROF("k_lsqr_post", stream);
-                postk<<<1, 1024, post_dyn, stream>>>(qa);
-            }
+            st = post();
+            if (st != CW_OK) return st;
         }
         CW_LAUNCH_CHECK();
         launched += nb;
+        unsigned ptimeout = 0;
+        CW_CUDA_TRY(cudaMemcpyAsync(&hs, state, sizeof(LsqrState), cudaMemcpyDeviceToHost, stream));
+        CW_CUDA_TRY(cudaMemcpyAsync(&ptimeout, pbar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
+        if (!precond_checked)
+            CW_CUDA_TRY(cudaMemcpyAsync(&hf, gflags, sizeof(Flags), cudaMemcpyDeviceToHost, stream));
+        CW_CUDA_TRY(cudaStreamSynchronize(stream));
+        if (ptimeout) return CW_ERR_TIMEOUT;
+        if (!precond_checked) {
+            precond_checked = true;
+            if (hf.timeout) return CW_ERR_TIMEOUT;
+            if (hf.rank || !(hf.klb <= 300.f)) {   // redo from the QR preconditioner
+                st = qr_precond();
+                if (st != CW_OK) return st;
+                st = start();
+                if (st != CW_OK) return st;
+                launched = 0;
+                continue;
+            }
+        }
+        if (hs.done || launched >= max_iter) break;
     }
     // x = x0 + M dy
     {

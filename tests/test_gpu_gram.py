@@ -5,7 +5,8 @@ Error model.  For d <= 256 the kernel splits each float32 value x into
 hi = x truncated to TF32 and lo = x - hi, and forms hi*hi + hi*lo + lo*hi on
 the tensor cores (lo itself truncated to TF32 there): each product is off by
 at most 3 * 2^-20 |x y|.  The products are summed in float32 over one CTA's
-rows (at most `rows_per` of them), then in float64 across CTAs; the Sb
+rows (at most `rows_per` of them), then across CTAs as float32 two-word
+sums (~44 bits, error negligible here); the Sb
 column is float32 FMAs over the same rows.  With Cauchy-Schwarz,
     |G - G_o|_ij <= (3 * 2^-20 + rows_per * 2^-23) sqrt(G_ii G_jj).
 The test allows 4 * 2^-20 + rows_per * 2^-22.  A kernel that dropped the

@@ -146,6 +146,42 @@ def test_lsqr_shapes(cw, n, d, k, m, seed):
     assert abs(_rho(A, b, x, rn) - _rho(A, b, x_o, rn)) <= RHO_TOL
 
 
+def test_lsqr_badly_scaled_columns_take_the_qr_preconditioner(cw):
+    """Columns scaled over four decades: R's diagonal ratio is far above the
+    Cholesky route's limit of 300, so the library redoes the iterations from
+    the float64 QR preconditioner; the result still matches the oracle."""
+    A0 = W.csr_uniform(60000, 48, 6, seed=71)
+    scale = torch.pow(10.0, torch.linspace(0, 4, 48, dtype=torch.float64)).to(torch.float32)
+    A = W.CSR(A0.n, A0.d, A0.row_ptr, A0.col, A0.val * scale[A0.col.long()])
+    b, _ = W.rhs(A, 0.1, seed=72)
+    x, it, test, x_o, it_o, test_o, conv_o = _lsqr_case(cw, A, b, 2048, 13)
+    assert conv_o and test <= 1e-6
+    assert abs(it - it_o) <= 1, (it, it_o)
+    _, rn = oracle.lstsq_exact_csr(A.row_ptr, A.col, A.val, A.d, b)
+    assert abs(_rho(A, b, x, rn) - _rho(A, b, x_o, rn)) <= RHO_TOL
+
+
+def test_lsqr_is_deterministic(cw):
+    """Every sum in the sketch, the preconditioner and the LSQR steps has a
+    fixed order: two runs give the same bits."""
+    A = W.csr_zipf(1 << 18, 200, 12, 1.1, seed=81, device="cuda")
+    b, _ = W.rhs(A, 0.05, seed=82)
+    x1, it1, t1 = cw.cw_lsqr_precond(A, b, 8192, 5)
+    x2, it2, t2 = cw.cw_lsqr_precond(A, b, 8192, 5)
+    assert it1 == it2 and t1 == t2
+    assert torch.equal(x1, x2)
+
+
+def test_lsqr_zero_iterations(cw):
+    A = W.csr_uniform(20000, 16, 4, seed=2)
+    b, _ = W.rhs(A, 0.5, seed=3)
+    x, it, test = cw.cw_lsqr_precond(A.to("cuda"), b.cuda(), 64, 1, rtol=1e-6, max_iter=0, allow_noconv=True)
+    assert it == 0
+    x_s = cw.cw_solve_sketch(A.to("cuda"), b.cuda(), 64, 1)
+    # no iteration: x is the sketch-and-solve start (Cholesky or QR route, float32 R^-1)
+    np.testing.assert_allclose(x.cpu().numpy(), x_s.cpu().numpy(), rtol=1e-4, atol=1e-5)
+
+
 def test_lsqr_max_iter_reports_noconv(cw):
     A = W.csr_uniform(20000, 16, 4, seed=2)
     b, _ = W.rhs(A, 0.5, seed=3)
