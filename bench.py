@@ -229,7 +229,7 @@ def measured_peak_hbm():
 
 
 # the sources each profiled kernel is built from: a capture stays valid until they change
-KERNEL_SOURCES = {"k_lsqr_pass": ("lsqr.cu", "cw_common.cuh"),
+KERNEL_SOURCES = {"k_lsqr_pass": ("lsqr_pass.cuh", "cw_common.cuh"),
                   "k_apply_csr": ("sketch.cu", "sketch_body.cuh", "cw_common.cuh")}
 
 

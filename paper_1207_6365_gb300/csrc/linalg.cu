@@ -689,6 +689,51 @@ __device__ __forceinline__ bool chol_block32(float (&col)[kCholB], int pb, float
     return ok;
 }
 
+// Rows of the shared-memory copy of a diagonal block: 16-byte aligned, so that
+// a row can be read back as 16-byte broadcasts.
+constexpr int kDgStride = kCholB + 4;
+
+// chol_block32 with the scaled row j published to Dg[j][.] in shared memory at
+// each pivot and read back by every lane as 16-byte broadcasts for the update
+// (one store and at most eight loads per pivot instead of 31 shuffles); the
+// arithmetic and its order are those of chol_block32.  Dg ends up holding R.
+__device__ __forceinline__ bool chol_block32_rows(float (&col)[kCholB], int pb, float& rinv_out,
+                                                  float (*Dg)[kDgStride]) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    rinv_out = 1.f;
+#pragma unroll
+    for (int j = 0; j < kCholB; ++j) {
+        const float piv = __shfl_sync(0xFFFFFFFFu, col[j], j);
+        if (j < pb) {
+            if (!(piv > 0.f)) ok = false;
+            const float rinv = rsqrtf(piv);
+            if (lane == j) {
+                col[j] = piv * rinv;
+                rinv_out = rinv;
+            } else if (lane > j) {
+                col[j] *= rinv;
+            }
+        }
+        Dg[j][lane] = col[j];
+        __syncwarp();
+        if (j < pb) {
+            const float rjk = col[j];
+#pragma unroll
+            for (int i4 = (j + 1) & ~3; i4 < kCholB; i4 += 4) {
+                const float4 r = *reinterpret_cast<const float4*>(&Dg[j][i4]);
+                const float rv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i4 + u;
+                    if (i > j && lane >= i) col[i] = fmaf(-rv[u], rjk, col[i]);
+                }
+            }
+        }
+    }
+    return ok;
+}
+
 __global__ void __launch_bounds__(512) k_chol_panel(float* __restrict__ W, int d, int nc, int p0,
                                                    unsigned* bad) {
     __shared__ float D[kCholB][kCholB + 1];
@@ -787,22 +832,20 @@ __global__ void __launch_bounds__(256) k_chol_update(float* __restrict__ W, int 
 __device__ __forceinline__ int chol_off(int i, int nc) { return i * nc - (i * (i + 1)) / 2; }
 
 // Warp 0: the diagonal block of panel p0 (pb columns) from P into registers,
-// factored by chol_block32, written back to P and to Dg, with 1 / R_jj in
+// factored by chol_block32_rows (which leaves R in Dg), written back to P, with 1 / R_jj in
 // Dinv.  Not inlined, so its 32 registers of column do not add to the
 // kernel's peak.  Returns false (every lane) on a non-positive pivot.
-__device__ __noinline__ bool chol_small_diag(float* P, float (*Dg)[kCholB + 1], float* Dinv, int nc, int p0,
+__device__ __noinline__ bool chol_small_diag(float* P, float (*Dg)[kDgStride], float* Dinv, int nc, int p0,
                                              int pb) {
     const int lane = threadIdx.x & 31;
     float col[kCholB];
 #pragma unroll
     for (int q = 0; q < kCholB; ++q) col[q] = (q <= lane && lane < pb) ? P[chol_off(p0 + q, nc) + p0 + lane] : 0.f;
     float rinv;
-    const bool ok = chol_block32(col, pb, rinv);
+    const bool ok = chol_block32_rows(col, pb, rinv, Dg);
 #pragma unroll
-    for (int q = 0; q < kCholB; ++q) {
+    for (int q = 0; q < kCholB; ++q)
         if (q <= lane && lane < pb) P[chol_off(p0 + q, nc) + p0 + lane] = col[q];
-        Dg[q][lane] = col[q];
-    }
     Dinv[lane] = rinv;
     return ok;
 }
@@ -812,7 +855,7 @@ __device__ __noinline__ bool chol_small_diag(float* P, float (*Dg)[kCholB + 1], 
 // the result goes to P and densely to Pan (zero past the last column, nc <= k
 // < s0 + tp, and below row pb).  Not inlined: the caller's loop would
 // otherwise hoist the Dg loads and spill.
-__device__ __noinline__ void chol_small_panel(float* P, float* Pan, const float (*Dg)[kCholB + 1],
+__device__ __noinline__ void chol_small_panel(float* P, float* Pan, const float (*Dg)[kDgStride],
                                               const float* Dinv, int nc, int p0, int pb, int s0, int tp, int k) {
     // rows 0..15 of the panel, then rows 16..31 (fewer live registers)
     float x[16], y[16];
@@ -870,7 +913,7 @@ __device__ __noinline__ void chol_small_panel(float* P, float* Pan, const float 
 __global__ void __launch_bounds__(512) k_chol_small(float* __restrict__ W, int d, int nc, int tpmax,
                                                    unsigned* bad) {
     extern __shared__ __align__(16) float P[];
-    __shared__ float Dg[kCholB][kCholB + 1];   // R of the current diagonal block
+    __shared__ __align__(16) float Dg[kCholB][kDgStride];   // R of the current diagonal block
     __shared__ float Dinv[kCholB];             // 1 / its diagonal
     __shared__ int fail;
     const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
