@@ -24,6 +24,7 @@ import datetime
 import hashlib
 import json
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -309,10 +310,34 @@ def run_oracle_child(rows, steps):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def host_info():
+    """The host the oracle ran on: logical CPUs, CPUs this process may use, CPU model."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        info["affinity"] = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        pass
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key, _, val = line.partition(":")
+                key = key.strip().lower()
+                if key in ("model name", "cpu model"):
+                    model = val.strip()
+                    break
+                if key == "cpu part" and model is None:
+                    model = "Arm CPU part " + val.strip()
+    except OSError:
+        pass
+    info["cpu"] = model or platform.machine()
+    return info
+
+
 def cpu_baseline_block(res, sample_desc):
     tot = sum(res["times"])
     return {"value": res["nnz"] * len(res["times"]) / tot, "unit": "nnz/s", "cores": 1, "kind": "oracle",
-            "sample": sample_desc, "seconds": tot, "lsqr_iters": res["iters"][-1]}
+            "sample": sample_desc, "seconds": tot, "lsqr_iters": res["iters"][-1], "host": host_info()}
 
 
 # ---------------------------------------------------------------- main arms
