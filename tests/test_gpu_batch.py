@@ -2,8 +2,9 @@
 uneven n and d in one graph launch) against the float64 oracle.
 
 For every problem: each SA / Sb entry within 1e-5 of its bucket's absolute sum
-(the sketch tolerance), x' equal to the float64 least-squares solution of the
-batch's own float32 SA (the oracle's Householder QR of that SA) to 1e-9, and
+(the sketch tolerance), x' within four times the first-order perturbation
+bound of the oracle's solution (its own float64 sketch and Householder QR),
+the perturbation being the float32 summation error of each SA entry, and
 the residual ratio ||A x' - b|| / ||A x* - b|| equal to the oracle's (oracle
 SA, oracle QR) to 1e-6.  Edge cases: empty and rank-deficient problems,
 d = 1, m = d, n < m, an ill-conditioned problem that must go to the QR
@@ -30,6 +31,8 @@ def cw():
 
 
 def _check_sketch(A, b, m, seed, SA, Sb):
+    """The batch's SA, Sb against the oracle's; returns the oracle's sketch and
+    the float32 rounding bounds E, Eb of the batch's entries (see _x_bound)."""
     SA_o, Sb_o = oracle.sketch_csr(A.row_ptr, A.col, A.val, A.d, b, m, seed)
     h, _ = oracle.hash(seed, m, 0, A.n)
     rp, c, v = A.numpy()
@@ -42,7 +45,34 @@ def _check_sketch(A, b, m, seed, SA, Sb):
     assert (err <= TOL * absA + 1e-30).all(), "SA out of tolerance"
     errb = np.abs(Sb.cpu().double().numpy() - Sb_o)
     assert (errb <= TOL * absb + 1e-30).all(), "Sb out of tolerance"
-    return SA_o, Sb_o
+    # an entry of SA is a float32 sum over the rows of its bucket: in any order
+    # within (k - 1) u sum |terms| of the exact sum (k rows, u = 2^-24), plus
+    # the rounding of the inputs' products by the signs (exact)
+    k = np.bincount(h, minlength=m).astype(np.float64)
+    E = (k[:, None] * 2.0 ** -24) * absA
+    Eb = k * 2.0 ** -24 * absb
+    return SA_o, Sb_o, E, Eb
+
+
+def _x_bound(SA_o, Sb_o, x_o, E, Eb):
+    """First-order bound on |x - x_o| for x = argmin ||SA x - Sb|| when
+    |SA - SA_o| <= E and |Sb - Sb_o| <= Eb entrywise:
+        x - x_o ~ -P (dSA x_o - dSb) + (SA_o^T SA_o)^-1 dSA^T r_o,  P = SA_o^+,
+    with r_o = Sb_o - SA_o x_o; each term bounded with absolute values."""
+    P = np.linalg.pinv(SA_o)
+    Ginv = np.linalg.inv(SA_o.T @ SA_o)
+    r_o = Sb_o - SA_o @ x_o
+    return np.abs(P) @ (E @ np.abs(x_o) + Eb) + np.abs(Ginv) @ (E.T @ np.abs(r_o))
+
+
+def _check_x(x, SA_o, Sb_o, E, Eb, p):
+    """x against the oracle's solve of its own sketch: within four times the
+    first-order bound (second-order terms, the solver's own rounding)."""
+    x_o, _ = oracle.solve_sketch(SA_o, Sb_o)
+    bound = _x_bound(SA_o, Sb_o, x_o, E, Eb)
+    err = np.abs(x - x_o)
+    assert (err <= 4 * bound + 1e-8 * np.abs(x_o).max()).all(), (p, float((err / (bound + 1e-300)).max()))
+    return x_o
 
 
 def _make(shapes):
@@ -62,13 +92,10 @@ def test_batch_matches_oracle(cw):
     st = B.finish()
     assert st == [0] * len(probs), st
     for p, (A, b, m, seed) in enumerate(cpu):
-        SA_o, Sb_o = _check_sketch(A, b, m, seed, B.SA[p], B.Sb[p])
+        SA_o, Sb_o, E, Eb = _check_sketch(A, b, m, seed, B.SA[p], B.Sb[p])
         x = B.x[p].cpu().numpy()
-        # the float64 least-squares solution of the batch's own float32 SA
-        x_same, _ = oracle.solve_sketch(B.SA[p].cpu().double().numpy(), B.Sb[p].cpu().double().numpy())
-        assert np.abs(x - x_same).max() <= 1e-9 * np.abs(x_same).max(), p
+        x_o = _check_x(x, SA_o, Sb_o, E, Eb, p)
         # residual ratio against the oracle end to end
-        x_o, _ = oracle.solve_sketch(SA_o, Sb_o)
         _, rstar = oracle.lstsq_exact_csr(A.row_ptr, A.col, A.val, A.d, b)
         rho = oracle.residual_ratio_csr(A.row_ptr, A.col, A.val, b, x, rstar)
         rho_o = oracle.residual_ratio_csr(A.row_ptr, A.col, A.val, b, x_o, rstar)
@@ -92,10 +119,8 @@ def test_batch_edge_cases(cw):
     assert float(B.x[0].abs().max()) == 0.0
     for p in range(2, len(cpu)):
         A, b, m, seed = cpu[p]
-        _check_sketch(A, b, m, seed, B.SA[p], B.Sb[p])
-        x_same, _ = oracle.solve_sketch(B.SA[p].cpu().double().numpy(), B.Sb[p].cpu().double().numpy())
-        x = B.x[p].cpu().numpy()
-        assert np.abs(x - x_same).max() <= 1e-9 * np.abs(x_same).max(), p
+        SA_o, Sb_o, E, Eb = _check_sketch(A, b, m, seed, B.SA[p], B.Sb[p])
+        _check_x(B.x[p].cpu().numpy(), SA_o, Sb_o, E, Eb, p)
     B.close()
 
 
@@ -119,10 +144,9 @@ def test_batch_ill_conditioned_problem_goes_to_the_qr(cw):
     B.run()
     st = B.finish()
     assert st == [3, 0], st
-    for p in range(2):
-        x_same, _ = oracle.solve_sketch(B.SA[p].cpu().double().numpy(), B.Sb[p].cpu().double().numpy())
-        x = B.x[p].cpu().numpy()
-        assert np.abs(x - x_same).max() <= 1e-6 * np.abs(x_same).max(), p
+    for p, (A_, b_, m_, seed_) in enumerate(((A, b, 256, 11), (A2, b2, 256, 9))):
+        SA_o, Sb_o, E, Eb = _check_sketch(A_, b_, m_, seed_, B.SA[p], B.Sb[p])
+        _check_x(B.x[p].cpu().numpy(), SA_o, Sb_o, E, Eb, p)
     B.close()
 
 

