@@ -72,7 +72,7 @@ def _moved_bytes(kernel, n, d, nnz, m):
 
 TIMED_KERNELS = ("k_lsqr_pass", "k_apply_csr", "k_coarse_scatter", "k_fine_sort", "k_tile_hist",
                  "k_lsqr_post_mc", "k_chol_small", "k_chol_panel", "k_chol_update", "k_tri_inv_f32", "k_gram_to_f32", "k_chol_finish",
-                 "k_copy_f32", "k_gram_tile", "k_gram_tc", "k_gram_tc_reduce", "k_gram_gemv", "k_qr_householder", "k_qr_blocked", "k_scan_tiles", "k_scan_bins",
+                 "k_lsqr_start", "k_gram_tile", "k_gram_tc", "k_gram_tc_reduce", "k_gram_gemv", "k_qr_householder", "k_qr_blocked", "k_scan_tiles", "k_scan_bins",
                  "k_scan_chunk_sums", "k_trsm_upper", "k_trsv_upper", "k_gram_reduce", "k_tri_inverse",
                  "k_transpose64", "k_upper_matvec", "k_to_f32_transposed", "k_set_last",
                  "k_tri_diag_inv", "k_tri_inv_blk")

@@ -44,10 +44,13 @@ int trsm_upper(const double* R, int d, const double* B, int k, double* X, cudaSt
 int tri_inverse(const double* R, int d, double* M, cudaStream_t stream);
 // [SA | Sb]^T [SA | Sb] (float64, symmetric, nc = d + (Sb != NULL)) on the
 // tensor cores (3xTF32); CW_ERR_SHAPE when d > 256.
-int gram_tc(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsigned* tflag, cudaStream_t stream);
+// W32 (nullable) receives the same matrix rounded to float32.
+int gram_tc(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsigned* tflag, cudaStream_t stream,
+            float* W32 = nullptr);
 // The same Gram matrix for any d <= 1024: tensor cores when d <= 256, float32
 // CUDA-core tiles with float64 partials otherwise.
-int gram_f64(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsigned* tflag, cudaStream_t stream);
+int gram_f64(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsigned* tflag, cudaStream_t stream,
+             float* W32 = nullptr);
 // Gram + Cholesky + explicit inverse in shared memory (LSQR preconditioner).
 // With flags_dev NULL it synchronises and returns CW_ERR_RANK (non-positive
 // pivot) or CW_ERR_TIMEOUT, *kappa_lb_host receiving R's diagonal ratio.

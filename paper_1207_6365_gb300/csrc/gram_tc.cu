@@ -289,7 +289,7 @@ __device__ __forceinline__ void gt_two_add(float& hi, float& lo, float xh, float
 // the result does not depend on scheduling.
 __global__ void __launch_bounds__(256) k_gram_tc_reduce(const float* __restrict__ part,
                                                         const float* __restrict__ vpart, int grid, int d, int dp,
-                                                        int nc, double* __restrict__ Gm) {
+                                                        int nc, double* __restrict__ Gm, float* __restrict__ W32) {
     const int ci = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if ((int)blockIdx.x * 32 + 31 < ci) return;   // the whole block below the diagonal
     __shared__ float2 sp[8][32];
@@ -327,6 +327,10 @@ __global__ void __launch_bounds__(256) k_gram_tc_reduce(const float* __restrict_
         const double t = (double)th + (double)tl;
         Gm[(int64_t)ci * nc + cj] = t;
         Gm[(int64_t)cj * nc + ci] = t;
+        if (W32) {
+            W32[(int64_t)ci * nc + cj] = (float)t;
+            W32[(int64_t)cj * nc + ci] = (float)t;
+        }
     }
 }
 
@@ -334,12 +338,12 @@ __global__ void __launch_bounds__(256) k_gram_tc_reduce(const float* __restrict_
 
 // [SA | Sb]^T [SA | Sb] into Gm (nc = d + 1, float64, symmetric; nc = d and
 // SA^T SA alone when Sb is NULL) on the tensor cores; CW_ERR_SHAPE (nothing
-// launched) when d > 256.  With
+// launched) when d > 256.  W32 (nullable): the same matrix rounded to float32.  With
 // `tflag` (device word, zeroed by the caller) an MMA wait that gave up is
 // recorded there and the call does not synchronise; without it the call
 // synchronises and returns CW_ERR_TIMEOUT for that case.
 int gram_tc(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsigned* tflag_ext,
-            cudaStream_t stream) {
+            cudaStream_t stream, float* W32) {
     if (d < 1 || d > kGtMaxD || m < 1) return CW_ERR_SHAPE;
     const int dp = (d + 15) & ~15;
     int grid = num_sms();
@@ -366,7 +370,7 @@ int gram_tc(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsi
     {
         CW_PROF("k_gram_tc_reduce", stream);
         k_gram_tc_reduce<<<dim3((unsigned)((nc + 31) / 32), (unsigned)nc), 256, 0, stream>>>(a.part, a.vpart, grid, d,
-                                                                                            dp, nc, Gm);
+                                                                                            dp, nc, Gm, W32);
     }
     CW_LAUNCH_CHECK();
     if (tflag_ext) return CW_OK;

@@ -1354,9 +1354,10 @@ int qr64(const float* SA, int64_t m, int d, const float* Sb, double* R, double* 
 
 // [SA | Sb]^T [SA | Sb] (float64, nc x nc, nc = d + (Sb != NULL)).  Does not
 // synchronise; an MMA wait of the tensor-core kernel that gave up sets *tflag.
-int gram_f64(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsigned* tflag, cudaStream_t stream) {
+int gram_f64(const float* SA, int64_t m, int d, const float* Sb, double* Gm, unsigned* tflag, cudaStream_t stream,
+             float* W32) {
     if (d < 1 || d > 1024) return CW_ERR_SHAPE;
-    if (d <= 256) return gram_tc(SA, m, d, Sb, Gm, tflag, stream);
+    if (d <= 256) return gram_tc(SA, m, d, Sb, Gm, tflag, stream, W32);
     const int nc = d + (Sb ? 1 : 0);
     const int ntile = (d + kGT - 1) / kGT;
     const int ntl = ntile * (ntile + 1) / 2;
@@ -1380,6 +1381,10 @@ int gram_f64(const float* SA, int64_t m, int d, const float* Sb, double* Gm, uns
     {
         CW_PROF("k_gram_reduce", stream);
         k_gram_reduce2<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(part, vpart, nchunk, ntile, d, nc, Gm);
+    }
+    if (W32) {
+        CW_PROF("k_gram_to_f32", stream);
+        k_gram_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(Gm, tot, W32);
     }
     CW_LAUNCH_CHECK();
     return CW_OK;
@@ -1406,14 +1411,10 @@ int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double
     unsigned* bad = ws.at<unsigned>(oF);
     float* klb = reinterpret_cast<float*>(bad + 2);
     CW_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned) * 2 + sizeof(float) * 2, stream));
-    const int64_t tot = (int64_t)nc * nc;
-    // bad[1]: an MMA wait of the tensor-core Gram gave up
-    int gst = gram_f64(SA, m, d, Sb, Gm, bad + 1, stream);
+    // the Gram matrix in Gm (float64) and W (float32); bad[1]: an MMA wait of
+    // the tensor-core Gram gave up
+    int gst = gram_f64(SA, m, d, Sb, Gm, bad + 1, stream, W);
     if (gst != CW_OK) return gst;
-    {
-        CW_PROF("k_gram_to_f32", stream);
-        k_gram_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(Gm, tot, W);
-    }
     // one-CTA factorization when the packed triangle and a dense 32-row panel fit
     const int tpmax = (nc + 7) & ~7;
     const size_t psm = sizeof(float) * ((((size_t)nc * (nc + 1) / 2) + 3) & ~size_t(3)) +

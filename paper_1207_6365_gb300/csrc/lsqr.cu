@@ -300,13 +300,6 @@ __global__ void k_to_f32_transposed(double* __restrict__ M, int d, float* __rest
     }
 }
 
-
-// y = float32 copy of x (n entries).
-__global__ void k_copy_f32(const double* __restrict__ x, int n, float* __restrict__ y) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < n) y[q] = (float)x[q];
-}
-
 // y = add + R x (R upper triangular, float64 row-major): one warp per row,
 // lane l taking columns i + l, i + 32 + l, ..., then a fixed shuffle tree.
 // Rows spread over many SMs: float64 issues slowly on this part.
@@ -320,6 +313,26 @@ __global__ void __launch_bounds__(256) k_upper_matvec(const double* __restrict__
     for (int j = i + lane; j < d; j += 32) s = fma(R[(size_t)i * d + j], x[j], s);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
     if (lane == 0) y[i] = (add ? add[i] : 0.0) + s;
+}
+
+// The start of the iteration in one launch: x0 = M c (the sketch-and-solve
+// solution, computed as k_upper_matvec does), vhat = x0 in float32 (the first
+// pass's input) and y0 = c (= R x0).
+__global__ void __launch_bounds__(256) k_lsqr_start(const double* __restrict__ M, int d,
+                                                   const double* __restrict__ c, double* __restrict__ x0,
+                                                   float* __restrict__ vhat, double* __restrict__ y0) {
+    const int lane = threadIdx.x & 31;
+    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (i >= d) return;
+    double s = 0.0;
+    for (int j = i + lane; j < d; j += 32) s = fma(M[(size_t)i * d + j], c[j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if (lane == 0) {
+        const double v = 0.0 + s;
+        x0[i] = v;
+        vhat[i] = (float)v;
+        y0[i] = c[i];
+    }
 }
 
 }  // namespace cw
@@ -451,16 +464,9 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     auto start = [&]() -> int {
         CW_CUDA_TRY(cudaMemsetAsync(state, 0, sizeof(LsqrState), stream));
         {
-            CW_PROF("k_upper_matvec", stream);  // x0 = M c: the sketch-and-solve start
-            k_upper_matvec<<<(d + 7) / 8, 256, 0, stream>>>(M, d, c, x0, nullptr);
+            CW_PROF("k_lsqr_start", stream);  // x0 = M c, vhat = x0 (float32), y0 = c
+            k_lsqr_start<<<(d + 7) / 8, 256, 0, stream>>>(M, d, c, x0, vhat, y0);
         }
-        CW_LAUNCH_CHECK();
-        // first pass input: vhat = x0 (float32); y0 = R x0 = c
-        {
-            CW_PROF("k_copy_f32", stream);
-            k_copy_f32<<<(d + 255) / 256, 256, 0, stream>>>(x0, d, vhat);
-        }
-        CW_CUDA_TRY(cudaMemcpyAsync(y0, c, sizeof(double) * d, cudaMemcpyDeviceToDevice, stream));
         CW_LAUNCH_CHECK();
         pa = PassArgs{A->row_ptr, A->col, A->val, vhat, b, z, ws.at<float2>(ogp), ws.at<double>(ozp),
                       ws.at<double>(obp), nullptr, status, n, d, dpad, 1.0f};
