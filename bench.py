@@ -40,7 +40,7 @@ WORKLOAD = ("large sparse regression: CSR n=2^24 x d=256, 16 distinct Zipf(1.1) 
             "b=A x0+0.01 noise, CountSketch m=65536 seed 1, LSQR preconditioned by R from SA to rtol 1e-6")
 N_ROWS, D, K_NNZ, ZIPF_S, M, SEED, RTOL = 1 << 24, 256, 16, 1.1, 65536, 1, 1e-6
 DATA_SEED_A, DATA_SEED_B = 1002, 2002
-SAMPLE_ROWS_BASELINE = 1 << 22   # cpu_baseline leg: rows of the same workload
+SAMPLE_ROWS_CPU = 1 << 22   # cpu_baseline leg: rows of the same workload
 SAMPLE_ROWS_REFERENCE = 1 << 20  # --impl reference: rows per step
 
 # kernels reported in the stage breakdown, with their algorithmic bytes per launch
@@ -727,7 +727,7 @@ def run_cw(args):
     cpu_baseline = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            res = run_oracle_child(SAMPLE_ROWS_BASELINE, 1)
+            res = run_oracle_child(SAMPLE_ROWS_CPU, 1)
             cpu_baseline = cpu_baseline_block(
                 res, "first 2^22 rows of the workload (same d, m, seed, Zipf columns, rtol): float64 CPU oracle "
                      "(C sketch loop, LAPACK QR, LSQR with C matvecs), one step, 1 thread")
