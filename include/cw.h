@@ -342,9 +342,12 @@ int cw_solve_sketch_dense(const float *A, int64_t n, int64_t d, int64_t lda, con
                           int64_t m, uint64_t seed, double *x, double *R, cw_stream stream);
 
 /*
- * cw_lsqr_precond - least squares by LSQR on y -> A R^-1 y with R from the
- * QR of SA (Section 7.6, Theorem "it reg"), started at the sketch-and-solve
- * solution, returning x = R^-1 y.
+ * cw_lsqr_precond - least squares by LSQR on y -> A R^-1 y with R the
+ * triangular factor of SA (R^T R = SA^T SA, the R of its QR; Section 7.6,
+ * Theorem "it reg"), started at the sketch-and-solve solution, returning
+ * x = R^-1 y.  R comes from a Cholesky of the Gram matrix (cw_gram's), or from
+ * the float64 Householder QR of SA when that Cholesky fails or R's diagonal
+ * ratio exceeds 300.
  * Stops when ||(A R^-1)^T r|| / (||A R^-1||_F ||r||) <= rtol or
  * ||r|| <= rtol (||b|| + ||A R^-1||_F ||y||) (LSQR's own estimates of the
  * norms except ||b|| and ||y||).  rtol > 0, max_iter >= 0.
