@@ -82,7 +82,8 @@ const char *cw_status_string(int status);
 int cw_version(void);
 
 /*
- * Synchronise `stream`, then return and clear the calling device's sticky
+ * cw_device_status (a utility, no operation of the paper) - synchronise
+ * `stream`, then return and clear the calling device's sticky
  * device-side flag: CW_OK, or CW_ERR_DEVICE if some kernel of this library
  * met invalid input since the last call, or CW_ERR_CUDA if the sync failed.
  */
@@ -98,7 +99,8 @@ int cw_hash(uint64_t seed, int64_t m, int64_t i0, int64_t count, int32_t *bucket
             cw_stream stream);
 
 /*
- * cw_csr_check - validate the CSR structure the sketch kernels assume:
+ * cw_csr_check (a utility, no operation of the paper) - validate the CSR
+ * structure the sketch kernels assume:
  * row_ptr[0] = 0, row_ptr[n] = nnz, row_ptr non-decreasing, every column in
  * [0, d) and no column twice within a row.  Returns CW_OK or CW_ERR_ARG.
  * The sketch kernels themselves detect out-of-range columns and decreasing
@@ -124,7 +126,8 @@ int cw_sketch_csr(const cw_csr *A, const float *b, int64_t m, uint64_t seed, flo
  * cw_sketch_csr_rows - as cw_sketch_csr for a row shard: local row i of A is
  * global row i0 + i of the full matrix and is hashed with that global index,
  * so the sum over shards of their SA equals the SA of the whole matrix
- * (the exchange step when rows are spread over several devices).
+ * (SA is linear in the rows of A, Section 2: the exchange step when rows are
+ * spread over several devices).
  */
 int cw_sketch_csr_rows(const cw_csr *A, int64_t i0, const float *b, int64_t m, uint64_t seed,
                        float *SA, float *Sb, cw_stream stream);
@@ -170,7 +173,9 @@ int cw_sketch_dense_values(const float *A, int64_t n, int64_t d, int64_t lda, co
                            uint64_t seed, const float *v, float *SA, float *Sb, cw_stream stream);
 
 /*
- * cw_sketch_values_backward_* - gv_i = dL/dv_i = <gSA[h(i), :], A_i> + gSb[h(i)] b_i
+ * cw_sketch_values_backward_* - (not an operation of the paper: the derivative
+ * of the values sketch above, whose positions are the map h of Section 2)
+ * gv_i = dL/dv_i = <gSA[h(i), :], A_i> + gSb[h(i)] b_i
  * for a loss L with gradients gSA = dL/dSA (m x d row-major, device) and
  * gSb = dL/dSb (m, device; NULL, or b NULL, drops the second term).  gv: n
  * floats (device), fully overwritten.  One pass over the rows of A, each row
@@ -294,12 +299,15 @@ int cw_sketch_csr_noalloc(const cw_csr *A, const float *b, int64_t m, uint64_t s
 
 /*
  * cw_sketch_dense - SA and Sb for dense row-major A (n x d, leading dimension
- * lda >= d).  Same limits and outputs as cw_sketch_csr.  Asynchronous.
+ * lda >= d): the sparse embedding of Section 2 applied in O(nd) = O(nnz(A))
+ * time (Theorem 1 for a dense A).  Same limits and outputs as cw_sketch_csr.
+ * Asynchronous.
  */
 int cw_sketch_dense(const float *A, int64_t n, int64_t d, int64_t lda, const float *b, int64_t m,
                     uint64_t seed, float *SA, float *Sb, cw_stream stream);
 
-/* cw_sketch_vec - Sx for an n-vector x (the d = 1 case).  Asynchronous. */
+/* cw_sketch_vec - Sx for an n-vector x (the d = 1 case of Section 2's S A).
+ * Asynchronous. */
 int cw_sketch_vec(const float *x, int64_t n, int64_t m, uint64_t seed, float *Sx,
                   cw_stream stream);
 
@@ -337,7 +345,8 @@ int cw_qr(const float *SA, int64_t m, int64_t d, const float *Sb, double *R, dou
 int cw_solve_sketch(const cw_csr *A, const float *b, int64_t m, uint64_t seed, double *x,
                     double *R, cw_stream stream);
 
-/* cw_solve_sketch_dense - as cw_solve_sketch for dense row-major A. */
+/* cw_solve_sketch_dense - as cw_solve_sketch (Theorem "lin reg") for dense
+ * row-major A. */
 int cw_solve_sketch_dense(const float *A, int64_t n, int64_t d, int64_t lda, const float *b,
                           int64_t m, uint64_t seed, double *x, double *R, cw_stream stream);
 
