@@ -14,7 +14,9 @@ lo terms would be off by about 2^-10 relative on the diagonal (truncation
 errors all have the sign of x^2), tens of times above that tolerance at the
 sizes below; a dropped stage or a misplaced column is off by far more.
 d > 256 takes the float32 CUDA-core tiles with the same bound (their row
-chunks play the part of rows_per).
+chunks play the part of rows_per).  tests/test_gram_tolerance.py checks on the
+CPU that an emulation of the kernel's arithmetic meets this tolerance and that
+the emulated mistakes above do not.
 """
 import math
 
