@@ -146,7 +146,9 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // Per row one 16-byte record {key, a, len, sigma*b}: a = row start (CSR) or
 // the row index (dense); written in coarse-bin order, stable within a bin.
-// Tile `tile` of the rows; Orow = the tile's output offsets per bin.
+// Tile `tile` of the rows; Orow = the tile's output offsets per bin.  The
+// tile's lines of row_ptr and b are prefetched into L2 while its rows are
+// hashed, and their loads go out eight rows per lane at a time.
 // VALS: the sketch's entries are the given values v_i instead of the signs:
 // the record's last word is v_i (times b_i with HAS_B) and the sign is unused.
 template <int MODE, bool HAS_B, bool OUTER, bool VALS = false>
@@ -159,6 +161,16 @@ __device__ __forceinline__ void coarse_scatter_body(const HashParams& hp, int64_
     uint32_t* cnt = sm3;                                // [kTileWarps][nbins]
     uint32_t* skeys = sm3 + kTileWarps * nbins;         // [kTileWarps][kTileRowsPerWarp]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {   // the tile's lines of row_ptr, b (and vals) into L2 while its rows are hashed
+        const int64_t t0 = tile * kTileRows;
+        const int rows = (n - t0) < (int64_t)kTileRows ? (int)(n - t0) : kTileRows;
+        const int lines = (rows + 32) / 32;
+        for (int k = threadIdx.x; k < lines; k += blockDim.x) {
+            if (MODE == kModeCSR) asm volatile("prefetch.global.L2 [%0];" ::"l"(row_ptr + t0 + 32 * k));
+            if (HAS_B && 32 * k < rows) asm volatile("prefetch.global.L2 [%0];" ::"l"(b + t0 + 32 * k));
+            if (VALS && 32 * k < rows) asm volatile("prefetch.global.L2 [%0];" ::"l"(vals + t0 + 32 * k));
+        }
+    }
     for (int q = threadIdx.x; q < kTileWarps * nbins; q += blockDim.x) cnt[q] = 0;
     __syncthreads();
     const int64_t r0 = tile * kTileRows + warp * kTileRowsPerWarp + lane;
@@ -188,13 +200,14 @@ __device__ __forceinline__ void coarse_scatter_body(const HashParams& hp, int64_
     }
     __syncthreads();
     const unsigned lt = lanemask_lt();
+    constexpr int GR = 8;  // rows per lane whose loads are in flight together
 #pragma unroll 1
-    for (int j0 = 0; j0 < kTileRowsPerLane; j0 += 4) {
+    for (int j0 = 0; j0 < kTileRowsPerLane; j0 += GR) {
         if (r0 - lane + 32 * j0 >= n) break;
-        int32_t st[4], ln[4];
-        float bv[4], wv[4];
+        int32_t st[GR], ln[GR];
+        float bv[GR], wv[GR];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < GR; ++u) {
             const int64_t r = r0 + 32 * (j0 + u);
             st[u] = 0;
             ln[u] = 0;
@@ -212,7 +225,7 @@ __device__ __forceinline__ void coarse_scatter_body(const HashParams& hp, int64_
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < GR; ++u) {
             const int j = j0 + u;
             const int64_t r = r0 + 32 * j;
             const bool valid = r < n;
