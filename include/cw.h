@@ -283,19 +283,30 @@ int cw_batch_destroy(cw_batch *plan);
  * so this call makes no cudaMalloc / cudaMallocAsync / cudaFree call and no
  * allocating library call.  Every GPU that loads the library holds that array
  * until the process exits.
- * Limit: n * 28 + (m + 1) * 4 bytes plus the tile histograms must fit in
- * 24 MiB (roughly n <= 800,000 rows for m = 65536); larger problems return
- * CW_ERR_SHAPE without launching anything.
+ * Limit: n * 28 (n * 24 without b) + (m + 1) * 4 bytes plus the tile
+ * histograms must fit in 24 MiB (roughly n <= 850,000 rows with b for
+ * m = 65536); larger problems return CW_ERR_SHAPE without launching anything.
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it; make that first call before capturing
  * any stream.  All calls share the array and it keeps the previous call's
  * contents (what must start at zero is cleared by every call); calls whose
  * work can overlap on the GPU race on it and must be ordered by the caller.
- * Input errors found on the device are kept in a separate static flag and are
- * not reported by cw_device_status().  Asynchronous.
+ * Input errors found on the device (a column out of range, a decreasing
+ * row_ptr) are kept in a separate static flag that cw_noalloc_status() reads
+ * and clears; cw_device_status() does not see it.  Asynchronous.
  */
 int cw_sketch_csr_noalloc(const cw_csr *A, const float *b, int64_t m, uint64_t seed, float *SA,
                           float *Sb, cw_stream stream);
+
+/*
+ * cw_noalloc_status - synchronise `stream`, then return and clear the input
+ * flag that cw_sketch_csr_noalloc calls on the current device have set since
+ * the last read: CW_OK, CW_ERR_DEVICE if one of them met invalid input, or
+ * CW_ERR_CUDA.  Like cw_sketch_csr_noalloc it allocates nothing (the word is
+ * copied into a host variable of the call), so the same callers can use it.
+ * (No counterpart in the paper.)
+ */
+int cw_noalloc_status(cw_stream stream);
 
 /*
  * cw_sketch_dense - SA and Sb for dense row-major A (n x d, leading dimension

@@ -26,9 +26,9 @@ __all__ = [
 
 HEADER = os.path.join(_build.ROOT, "include", "cw.h")
 EXPORTS = (
-    "cw_status_string", "cw_version", "cw_device_status", "cw_csr_check", "cw_hash", "cw_sketch_csr",
-    "cw_sketch_csr_rows", "cw_sketch_csr_general", "cw_sketch_csr_noalloc", "cw_sketch_dense", "cw_sketch_vec",
-    "cw_gram", "cw_qr", "cw_solve_sketch", "cw_batch_create", "cw_batch_run", "cw_batch_finish", "cw_batch_info",
+    "cw_status_string", "cw_version", "cw_device_status", "cw_selftest_barrier_timeout", "cw_csr_check", "cw_hash", "cw_sketch_csr",
+    "cw_sketch_csr_rows", "cw_sketch_csr_general", "cw_sketch_csr_noalloc", "cw_noalloc_status", "cw_sketch_dense",
+    "cw_sketch_vec", "cw_gram", "cw_qr", "cw_solve_sketch", "cw_batch_create", "cw_batch_run", "cw_batch_finish", "cw_batch_info",
     "cw_batch_phases", "cw_batch_destroy", "cw_sketch_csr_values", "cw_sketch_dense_values",
     "cw_sketch_values_backward_csr", "cw_sketch_values_backward_dense", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
     "cw_launch_count", "cw_profile_enable", "cw_profile_get", "cw_profile_reset",
@@ -62,11 +62,13 @@ _SIGS = {
     "cw_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "cw_version": ([], ctypes.c_int),
     "cw_device_status": ([_p], ctypes.c_int),
+    "cw_selftest_barrier_timeout": ([_i32, _i64, _p], ctypes.c_int),
     "cw_csr_check": ([ctypes.POINTER(_CSR), _p], ctypes.c_int),
     "cw_hash": ([_u64, _i64, _i64, _i64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_csr": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_csr_rows": ([ctypes.POINTER(_CSR), _i64, _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_sketch_csr_noalloc": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
+    "cw_noalloc_status": ([_p], ctypes.c_int),
     "cw_sketch_csr_values": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p, _p], ctypes.c_int),
     "cw_sketch_dense_values": ([_p, _i64, _i64, _i64, _p, _i64, _u64, _p, _p, _p, _p], ctypes.c_int),
     "cw_sketch_values_backward_csr": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _p, _p, _p, _p], ctypes.c_int),

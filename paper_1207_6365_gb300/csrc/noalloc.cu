@@ -13,7 +13,9 @@
 // call's contents; the kernels clear what must start at zero on every call.
 // Calls whose work overlaps on the GPU (different streams, or the same stream
 // with graph-level concurrency) race on the array and must be serialised by
-// the caller.
+// the caller.  Input errors found on the device (a column out of range, a
+// decreasing row_ptr) go to a second static word that cw_noalloc_status reads
+// and clears, again without allocating.
 #include <mutex>
 
 #include "cw_common.cuh"
@@ -77,4 +79,17 @@ extern "C" int cw_sketch_csr_noalloc(const cw_csr* A, const float* b, int64_t m,
     const cw::ProfSuppress no_events;  // no CUDA events are created inside this call
     return cw::sketch_impl(cw::kSketchCSR, A->n, A->d, 0, 0, A->row_ptr, A->col, A->val, nullptr, b, m, seed, SA,
                            b ? Sb : nullptr, nullptr, stream, nullptr, &ws);
+}
+
+extern "C" int cw_noalloc_status(cw_stream stream) {
+    void* scratch = nullptr;
+    unsigned* status = nullptr;
+    int st = cw::noalloc_setup(&scratch, &status);
+    if (st != CW_OK) return st;
+    unsigned v = 0;  // host word on the stack: nothing is allocated
+    cudaStream_t s = (cudaStream_t)stream;
+    CW_CUDA_TRY(cudaMemcpyAsync(&v, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CW_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
+    CW_CUDA_TRY(cudaStreamSynchronize(s));
+    return v ? CW_ERR_DEVICE : CW_OK;
 }
