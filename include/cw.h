@@ -90,6 +90,18 @@ int cw_version(void);
 int cw_device_status(cw_stream stream);
 
 /*
+ * cw_selftest_barrier_timeout (a test utility, no operation of the paper) -
+ * runs the library's bounded grid barrier (the one its cooperative kernels
+ * use) with `blocks` blocks that wait for one arrival more than the grid has,
+ * so every wait gives up after spin_limit polls (about 64 ns apart) and its
+ * block returns.  Returns CW_ERR_TIMEOUT, the status every timed-out
+ * device-side wait of the library produces; CW_OK would mean the barrier did
+ * not wait.  blocks in [1, 1024], spin_limit in [1, 2^24], else CW_ERR_ARG.
+ * Synchronises `stream`; the context stays usable afterwards.
+ */
+int cw_selftest_barrier_timeout(int32_t blocks, int64_t spin_limit, cw_stream stream);
+
+/*
  * cw_hash - the map (h, sigma) defining S (paper Section 2).
  * bucket[k] = h(i0 + k) in [0, m), sign[k] = sigma(i0 + k) in {+1, -1} for
  * k < count.  Requirements: m >= 1, 0 <= i0, i0 + count <= 2^62.  Either

@@ -179,6 +179,34 @@ const char* cw_status_string(int status) {
 
 int cw_version(void) { return 100; }
 
+// Every block waits at a grid barrier that expects one arrival more than the
+// grid has, so each wait runs out after spin_limit polls and the block returns.
+__global__ void k_barrier_timeout_probe(unsigned* bar, unsigned* flag, long long spin_limit) {
+    cw::grid_barrier(bar, gridDim.x + 1, flag, spin_limit);
+}
+
+int cw_selftest_barrier_timeout(int32_t blocks, int64_t spin_limit, cw_stream stream) {
+    if (blocks < 1 || blocks > 1024 || spin_limit < 1 || spin_limit > (1ll << 24)) return CW_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned* w = nullptr;
+    CW_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&w), 4 * sizeof(unsigned), s));
+    cudaError_t e = cudaMemsetAsync(w, 0, 4 * sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+        cw::count_launch();
+        k_barrier_timeout_probe<<<blocks, 32, 0, s>>>(w, w + 2, spin_limit);
+        e = cudaGetLastError();
+    }
+    unsigned flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, w + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(w, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return CW_ERR_CUDA;
+    }
+    return flag ? CW_ERR_TIMEOUT : CW_OK;
+}
+
 int cw_device_status(cw_stream stream) {
     unsigned* w = cw::device_status_word();
     if (!w) return CW_ERR_CUDA;

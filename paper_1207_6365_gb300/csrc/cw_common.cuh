@@ -323,8 +323,10 @@ class Scratch {
 constexpr long long kBarrierSpinLimit = 1ll << 24;  // ~1 s with 64 ns sleeps
 
 // bar[0] = arrival count, bar[1] = generation.  Returns false (after flagging
-// the status word) when the wait exceeded its limit; the caller must return.
-static __device__ __noinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* timeout_flag) {
+// the status word) when the wait exceeded its limit (spin_limit polls); the
+// caller must return.
+static __device__ __noinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* timeout_flag,
+                                                 long long spin_limit = kBarrierSpinLimit) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -340,7 +342,7 @@ static __device__ __noinline__ bool grid_barrier(unsigned* bar, unsigned nblocks
             long long it = 0;
             while (atomicAdd(&bar[1], 0u) == gen) {
                 __nanosleep(64);
-                if (++it > kBarrierSpinLimit) {
+                if (++it > spin_limit) {
                     atomicExch(timeout_flag, 1u);
                     ok = 0;
                     break;

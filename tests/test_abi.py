@@ -50,6 +50,10 @@ def test_host_side_validation_rejects_bad_arguments():
     assert lib.cw_hash(1, 10, -1, 10, null, null, null) == -3
     assert lib.cw_hash(1, 10, 2**62, 10, null, null, null) == -3
     assert lib.cw_sketch_csr(null, null, 10, 1, null, null, null) == -1
+    # the barrier self-test checks its arguments before touching the device
+    assert lib.cw_selftest_barrier_timeout(0, 100, null) == -1
+    assert lib.cw_selftest_barrier_timeout(2, 0, null) == -1
+    assert lib.cw_selftest_barrier_timeout(2, (1 << 24) + 1, null) == -1
     c = cw._CSR()
     c.n, c.d, c.nnz = 10, 4, 10
     assert lib.cw_sketch_csr(ctypes.byref(c), null, 0, 1, ctypes.c_void_p(16), null, null) == -2
