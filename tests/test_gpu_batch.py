@@ -9,7 +9,11 @@ the residual ratio ||A x' - b|| / ||A x* - b|| equal to the oracle's (oracle
 SA, oracle QR) to 1e-6.  Edge cases: empty and rank-deficient problems,
 d = 1, m = d, n < m, an ill-conditioned problem that must go to the QR
 fallback, determinism, graph and direct launches agreeing, and the autotuner
-with its cache file.
+with its cache file.  Every variant the autotuner can choose (segmented sum
+with 16 or 32 lanes per row, or over whole 16- or 8-bucket ranges; slabs of
+512 and 4096 bucket rows; one or two CTAs per SM) is forced through the tune
+cache and checked the same way, on a set that includes a problem of the
+workload's largest shape (n = 2^18, d = 128, m = 65536).
 """
 import numpy as np
 import pytest
@@ -183,3 +187,77 @@ def test_batch_autotune_and_cache(cw, tmp_path, monkeypatch):
     assert B2.info()["tuned"] == 2 and B2.info()["slab"] == info["slab"]
     B.close()
     B2.close()
+
+
+# ---------------------------------------------------------------- every tuned variant against the oracle
+
+def _fnv(h, v):
+    # FNV-1a over the eight little-endian bytes of v (the tune cache's key)
+    for k in range(8):
+        h ^= (v >> (8 * k)) & 0xFF
+        h = (h * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _shape_key(cpu):
+    h = 1469598103934665603
+    h = _fnv(h, len(cpu))
+    h = _fnv(h, torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    for A, _, m, _ in cpu:
+        for v in (A.n, A.d, A.nnz, m):
+            h = _fnv(h, v)
+    return h
+
+
+_VARIANT_SET = {}
+
+
+def _variant_set():
+    """Problems of uneven n and d, one of them at the workload's largest shape,
+    with the oracle's sketch, its bounds and solution (computed once)."""
+    if not _VARIANT_SET:
+        shapes = W.batch_shapes(10, seed=13, log2n=(9, 14), dset=(16, 33, 64, 128))
+        shapes.append(dict(n=1 << 18, d=128, m=65536, kmin=4, kmax=32, seed=77))
+        probs, cpu = _make(shapes)
+        ref = []
+        for A, b, m, seed in cpu:
+            SA_o, Sb_o = oracle.sketch_csr(A.row_ptr, A.col, A.val, A.d, b, m, seed)
+            h, _ = oracle.hash(seed, m, 0, A.n)
+            rp, c, v = A.numpy()
+            rows = np.repeat(np.arange(A.n), np.diff(rp))
+            absA = np.zeros((m, A.d))
+            np.add.at(absA, (h[rows], c), np.abs(v.astype(np.float64)))
+            absb = np.zeros(m)
+            np.add.at(absb, h, np.abs(b.double().numpy()))
+            k = np.bincount(h, minlength=m).astype(np.float64)
+            E, Eb = (k[:, None] * 2.0 ** -24) * absA, k * 2.0 ** -24 * absb
+            x_o, _ = oracle.solve_sketch(SA_o, Sb_o)
+            ref.append(dict(SA_o=SA_o, Sb_o=Sb_o, absA=absA, absb=absb,
+                            bound=_x_bound(SA_o, Sb_o, x_o, E, Eb), x_o=x_o))
+        _VARIANT_SET.update(probs=probs, cpu=cpu, ref=ref)
+    return _VARIANT_SET
+
+
+@pytest.mark.parametrize("cps", [1, 2])
+@pytest.mark.parametrize("slab", [512, 4096])
+@pytest.mark.parametrize("lpr", [16, 32, 0, -8])
+def test_batch_every_tuned_variant_matches_oracle(cw, tmp_path, monkeypatch, lpr, slab, cps):
+    V = _variant_set()
+    cache = tmp_path / "tune.txt"
+    cache.write_text("batch %x %d %d %d\n" % (_shape_key(V["cpu"]), slab, cps, lpr))
+    monkeypatch.setenv("CW_TUNE_CACHE", str(cache))
+    B = cw.Batch(V["probs"], autotune=True, keep_sketch=True)
+    info = B.info()
+    assert info["tuned"] == 2, info  # taken from the cache, not re-tuned
+    assert (info["slab"], info["ctas_per_sm"], info["lanes_per_row"]) == (slab, cps, lpr), info
+    B.run()
+    assert B.finish() == [0] * len(V["probs"])
+    for p, R in enumerate(V["ref"]):
+        err = np.abs(B.SA[p].cpu().double().numpy() - R["SA_o"])
+        assert (err <= TOL * R["absA"] + 1e-30).all(), ("SA", p)
+        errb = np.abs(B.Sb[p].cpu().double().numpy() - R["Sb_o"])
+        assert (errb <= TOL * R["absb"] + 1e-30).all(), ("Sb", p)
+        x = B.x[p].cpu().numpy()
+        err_x = np.abs(x - R["x_o"])
+        assert (err_x <= 4 * R["bound"] + 1e-8 * np.abs(R["x_o"]).max()).all(), ("x", p)
+    B.close()
