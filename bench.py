@@ -96,6 +96,7 @@ def parse():
     ap.add_argument("--only-batch", type=int, default=0,
                     help="only plan and run the first N problems of the batched workload (profiling)")
     ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-sketch-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -297,6 +298,38 @@ def oracle_worker(rows, steps):
     print(json.dumps({"rows": rows, "nnz": nnz, "times": ts, "iters": its}))
 
 
+def oracle_sketch_worker(rows, reps):
+    """Runs in a child process: the all-core float64 oracle sketch (SA and Sb,
+    rows sorted by bucket, buckets summed in parallel) on the workload's first
+    `rows` rows; prints one JSON line."""
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    A, b = make_problem(dev, rows=rows)
+    rp, col, val = A.numpy()
+    b_np = b.cpu().numpy()
+    del A, b
+    import oracle
+    oracle.build()
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.sketch_csr_parallel(rp, col, val, D, b_np, M, SEED, threads=threads)
+        ts.append(time.perf_counter() - t0)
+    print(json.dumps({"rows": rows, "nnz": int(rp[-1]), "times": ts, "threads": threads}))
+
+
+def run_oracle_sketch_child(rows, reps):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        env.pop(k, None)
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sketch-worker", str(rows),
+                          "--oracle-steps", str(reps)], env=env, capture_output=True, text=True, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sketch worker failed:\n" + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 def run_oracle_child(rows, steps):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
@@ -409,6 +442,7 @@ def row_timings(cw, A, b, stream, peak):
     rows["A1_A2_hash_sort_ms"] = sum(v for k, v in st.items() if k in sort_k)
     rows["A3_segmented_sum_ms"] = st.get("k_apply_csr")
     rows["A1_A3_sketch_csr_ms"] = ms
+    rows.update(tiny_latency(cw, stream))
     rows["A4_qr_fp64_ms"] = _timed(lambda: cw.cw_qr(SA, Sb), stream, reps=2)
     rows["A5_sketch_and_solve_ms"] = _timed(lambda: cw.cw_solve_sketch(A, b, M, SEED), stream, reps=2)
     # generalized sparse embedding: q = 1024 blocks, v = 16, kappa = 4 (t = 65536 rows, as SA above)
@@ -464,7 +498,68 @@ def row_timings(cw, A, b, stream, peak):
     rows["dense_workload"] = "A: n=2^22 x d=512 float32 N(0,1) (timing only), m=65536, G: 512 x 32, seed 1"
     del A3, G3
     torch.cuda.empty_cache()
+    rows.update(leverage_error_row(cw))
     return rows
+
+
+def tiny_latency(cw, stream, calls=50):
+    """The tiny sketch-and-solve configuration: CSR n = 65536, d = 32, 8 uniform
+    distinct columns per row, b = A x0 + 0.1 noise, m = 4096, seed 1.  Latency of
+    one cw_solve_sketch call (sketch, float64 QR, solve; it returns after x' is
+    on the device) as the caller sees it (host wall clock, median of `calls`),
+    and of the sketch alone (CUDA events)."""
+    import torch
+    import workloads as W
+    A = W.csr_uniform(65536, 32, 8, seed=1001, device="cuda")
+    b, _ = W.rhs(A, 0.1, seed=2001)
+    b = b.cuda()
+    for _ in range(3):
+        cw.cw_solve_sketch(A, b, 4096, 1)
+    torch.cuda.synchronize()
+    wall = []
+    for _ in range(calls):
+        t0 = time.perf_counter()
+        cw.cw_solve_sketch(A, b, 4096, 1)
+        torch.cuda.synchronize()
+        wall.append((time.perf_counter() - t0) * 1e6)
+    sk_us = 1000.0 * _timed(lambda: cw.cw_sketch_csr(A, b, 4096, 1), stream, reps=20, warm=3)
+    return {"C1_solve_sketch_us": statistics.median(wall), "C1_solve_sketch_us_min": min(wall),
+            "C1_sketch_csr_us": sk_us,
+            "C1_workload": "CSR n=65536, d=32, 8 uniform distinct columns/row, m=4096, seed 1"}
+
+
+def leverage_error_row(cw, sample=1 << 16):
+    """The dense leverage configuration: A = U diag(sigma) V^T, n = 2^22, d = 512,
+    U and V Haar, sigma geometric from 1 to 1e-6 (kappa = 1e6), m = 65536,
+    G 512 x 32.  The library's leverage scores against the float64 oracle's
+    same algorithm (its own sketch of the stored A, its own QR, the same G) on
+    `sample` rows drawn uniformly (seed 9)."""
+    import numpy as np
+    import torch
+    import oracle
+    import workloads as W
+    t0 = time.perf_counter()
+    n, d, k = 1 << 22, 512, 32
+    A = W.dense_lowrank(n, d, W.geometric_sigma(d, 1e-6), seed=1003, device="cuda")
+    G = W.gaussian(d, k, seed=2)
+    lev = cw.cw_leverage(A, M, SEED, G.cuda())
+    torch.cuda.synchronize()
+    t_gpu = time.perf_counter() - t0
+    A_h = A.cpu().numpy()
+    lev_h = lev.cpu().double().numpy()
+    del A, lev
+    torch.cuda.empty_cache()
+    t1 = time.perf_counter()
+    SA_o, _ = oracle.sketch_dense(A_h, None, M, SEED)
+    R_o, _ = oracle.qr_r(SA_o)
+    rows = np.random.default_rng(9).choice(n, size=sample, replace=False)
+    lev_o = oracle.leverage_same(A_h, R_o, G.numpy(), rows=rows)
+    rel = np.abs(lev_h[rows] - lev_o) / lev_o
+    return {"C3_leverage_rel_err_max": float(rel.max()), "C3_leverage_rel_err_median": float(np.median(rel)),
+            "C3_leverage_rows_checked": int(sample), "C3_leverage_target": 1e-3,
+            "C3_seconds_generate_and_gpu": t_gpu, "C3_seconds_oracle": time.perf_counter() - t1,
+            "C3_workload": "dense A = U diag(sigma) V^T, n=2^22, d=512, U, V Haar, sigma 1 -> 1e-6, m=65536, "
+                           "G 512 x 32; oracle: float64 sketch of the stored A, QR, same G, on sampled rows"}
 
 
 def batch_timings(cw, stream, count=512):
@@ -524,7 +619,19 @@ def batch_timings(cw, stream, count=512):
              "kb_fine_sort", "kb_set_last", "kb_apply_csr", "k_batch_solve")  # (kb_apply_csr: any variant)
     out["N1_stages_ms"] = _stage_ms(cw, names, 1)
     E.close()
-    # one problem at a time through the single-problem API
+    # one problem at a time with the same solver: a one-problem plan per problem
+    # (the batch's sketch kernels and persistent solve kernel, one graph each),
+    # launched one after the other
+    singles = [cw.Batch([pr], autotune=False) for pr in probs]
+    for S1 in singles:
+        S1.run()
+        S1.finish()
+    out["N1_one_at_a_time_same_solver_ms"] = _timed(lambda: [S1.run() for S1 in singles], stream, reps=2, warm=1)
+    for S1 in singles:
+        S1.close()
+    del singles
+    out["N1_speedup_same_solver"] = out["N1_one_at_a_time_same_solver_ms"] / out["N1_batched_ms"]
+    # one problem at a time through the single-problem API (float64 Householder QR)
     def one_by_one():
         for A, b, m, seed in probs:
             cw.cw_solve_sketch(A, b, m, seed)
@@ -667,6 +774,24 @@ def run_cw(args):
     torch.cuda.synchronize()
     sk_ms = s0.elapsed_time(s1) / reps
     sk_bytes = nnz * 8 + (n + 1) * 4 + n * 4 + M * D * 4 + M * 4
+    cw.profile_reset()
+    cw.profile_enable(True)
+    for _ in range(reps):
+        cw.cw_sketch_csr(A, b, M, SEED, SA, Sb)
+    torch.cuda.synchronize()
+    cw.profile_enable(False)
+    sk_stages = {}
+    for kname in ("k_tile_hist", "k_scan_chunk_sums", "k_scan_bins", "k_scan_tiles", "k_coarse_scatter",
+                  "k_fine_sort", "k_set_last", "k_apply_csr"):
+        cnt, tot = cw.profile_get(kname)
+        if cnt:
+            sk_stages[kname] = tot / reps
+    sk_ach = sk_bytes / (sk_ms / 1000.0) / 1e9
+    sketch_roofline = {"call": "cw_sketch_csr (hash, bucket sort, segmented sum: 8 kernels)", "bound": "hbm",
+                       "achieved": sk_ach, "peak": peak, "unit": "GB/s", "frac": sk_ach / peak,
+                       "peak_source": peak_kind, "alg_bytes_per_call": sk_bytes, "ms": sk_ms,
+                       "nnz_per_s": nnz / (sk_ms / 1000.0), "traffic": ncu_traffic("k_apply_csr"),
+                       "traffic_of": "k_apply_csr (the segmented sum)", "stages_ms": sk_stages}
     del SA, Sb
 
     # end to end through the C ABI from pinned host buffers
@@ -724,6 +849,18 @@ def run_cw(args):
                 torch.cuda.synchronize()
                 torch.cuda.empty_cache()
 
+    cpu_all = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            r2 = run_oracle_sketch_child(n, 3)
+            tt = min(r2["times"])
+            cpu_all = {"value": r2["nnz"] / tt, "unit": "nnz/s", "cores": r2["threads"], "kind": "oracle",
+                       "sample": "SA and Sb of the whole workload (n = %d rows) by the float64 oracle on all "
+                                 "host cores (rows sorted by bucket, buckets summed in parallel), best of 3"
+                                 % r2["rows"],
+                       "seconds": tt, "gpu_sketch_nnz_per_s": nnz / (sk_ms / 1000.0), "host": host_info()}
+        except Exception as exc:  # report, do not hide, a failed baseline
+            cpu_all = {"error": str(exc)[-300:]}
     cpu_baseline = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -745,9 +882,8 @@ def run_cw(args):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches_all), "lsqr_iters": iters[-1] if iters else None,
-                "sketch": {"ms": sk_ms, "nnz_per_s": nnz / (sk_ms / 1000.0),
-                           "alg_GBps": sk_bytes / (sk_ms / 1000.0) / 1e9,
-                           "frac_of_peak": sk_bytes / (sk_ms / 1000.0) / 1e9 / peak},
+                "sketch_roofline": sketch_roofline,
+                "cpu_baseline_all_cores": cpu_all,
                 "stages": stages, "rows": rows}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -802,6 +938,9 @@ def main():
         return run_qr_only(args.only_qr[0], args.only_qr[1])
     if args.oracle_worker:
         oracle_worker(args.oracle_worker, args.oracle_steps)
+        return 0
+    if args.oracle_sketch_worker:
+        oracle_sketch_worker(args.oracle_sketch_worker, args.oracle_steps)
         return 0
     if args.impl == "reference":
         return run_reference(args)

@@ -28,6 +28,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#include <omp.h>
 
 #define ORC_P ((uint64_t)0x1FFFFFFFFFFFFFFFull) /* 2^61 - 1 */
 
@@ -143,6 +144,55 @@ void orc_sketch_csr(int64_t n, int64_t d, const int32_t *row_ptr, const int32_t 
             SA[h * d + col[k]] += (double)s * (double)val[k];
         if (Sb) Sb[h] += (double)s * (double)b[i];
     }
+}
+
+/*
+ * The same SA and Sb on all host cores, for the CPU baseline's all-core
+ * variant: every row's (h, sigma) is computed in parallel, the rows are
+ * counting-sorted by bucket (stable: ascending row order inside a bucket,
+ * the permutation P of Section 5.2), and the buckets are summed in parallel,
+ * each over its rows in ascending order.  Every entry of SA and Sb is thus the
+ * same float64 sum, taken in the same order, as in orc_sketch_csr: the two
+ * give bitwise identical results.  `threads` <= 0 uses the OpenMP default.
+ */
+void orc_sketch_csr_parallel(int64_t n, int64_t d, const int32_t *row_ptr, const int32_t *col,
+                             const float *val, const float *b, int64_t m, uint64_t seed, int64_t i0,
+                             int threads, double *SA, double *Sb)
+{
+    orc_poly P;
+    int64_t i, j;
+    int64_t *h = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int *sg = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int64_t *start = (int64_t *)calloc((size_t)m + 1, sizeof(int64_t));
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (threads <= 0) threads = omp_get_max_threads();
+    orc_coefficients(seed, &P);
+    memset(SA, 0, sizeof(double) * (size_t)m * (size_t)d);
+    if (Sb) memset(Sb, 0, sizeof(double) * (size_t)m);
+#pragma omp parallel for num_threads(threads) schedule(static)
+    for (i = 0; i < n; ++i) orc_bucket_sign(&P, (uint64_t)(i0 + i), (uint64_t)m, &h[i], &sg[i]);
+    for (i = 0; i < n; ++i) ++start[h[i] + 1];
+    for (j = 0; j < m; ++j) start[j + 1] += start[j];
+    {
+        int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+        memcpy(fill, start, sizeof(int64_t) * (size_t)m);
+        for (i = 0; i < n; ++i) order[fill[h[i]]++] = i;
+        free(fill);
+    }
+#pragma omp parallel for num_threads(threads) schedule(dynamic, 64)
+    for (j = 0; j < m; ++j) {
+        int64_t q, k;
+        for (q = start[j]; q < start[j + 1]; ++q) {
+            const int64_t r = order[q];
+            for (k = row_ptr[r]; k < row_ptr[r + 1]; ++k)
+                SA[j * d + col[k]] += (double)sg[r] * (double)val[k];
+            if (Sb) Sb[j] += (double)sg[r] * (double)b[r];
+        }
+    }
+    free(h);
+    free(sg);
+    free(start);
+    free(order);
 }
 
 /*

@@ -231,6 +231,15 @@ def test_leverage_matches_same_algorithm_ill_conditioned(cw):
     assert 0.8 < np.median(lev / u) < 1.25
 
 
+def test_leverage_at_the_dense_workload_shape(cw):
+    # the dense leverage workload's d, m, k and kappa (d = 512: eight 64-column
+    # chunks of the tensor-core product; a 65536 x 512 sketch: sixteen panels of
+    # the blocked float64 QR), on 2^17 rows instead of 2^22
+    A, lev, lev_o = _lev_case(cw, 1 << 17, 512, 65536, 32, 1e6, seed=23)
+    rel = np.abs(lev - lev_o) / lev_o
+    assert rel.max() <= 1e-3, rel.max()
+
+
 @pytest.mark.parametrize("n,d,m,k", [(20001, 100, 1024, 32), (5000, 33, 700, 7), (3000, 520, 2048, 40),
                                      (30001, 200, 2048, 32), (10000, 128, 1024, 7)])
 def test_leverage_shapes(cw, n, d, m, k):

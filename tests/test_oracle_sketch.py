@@ -95,3 +95,16 @@ def test_frobenius_expectation_matrix():
         vals.append(float((SA ** 2).sum()))
     vals = np.array(vals)
     assert abs(vals.mean() / fro - 1) < 5 * vals.std() / np.sqrt(len(vals)) / fro
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_all_core_variant_equals_the_plain_loop_bitwise(threads):
+    # the all-core variant sums each bucket's rows in the same ascending order
+    # as the plain row loop, so its float64 results are identical
+    A = W.csr_random_lengths(30001, 24, 0, 20, seed=41, empty_frac=0.1)
+    b = torch.randn(A.n, generator=torch.Generator().manual_seed(42))
+    for m, seed in ((1000, 3), (7, 5), (65536, 1)):
+        SA, Sb = oracle.sketch_csr(A.row_ptr, A.col, A.val, A.d, b, m, seed, i0=17)
+        SAp, Sbp = oracle.sketch_csr_parallel(A.row_ptr, A.col, A.val, A.d, b, m, seed, i0=17, threads=threads)
+        np.testing.assert_array_equal(SA, SAp)
+        np.testing.assert_array_equal(Sb, Sbp)
