@@ -392,6 +392,24 @@ int cw_lsqr_precond(const cw_csr *A, const float *b, int64_t m, uint64_t seed, d
                     cw_stream stream);
 
 /*
+ * cw_lsqr_precond_host - cw_lsqr_precond (Section 7.6, Theorem "it reg") for A
+ * and b in HOST memory: A->row_ptr, A->col, A->val, b and x are host pointers
+ * (page-locked memory lets the copies run asynchronously).  The library
+ * allocates the device copy, copies A in eight row chunks of about equal
+ * nonzero count on a stream of its own and sketches each chunk as soon as it
+ * has landed, as a row shard with its global row offset: SA = sum over the
+ * chunks of S_k A_k in chunk order (Section 2's S applied block by block; the
+ * float32 sums are grouped by chunk, so SA can differ from cw_sketch_csr's in
+ * the last bits, deterministically).  Then the preconditioner and the LSQR
+ * iterations run as in cw_lsqr_precond, and x (d float64) is copied back.
+ * Requires row_ptr[0] = 0 and row_ptr[n] = nnz (CW_ERR_ARG otherwise).  Same
+ * limits, statuses and stopping rule as cw_lsqr_precond.  Synchronises.
+ */
+int cw_lsqr_precond_host(const cw_csr *A, const float *b, int64_t m, uint64_t seed, double rtol,
+                         int32_t max_iter, double *x, int32_t *iters, double *final_test,
+                         cw_stream stream);
+
+/*
  * cw_leverage - approximate leverage scores (Section 6, Theorem "icml"):
  * lev[i] = ||(A R^-1 G)_i||^2 / k, with R from the QR of SA (S with m rows
  * and `seed`) and G a d x k float64 Gaussian matrix supplied by the caller

@@ -19,7 +19,7 @@ from . import _build
 __all__ = [
     "CWError", "lib", "load", "status_string", "device_status", "cw_csr_check",
     "cw_hash", "cw_sketch_csr", "cw_sketch_csr_rows", "cw_sketch_csr_general", "cw_sketch_dense", "cw_sketch_vec",
-    "cw_gram", "cw_qr", "cw_solve_sketch", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
+    "cw_gram", "cw_qr", "cw_solve_sketch", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_lsqr_precond_host", "cw_leverage",
     "cw_sketch_csr_values", "cw_sketch_dense_values", "cw_sketch_values_backward_csr",
     "cw_sketch_values_backward_dense", "SketchValues", "Batch", "EXPORTS", "HEADER",
 ]
@@ -30,8 +30,8 @@ EXPORTS = (
     "cw_sketch_csr_rows", "cw_sketch_csr_general", "cw_sketch_csr_noalloc", "cw_noalloc_status", "cw_sketch_dense",
     "cw_sketch_vec", "cw_gram", "cw_qr", "cw_solve_sketch", "cw_batch_create", "cw_batch_run", "cw_batch_finish", "cw_batch_info",
     "cw_batch_phases", "cw_batch_destroy", "cw_sketch_csr_values", "cw_sketch_dense_values",
-    "cw_sketch_values_backward_csr", "cw_sketch_values_backward_dense", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_leverage",
-    "cw_launch_count", "cw_profile_enable", "cw_profile_get", "cw_profile_reset",
+    "cw_sketch_values_backward_csr", "cw_sketch_values_backward_dense", "cw_solve_sketch_dense", "cw_lsqr_precond",
+    "cw_lsqr_precond_host", "cw_leverage", "cw_launch_count", "cw_profile_enable", "cw_profile_get", "cw_profile_reset",
 )
 
 
@@ -87,6 +87,8 @@ _SIGS = {
     "cw_solve_sketch_dense": ([_p, _i64, _i64, _i64, _p, _i64, _u64, _p, _p, _p], ctypes.c_int),
     "cw_lsqr_precond": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _f64, _i32, _p,
                          ctypes.POINTER(_i32), ctypes.POINTER(_f64), _p], ctypes.c_int),
+    "cw_lsqr_precond_host": ([ctypes.POINTER(_CSR), _p, _i64, _u64, _f64, _i32, _p,
+                              ctypes.POINTER(_i32), ctypes.POINTER(_f64), _p], ctypes.c_int),
     "cw_leverage": ([_p, _i64, _i64, _i64, _i64, _u64, _i32, _p, _p, _p], ctypes.c_int),
     "cw_gram": ([_p, _i64, _i64, _p, _p, _p], ctypes.c_int),
     "cw_launch_count": ([], ctypes.c_longlong),
@@ -464,6 +466,37 @@ def cw_lsqr_precond(A, b, m, seed, rtol=1e-6, max_iter=100, allow_noconv=False):
                                 _ptr(x, torch.float64, "x"), ctypes.byref(it), ctypes.byref(ft), _stream())
     if not (allow_noconv and st == -6):
         _check(st, "cw_lsqr_precond")
+    return x, it.value, ft.value
+
+
+def _host_ptr(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("%s must be a host (CPU) torch.Tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def cw_lsqr_precond_host(A, b, m, seed, rtol=1e-6, max_iter=100, allow_noconv=False, x=None):
+    """cw_lsqr_precond for A (CSR) and b in host memory (page-locked tensors copy
+    asynchronously); returns (x float64 d on the host, iterations, final test)."""
+    c = _CSR()
+    c.n, c.d = int(A.n), int(A.d)
+    c.nnz = int(A.col.numel())
+    c.row_ptr = _host_ptr(A.row_ptr, torch.int32, "row_ptr")
+    c.col = _host_ptr(A.col, torch.int32, "col") if c.nnz else None
+    c.val = _host_ptr(A.val, torch.float32, "val") if c.nnz else None
+    if x is None:
+        x = torch.empty(A.d, dtype=torch.float64)
+    it = ctypes.c_int32(0)
+    ft = ctypes.c_double(0.0)
+    st = load().cw_lsqr_precond_host(ctypes.byref(c), _host_ptr(b, torch.float32, "b"), m, seed, float(rtol),
+                                     int(max_iter), _host_ptr(x, torch.float64, "x"), ctypes.byref(it),
+                                     ctypes.byref(ft), _stream())
+    if not (allow_noconv and st == -6):
+        _check(st, "cw_lsqr_precond_host")
     return x, it.value, ft.value
 
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "cw.h"
+
 namespace cw {
 
 enum SketchModeId { kSketchCSR = 0, kSketchDense = 1, kSketchVec = 2 };
@@ -28,12 +30,20 @@ struct SketchLayout {
 
 // SA / Sb of a CSR, dense or vector input (see sketch.cu).  With `ext`, all
 // scratch is carved from ext->base (CW_ERR_SHAPE when it does not fit).
+// accumulate (CSR only, without lay or vals): add this call's S A and S b to
+// SA and Sb instead of overwriting them (row shards of one matrix, i0 their
+// first global row, summed in call order).
 int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const int32_t* row_ptr,
                 const int32_t* col, const float* val, const float* A, const float* b, int64_t m,
                 uint64_t seed, float* SA, float* Sb, int32_t* bucket_ptr_out, cudaStream_t stream,
                 double* SA64 = nullptr, const SketchWorkspace* ext = nullptr, const SketchLayout* lay = nullptr,
-                const float* vals = nullptr);
+                const float* vals = nullptr, bool accumulate = false);
 int validate_common(int64_t n, int64_t d, int64_t m);
+
+// The preconditioned LSQR of cw_lsqr_precond (lsqr.cu); SA_in / Sb_in (device,
+// the sketch of A and b with `seed`) skip its sketch step when both are given.
+int lsqr_run(const cw_csr* A, const float* b, int64_t m, uint64_t seed, double rtol, int32_t max_iter, double* x,
+             int32_t* iters, double* final_test, cudaStream_t stream, const float* SA_in, const float* Sb_in);
 
 // float64 Householder QR of [SA | Sb]; synchronises.  SA64 (row-major float64)
 // replaces SA when given.

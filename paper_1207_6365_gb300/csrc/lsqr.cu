@@ -337,10 +337,12 @@ __global__ void __launch_bounds__(256) k_lsqr_start(const double* __restrict__ M
 
 }  // namespace cw
 
-using namespace cw;
+namespace cw {
 
-extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint64_t seed, double rtol,
-                               int32_t max_iter, double* x, int32_t* iters, double* final_test, cw_stream stream) {
+// The preconditioned LSQR of cw_lsqr_precond; with SA_in / Sb_in given (device,
+// the sketch of A and b with `seed`, already formed), the sketch step is skipped.
+int lsqr_run(const cw_csr* A, const float* b, int64_t m, uint64_t seed, double rtol, int32_t max_iter, double* x,
+             int32_t* iters, double* final_test, cudaStream_t stream, const float* SA_in, const float* Sb_in) {
     if (!A || !b || !x) return CW_ERR_ARG;
     if (!(rtol > 0.0) || max_iter < 0) return CW_ERR_ARG;
     int st = validate_common(A->n, A->d, m);
@@ -370,8 +372,9 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     if (pass_smem > 227 * 1024) return CW_ERR_SHAPE;
 
     Scratch ws(stream);
-    const size_t oSA = ws.reserve(sizeof(float) * (size_t)m * d);
-    const size_t oSb = ws.reserve(sizeof(float) * (size_t)m);
+    const bool given = SA_in && Sb_in;
+    const size_t oSA = given ? 0 : ws.reserve(sizeof(float) * (size_t)m * d);
+    const size_t oSb = given ? 0 : ws.reserve(sizeof(float) * (size_t)m);
     const size_t oR = ws.reserve(sizeof(double) * (size_t)d * d);
     const size_t oM = ws.reserve(sizeof(double) * (size_t)d * d);
     const size_t oM32 = ws.reserve(sizeof(float) * (size_t)d * d);
@@ -393,8 +396,8 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     const size_t otv = ws.reserve(sizeof(double) * (size_t)d);
     const size_t osh = ws.reserve(sizeof(double) * 2 * (size_t)(nsm > 0 ? nsm : 1));
     CW_CUDA_TRY(ws.alloc());
-    float* SA = ws.at<float>(oSA);
-    float* Sb = ws.at<float>(oSb);
+    float* SA = given ? const_cast<float*>(SA_in) : ws.at<float>(oSA);
+    float* Sb = given ? const_cast<float*>(Sb_in) : ws.at<float>(oSb);
     double* R = ws.at<double>(oR);
     double* M = ws.at<double>(oM);
     float* M32T = ws.at<float>(oM32);
@@ -405,9 +408,11 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     float* z = ws.at<float>(oz);
     LsqrState* state = ws.at<LsqrState>(ost);
 
-    st = sketch_impl(kSketchCSR, n, d, 0, 0, A->row_ptr, A->col, A->val, nullptr, b, m, seed, SA, Sb, nullptr,
-                     stream);
-    if (st != CW_OK) return st;
+    if (!given) {
+        st = sketch_impl(kSketchCSR, n, d, 0, 0, A->row_ptr, A->col, A->val, nullptr, b, m, seed, SA, Sb, nullptr,
+                         stream);
+        if (st != CW_OK) return st;
+    }
     // preconditioner M = R^-1: R from the Cholesky factor of the Gram matrix of
     // SA (one shared-memory kernel), or from the float64 Householder QR of SA
     // when the Cholesky route is not safe (large diagonal ratio, a failed
@@ -544,4 +549,13 @@ extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint6
     if (iters) *iters = hs.iters;
     if (final_test) *final_test = hs.test2;
     return hs.converged ? CW_OK : CW_ERR_NOCONV;
+}
+
+}  // namespace cw
+
+using namespace cw;
+
+extern "C" int cw_lsqr_precond(const cw_csr* A, const float* b, int64_t m, uint64_t seed, double rtol,
+                               int32_t max_iter, double* x, int32_t* iters, double* final_test, cw_stream stream) {
+    return lsqr_run(A, b, m, seed, rtol, max_iter, x, iters, final_test, (cudaStream_t)stream, nullptr, nullptr);
 }

@@ -289,13 +289,15 @@ __global__ void k_set_last(int32_t* bucket_ptr, int64_t m, int32_t n) { bucket_p
 int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const int32_t* row_ptr,
                 const int32_t* col, const float* val, const float* A, const float* b, int64_t m,
                 uint64_t seed, float* SA, float* Sb, int32_t* bucket_ptr_out, cudaStream_t stream,
-                double* SA64, const SketchWorkspace* ext, const SketchLayout* lay, const float* vals) {
+                double* SA64, const SketchWorkspace* ext, const SketchLayout* lay, const float* vals,
+                bool accumulate) {
     // with vals, the CSR pass forms SA only (its rb carries v_i); Sb comes
     // from a separate vector pass of the caller
     const bool has_b = b != nullptr && (mode == kModeVec || Sb != nullptr) && !(vals && mode == kModeCSR);
     if (lay && mode != kModeCSR) return CW_ERR_ARG;
     if (vals && (lay || SA64)) return CW_ERR_ARG;
-    if (n == 0 && lay) return CW_OK;   // the caller zeroed the whole output
+    if (accumulate && (mode != kModeCSR || lay || vals || bucket_ptr_out)) return CW_ERR_ARG;
+    if (n == 0 && (lay || accumulate)) return CW_OK;   // the caller zeroed the whole output / nothing to add
     if (n == 0) {
         if (SA && d > 0) CW_CUDA_TRY(cudaMemsetAsync(SA, 0, sizeof(float) * (size_t)m * (size_t)d, stream));
         if (SA64 && d > 0) CW_CUDA_TRY(cudaMemsetAsync(SA64, 0, sizeof(double) * (size_t)m * (size_t)d, stream));
@@ -411,7 +413,7 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
         const bool vec4 = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(SA) & 15) == 0);
         CsrApplyArgs a{r2, rb, bptr, col, val, SA, Sb, counter, status, m, (int)d, p.dpad, p.acc_global,
                        vec4 ? 1 : 0, lay ? lay->v : 0, lay ? lay->stride : 0, lay ? lay->off : 0,
-                       lay ? lay->scale : 1.f};
+                       lay ? lay->scale : 1.f, accumulate ? 1 : 0};
 #define CW_K4C(LPR, HB)                                                   \
     do {                                                                  \
         auto kf = k_apply_csr<LPR, 8, HB>;                                \

@@ -397,6 +397,7 @@ struct CsrApplyArgs {
     // (map_v == 0: row u), values times `scale`
     int64_t map_v, map_stride, map_off;
     float scale;
+    int accumulate;          // add the bucket sums to SA and Sb instead of overwriting them
 };
 
 // Persistent warps take whole buckets from a counter; sub-warp `sub` of
@@ -418,7 +419,8 @@ __device__ __forceinline__ void apply_csr_bucket(const CsrApplyArgs& a, unsigned
         float* SArow = a.SA + (size_t)orow * a.d;
         float* myacc;
         if (a.acc_global) {
-            for (int c = lane; c < a.d; c += 32) SArow[c] = 0.f;
+            if (!a.accumulate)
+                for (int c = lane; c < a.d; c += 32) SArow[c] = 0.f;
             myacc = SArow;
         } else {
             for (int c = lane; c < COPIES * a.dpad; c += 32) accw[c] = 0.f;
@@ -500,6 +502,10 @@ __device__ __forceinline__ void apply_csr_bucket(const CsrApplyArgs& a, unsigned
                         v.x += o[0]; v.y += o[1]; v.z += o[2]; v.w += o[3];
                     }
                     if (a.scale != 1.f) v = make_float4(v.x * a.scale, v.y * a.scale, v.z * a.scale, v.w * a.scale);
+                    if (a.accumulate) {
+                        const float4 o = *reinterpret_cast<const float4*>(SArow + c);
+                        v = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+                    }
                     *reinterpret_cast<float4*>(SArow + c) = v;
                 }
             } else {
@@ -507,14 +513,14 @@ __device__ __forceinline__ void apply_csr_bucket(const CsrApplyArgs& a, unsigned
                     float v = accw[c];
 #pragma unroll
                     for (int cp = 1; cp < COPIES; ++cp) v += accw[cp * a.dpad + c];
-                    SArow[c] = v * a.scale;
+                    SArow[c] = a.accumulate ? SArow[c] + v * a.scale : v * a.scale;
                 }
             }
         } else if (a.scale != 1.f) {
             __syncwarp();
             for (int c = lane; c < a.d; c += 32) SArow[c] *= a.scale;
         }
-        if (HAS_B && a.Sb && lane == 0) a.Sb[orow] = sbacc * a.scale;
+        if (HAS_B && a.Sb && lane == 0) a.Sb[orow] = a.accumulate ? a.Sb[orow] + sbacc * a.scale : sbacc * a.scale;
         __syncwarp();
     }
 }

@@ -50,6 +50,16 @@ def test_host_side_validation_rejects_bad_arguments():
     assert lib.cw_hash(1, 10, -1, 10, null, null, null) == -3
     assert lib.cw_hash(1, 10, 2**62, 10, null, null, null) == -3
     assert lib.cw_sketch_csr(null, null, 10, 1, null, null, null) == -1
+    # the host-memory LSQR checks row_ptr's ends before touching the device
+    rp = (ctypes.c_int32 * 3)(0, 2, 3)
+    hc = cw._CSR()
+    hc.n, hc.d, hc.nnz = 2, 2, 4
+    hc.row_ptr = ctypes.cast(rp, ctypes.c_void_p)
+    hc.col = ctypes.c_void_p(16)
+    hc.val = ctypes.c_void_p(16)
+    xh = (ctypes.c_double * 2)()
+    assert lib.cw_lsqr_precond_host(ctypes.byref(hc), ctypes.c_void_p(16), 8, 1, 1e-6, 10, xh, None, None,
+                                    null) == -1
     # the barrier self-test checks its arguments before touching the device
     assert lib.cw_selftest_barrier_timeout(0, 100, null) == -1
     assert lib.cw_selftest_barrier_timeout(2, 0, null) == -1
