@@ -63,7 +63,9 @@ __device__ __forceinline__ float4 ld_stream_f4(const float* p) {
 // eight rows per step; all four steps' 16-byte loads are issued before the
 // first is used.  Row slot q of a step accumulates into copy q, so no two
 // lanes ever update the same address in one instruction and every address is
-// updated in program order: the sums are the same in every run.
+// updated in program order: the sums are the same in every run.  A row's
+// columns must be distinct (as for the sketch kernels; cw_csr_check tests it):
+// a lane reads its four accumulators before writing them.
 // Other batches: a half-warp per row (16 lanes, longer rows loop), four rows
 // at a time, two accumulator copies.
 template <int kW>
@@ -163,10 +165,13 @@ __global__ void __launch_bounds__(kW * 32, 1) k_lsqr_pass(PassArgs a) {
                 const float zt = __shfl_sync(0xFFFFFFFFu, z, (lane & 7) * 4);
                 if ((lane >> 3) == step) zreg = zt;
                 if (act) {
-                    qacc[c.x] = fmaf(v.x, z, qacc[c.x]);
-                    qacc[c.y] = fmaf(v.y, z, qacc[c.y]);
-                    qacc[c.z] = fmaf(v.z, z, qacc[c.z]);
-                    qacc[c.w] = fmaf(v.w, z, qacc[c.w]);
+                    // a row's columns are distinct (a requirement on the input), so
+                    // the four loads can all go out before the four stores
+                    const float a0 = qacc[c.x], a1 = qacc[c.y], a2 = qacc[c.z], a3 = qacc[c.w];
+                    qacc[c.x] = fmaf(v.x, z, a0);
+                    qacc[c.y] = fmaf(v.y, z, a1);
+                    qacc[c.z] = fmaf(v.z, z, a2);
+                    qacc[c.w] = fmaf(v.w, z, a3);
                 }
                 __syncwarp();
             }
