@@ -642,43 +642,67 @@ def batch_timings(cw, stream, count=512):
     return out
 
 
-def learned_rows(cw, n_train=64, n_test=16, epochs=20, n=1 << 20, d=128, m=2048):
-    """The learned-sketch workload: a family A = U diag(j^-1.5) V_fam^T + 1e-3 N(0,1)
-    (n = 2^20, d = 128, V_fam fixed by seed 7, U Haar per matrix), b = A x0 + 0.05
-    noise; m = 2048 = 1024 learned rows (values at fixed hash positions) + 1024
-    random CountSketch rows; Adam lr 1e-3 on rho^2 - 1 through the backward kernel.
-    Fewer matrices than the 2000 / 200 of the recipe (all kept in HBM); the test
-    residual ratios of the plain CountSketch (m = 2048) and of the learned + random
-    sketch (the float64 oracle re-judges the trained sketch in the GPU tests)."""
+def learned_rows(cw, n_train=2000, n_report=200, n_select=100, epochs=20, n=1 << 20, d=128, m=2048):
+    """The learned-sketch workload at the recipe's counts: a family
+    A = U diag(j^-1.5) V_fam^T + 1e-3 N(0,1) (n = 2^20, d = 128, V_fam fixed by
+    seed 7, U Haar per matrix), b = A x0 + 0.05 noise; 2000 training matrices,
+    100 selection matrices and 200 report matrices, each its own seed.
+    m = 2048 = 1024 learned rows (values tied per bucket, w_k, at the fixed hash
+    positions of seed 11) + 1024 random CountSketch rows (seed 12); Adam lr 1e-3,
+    20 epochs, one matrix per step, on rho^2 - 1 through the library's
+    backward (trained through the Cholesky factor of the sketched Gram matrix;
+    every reported ratio comes from the Householder QR solve).  Each matrix is
+    generated once and kept as its sufficient statistics (the two sketches and
+    the Gram matrix of [A b]), all the loss needs.  select_or_fallback decides
+    on the selection set; the report set gives the ratios."""
+    import math
     import time
     import torch
     import workloads as W
     from paper_1207_6365_gb300 import learned as L
     t0 = time.time()
     V, sig = W.family_basis(d, seed=7, device="cuda")
-    sk = L.LearnedSketch(n, m, seed_L=11, seed_R=12)
+    sk = L.TiedSketch(m, seed_L=11, seed_R=12, method="normal")
 
     def member(k):
         A, b = W.family_matrix(k, n, V, sig, device="cuda")
-        return A, b, L.MatrixStats(A, b), sk.random_half(A, b)
+        return sk.member(A, b, m, seed_P=13)
     train_set = [member(k) for k in range(n_train)]
-    test_set = [member(100000 + k) for k in range(n_test)]
+    select_set = [member(200000 + k) for k in range(n_select)]
+    report_set = [member(100000 + k) for k in range(n_report)]
     torch.cuda.synchronize()
     t_gen = time.time() - t0
-    p0, l0 = L.evaluate(sk, test_set, m, seed_P=13)
-    torch.cuda.synchronize()
+    _, l0 = L.evaluate(sk, report_set)
     t1 = time.time()
     hist = L.train(sk, train_set, epochs, lr=1e-3)
     torch.cuda.synchronize()
     t_train = time.time() - t1
-    p1, l1 = L.evaluate(sk, test_set, m, seed_P=13)
-    out = {"N3_workload": "family n=2^20 x d=128, %d train / %d test matrices (recipe: 2000 / 200), m=2048 = "
-                          "1024 learned + 1024 random rows, Adam lr 1e-3, %d epochs" % (n_train, n_test, epochs),
-           "N3_test_ratio_plain_countsketch": p1, "N3_test_ratio_learned_random_init": l0,
-           "N3_test_ratio_learned_random_trained": l1, "N3_selected": "learned" if l1 < p1 else "plain",
+    sel = L.select_or_fallback(sk, select_set, m, seed_P=13)
+    p1, l1 = L.evaluate(sk, report_set)
+    diff = [a - b for a, b in zip(l1, p1)]
+    mean = sum(diff) / len(diff)
+    se = math.sqrt(sum((x - mean) ** 2 for x in diff) / (len(diff) - 1) / len(diff))
+    # what the values learned: their spread, and their correlation with
+    # 1/sqrt(bucket load) of the learned half (the weights that give every
+    # sketched row the same variance)
+    w = sk.w.detach().double()
+    bucket, _ = cw.cw_hash(11, m // 2, 0, n)
+    load = torch.bincount(bucket.long(), minlength=m // 2).double()
+    corr = float(torch.corrcoef(torch.stack([w, load.rsqrt()]))[0, 1])
+    out = {"N3_workload": "family n=2^20 x d=128, %d train / %d selection / %d report matrices (recipe: 2000 train / "
+                          "200 test), m=2048 = 1024 learned rows (values tied per bucket) + 1024 random rows, Adam lr "
+                          "1e-3, %d epochs, one matrix per step" % (n_train, n_select, n_report, epochs),
+           "N3_test_ratio_plain_countsketch": sum(p1) / len(p1),
+           "N3_test_ratio_learned_random_init": sum(l0) / len(l0),
+           "N3_test_ratio_learned_random_trained": sum(l1) / len(l1),
+           "N3_trained_minus_plain_mean_and_se": [mean, se],
+           "N3_gaussian_sketch_ratio": L.gaussian_sketch_ratio(m, d),
+           "N3_selection_means_plain_learned": [sel.mean_plain, sel.mean_learned],
+           "N3_selected": sel.name,
            "N3_train_loss_first_last_epoch": [hist[0], hist[-1]],
+           "N3_w_mean_std_corr_with_rsqrt_load": [float(w.mean()), float(w.std()), corr],
            "N3_train_ms_per_step": t_train * 1000.0 / (epochs * n_train), "N3_generate_s": t_gen}
-    del train_set, test_set
+    del train_set, select_set, report_set
     torch.cuda.empty_cache()
     return out
 

@@ -374,6 +374,73 @@ int cw_solve_sketch_dense(const float *A, int64_t n, int64_t d, int64_t lda, con
                           int64_t m, uint64_t seed, double *x, double *R, cw_stream stream);
 
 /*
+ * Training a sketch (not operations of the paper: the derivatives of its
+ * sketch-and-solve, and the loss that judges it).
+ *
+ * cw_solve_sketched - x' = argmin ||SA x - Sb|| for an already sketched system
+ * (Theorem "lin reg"), as R^-1 Q^T Sb from the float64 Householder QR of SA
+ * (proof of Theorem "renRegAlg").  SA: m x d float32 row-major, Sb: m float32
+ * (device).  x: d float64 (device); R: d x d float64 row-major (device) or
+ * NULL.  Requires 1 <= d <= m, d <= 1024.  CW_ERR_RANK for a numerically
+ * rank-deficient SA (x not written).  Synchronises.
+ */
+int cw_solve_sketched(const float *SA, const float *Sb, int64_t m, int64_t d, double *x, double *R,
+                      cw_stream stream);
+
+/*
+ * cw_solve_sketched_backward - the gradients of a loss L(x') with respect to
+ * the sketched system of cw_solve_sketched, given gx = dL/dx' (d float64,
+ * device) and that call's R and x:
+ *   z = R^-1 R^-T gx,  r = Sb - SA x,  gSA = r z^T - (SA z) x^T,  gSb = SA z
+ * (differentiating SA^T SA x = SA^T Sb).  R may equally be cw_normal_solve's
+ * factor of the same system.  gSA (m x d) and gSb (m) float32 (device), fully
+ * overwritten; the row sums are float64.  Same limits as cw_solve_sketched.
+ * Asynchronous.
+ */
+int cw_solve_sketched_backward(const float *SA, const float *Sb, int64_t m, int64_t d, const double *R,
+                               const double *x, const double *gx, float *gSA, float *gSb, cw_stream stream);
+
+/*
+ * cw_normal_solve - the least-squares solution from the bordered Gram matrix
+ * G = [A b]^T [A b] ((d+1) x (d+1) float64 row-major, device; what cw_gram
+ * writes for A and b): the upper Cholesky factor of G is [[R, c], [0, rho]]
+ * with x* = R^-1 c and rho^2 = ||A x* - b||^2.  x: d float64, r2: one
+ * float64 (device); R: d x d float64 row-major, upper (R^T R = A^T A,
+ * positive diagonal: the R of A's QR), or NULL.  Given cw_gram of a sketched
+ * system it is the normal-equations counterpart of cw_solve_sketched.
+ * CW_ERR_RANK when a pivot of A's block is not above 1e-14 of its diagonal
+ * entry (outputs not written).  Requires 1 <= d <= 1024.  Synchronises.
+ */
+int cw_normal_solve(const double *G, int64_t d, double *x, double *r2, double *R, cw_stream stream);
+
+/*
+ * cw_excess_residual - rho^2 - 1 for rho = ||A x - b|| / ||A x* - b||:
+ * loss = (x - x*)^T G_AA (x - x*) / r2 (the residual of x* is orthogonal to
+ * the range of A), and gx = dloss/dx = 2 G_AA (x - x*) / r2.  G as for
+ * cw_normal_solve (its leading d x d block is used), xstar and r2 from that
+ * call, x: d float64.  loss: one float64; gx: d float64 or NULL (device).
+ * Requires 1 <= d <= 1024.  Asynchronous.
+ */
+int cw_excess_residual(const double *G, int64_t d, const double *xstar, const double *r2, const double *x,
+                       double *loss, double *gx, cw_stream stream);
+
+/*
+ * cw_scale_rows - values tied per bucket: a sketch whose value at column i is
+ * w_{h(i)} sigma(i) equals diag(w) S, so its sketch is the plain one with
+ * row k scaled by w_k.  M[k, :] = w_k P[k, :] and y[k] = w_k Pb[k] for
+ * k < ms, copied unchanged for ms <= k < m (a stacked [tied; random] sketch).
+ * P, M: m x d float32 row-major; Pb, y: m float32 or both NULL; w: ms float32
+ * (device).  Requires 0 <= ms <= m.  Asynchronous.
+ * cw_scale_rows_backward - gw_k = <gM[k, :], P[k, :]> + gy[k] Pb[k] for
+ * k < ms (float64 sums); gw: ms float32 (device), fully overwritten; Pb and
+ * gy both given or both NULL.  Asynchronous.
+ */
+int cw_scale_rows(const float *P, const float *Pb, int64_t m, int64_t d, int64_t ms, const float *w, float *M,
+                  float *y, cw_stream stream);
+int cw_scale_rows_backward(const float *P, const float *Pb, int64_t ms, int64_t d, const float *gM,
+                           const float *gy, float *gw, cw_stream stream);
+
+/*
  * cw_lsqr_precond - least squares by LSQR on y -> A R^-1 y with R the
  * triangular factor of SA (R^T R = SA^T SA, the R of its QR; Section 7.6,
  * Theorem "it reg"), started at the sketch-and-solve solution, returning

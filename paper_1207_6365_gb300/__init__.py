@@ -22,6 +22,8 @@ __all__ = [
     "cw_gram", "cw_qr", "cw_solve_sketch", "cw_solve_sketch_dense", "cw_lsqr_precond", "cw_lsqr_precond_host", "cw_leverage",
     "cw_sketch_csr_values", "cw_sketch_dense_values", "cw_sketch_values_backward_csr",
     "cw_sketch_values_backward_dense", "SketchValues", "Batch", "EXPORTS", "HEADER",
+    "cw_solve_sketched", "cw_solve_sketched_backward", "cw_normal_solve", "cw_excess_residual", "cw_scale_rows",
+    "cw_scale_rows_backward", "SketchedSolve", "ScaleRows",
 ]
 
 HEADER = os.path.join(_build.ROOT, "include", "cw.h")
@@ -32,6 +34,8 @@ EXPORTS = (
     "cw_batch_phases", "cw_batch_destroy", "cw_sketch_csr_values", "cw_sketch_dense_values",
     "cw_sketch_values_backward_csr", "cw_sketch_values_backward_dense", "cw_solve_sketch_dense", "cw_lsqr_precond",
     "cw_lsqr_precond_host", "cw_leverage", "cw_launch_count", "cw_profile_enable", "cw_profile_get", "cw_profile_reset",
+    "cw_solve_sketched", "cw_solve_sketched_backward", "cw_normal_solve", "cw_excess_residual", "cw_scale_rows",
+    "cw_scale_rows_backward",
 )
 
 
@@ -91,6 +95,12 @@ _SIGS = {
                               ctypes.POINTER(_i32), ctypes.POINTER(_f64), _p], ctypes.c_int),
     "cw_leverage": ([_p, _i64, _i64, _i64, _i64, _u64, _i32, _p, _p, _p], ctypes.c_int),
     "cw_gram": ([_p, _i64, _i64, _p, _p, _p], ctypes.c_int),
+    "cw_solve_sketched": ([_p, _p, _i64, _i64, _p, _p, _p], ctypes.c_int),
+    "cw_solve_sketched_backward": ([_p, _p, _i64, _i64, _p, _p, _p, _p, _p, _p], ctypes.c_int),
+    "cw_normal_solve": ([_p, _i64, _p, _p, _p, _p], ctypes.c_int),
+    "cw_excess_residual": ([_p, _i64, _p, _p, _p, _p, _p, _p], ctypes.c_int),
+    "cw_scale_rows": ([_p, _p, _i64, _i64, _i64, _p, _p, _p, _p], ctypes.c_int),
+    "cw_scale_rows_backward": ([_p, _p, _i64, _i64, _p, _p, _p, _p], ctypes.c_int),
     "cw_launch_count": ([], ctypes.c_longlong),
     "cw_profile_enable": ([ctypes.c_int], ctypes.c_int),
     "cw_profile_get": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_f64)], ctypes.c_int),
@@ -366,6 +376,125 @@ class SketchValues(torch.autograd.Function):
         fn = cw_sketch_values_backward_dense if ctx.dense else cw_sketch_values_backward_csr
         gv = fn(ctx.A, ctx.b, ctx.m, ctx.seed, gSA.float(), None if gSb is None else gSb.float())
         return gv, None, None, None, None
+
+
+def cw_solve_sketched(SA, Sb):
+    """(x' float64 d, R float64 d x d): argmin ||SA x - Sb|| by the float64 Householder QR of SA."""
+    m, d = SA.shape
+    x = torch.empty(d, dtype=torch.float64, device=SA.device)
+    R = torch.empty(d, d, dtype=torch.float64, device=SA.device)
+    _check(load().cw_solve_sketched(_ptr(SA, torch.float32, "SA"), _ptr(Sb, torch.float32, "Sb"), m, d,
+                                    _ptr(x, torch.float64, "x"), _ptr(R, torch.float64, "R"), _stream()),
+           "cw_solve_sketched")
+    return x, R
+
+
+def cw_solve_sketched_backward(SA, Sb, R, x, gx):
+    """(gSA, gSb) float32: the gradients of L(x') given gx = dL/dx' (float64)."""
+    m, d = SA.shape
+    gSA = torch.empty(m, d, dtype=torch.float32, device=SA.device)
+    gSb = torch.empty(m, dtype=torch.float32, device=SA.device)
+    _check(load().cw_solve_sketched_backward(_ptr(SA, torch.float32, "SA"), _ptr(Sb, torch.float32, "Sb"), m, d,
+                                             _ptr(R, torch.float64, "R"), _ptr(x, torch.float64, "x"),
+                                             _ptr(gx, torch.float64, "gx"), _ptr(gSA, torch.float32, "gSA"),
+                                             _ptr(gSb, torch.float32, "gSb"), _stream()),
+           "cw_solve_sketched_backward")
+    return gSA, gSb
+
+
+def cw_normal_solve(G, want_R=False):
+    """(x* float64 d, r2 float64 0-dim[, R float64 d x d]) from the bordered
+    Gram [A b]^T [A b] ((d+1) x (d+1))."""
+    d = G.shape[0] - 1
+    x = torch.empty(d, dtype=torch.float64, device=G.device)
+    r2 = torch.empty((), dtype=torch.float64, device=G.device)
+    R = torch.empty(d, d, dtype=torch.float64, device=G.device) if want_R else None
+    _check(load().cw_normal_solve(_ptr(G, torch.float64, "G"), d, _ptr(x, torch.float64, "x"),
+                                  _ptr(r2, torch.float64, "r2"), _ptr(R, torch.float64, "R"), _stream()),
+           "cw_normal_solve")
+    return (x, r2, R) if want_R else (x, r2)
+
+
+def cw_excess_residual(G, xstar, r2, x, want_grad=True):
+    """(rho^2 - 1 float64 0-dim, its gradient in x float64 d or None)."""
+    d = G.shape[0] - 1
+    loss = torch.empty((), dtype=torch.float64, device=G.device)
+    gx = torch.empty(d, dtype=torch.float64, device=G.device) if want_grad else None
+    _check(load().cw_excess_residual(_ptr(G, torch.float64, "G"), d, _ptr(xstar, torch.float64, "xstar"),
+                                     _ptr(r2, torch.float64, "r2"), _ptr(x, torch.float64, "x"),
+                                     _ptr(loss, torch.float64, "loss"), _ptr(gx, torch.float64, "gx"), _stream()),
+           "cw_excess_residual")
+    return loss, gx
+
+
+def cw_scale_rows(P, Pb, ms, w, M=None, y=None):
+    """(M, y): the first ms rows of P (and Pb) scaled by w, the rest copied."""
+    m, d = P.shape
+    M = torch.empty_like(P) if M is None else M
+    if Pb is not None and y is None:
+        y = torch.empty_like(Pb)
+    _check(load().cw_scale_rows(_ptr(P, torch.float32, "P"), _ptr(Pb, torch.float32, "Pb"), m, d, ms,
+                                _ptr(w, torch.float32, "w"), _ptr(M, torch.float32, "M"),
+                                _ptr(y, torch.float32, "y"), _stream()), "cw_scale_rows")
+    return M, y
+
+
+def cw_scale_rows_backward(P, Pb, ms, gM, gy):
+    """gw (ms float32): gw_k = <gM_k, P_k> + gy_k Pb_k."""
+    d = P.shape[1]
+    gw = torch.empty(ms, dtype=torch.float32, device=P.device)
+    _check(load().cw_scale_rows_backward(_ptr(P, torch.float32, "P"), _ptr(Pb, torch.float32, "Pb"), ms, d,
+                                         _ptr(gM, torch.float32, "gM"), _ptr(gy, torch.float32, "gy"),
+                                         _ptr(gw, torch.float32, "gw"), _stream()), "cw_scale_rows_backward")
+    return gw
+
+
+class SketchedSolve(torch.autograd.Function):
+    """x' = argmin ||SA x - Sb|| (float64) as a differentiable function of the
+    sketched system: forward cw_solve_sketched (method "qr", the Householder
+    QR) or cw_gram + cw_normal_solve (method "normal", the Cholesky factor of
+    [SA Sb]^T [SA Sb]: the same R and x' up to rounding, without the QR's grid
+    barriers), backward cw_solve_sketched_backward (the hand-derived gradients
+    of the normal equations)."""
+
+    @staticmethod
+    def forward(ctx, SA, Sb, method="qr"):
+        SA, Sb = SA.detach().contiguous(), Sb.detach().contiguous()
+        if method == "qr":
+            x, R = cw_solve_sketched(SA, Sb)
+        elif method == "normal":
+            x, _, R = cw_normal_solve(cw_gram(SA, Sb), want_R=True)
+        else:
+            raise ValueError("method must be 'qr' or 'normal'")
+        ctx.save_for_backward(SA, Sb, R, x)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        SA, Sb, R, x = ctx.saved_tensors
+        gSA, gSb = cw_solve_sketched_backward(SA, Sb, R, x, gx.contiguous().double())
+        return gSA, gSb, None
+
+
+class ScaleRows(torch.autograd.Function):
+    """(M, y) = the first ms rows of (P, Pb) scaled by w (values tied per
+    bucket: diag(w) S A); only w receives a gradient (cw_scale_rows_backward)."""
+
+    @staticmethod
+    def forward(ctx, w, P, Pb, ms):
+        M, y = cw_scale_rows(P, Pb, ms, w.detach().contiguous())
+        ctx.P, ctx.Pb, ctx.ms = P, Pb, ms
+        return M, y
+
+    @staticmethod
+    def backward(ctx, gM, gy):
+        if gM is None:
+            gM = torch.zeros_like(ctx.P)
+        if gy is None and ctx.Pb is not None:
+            gy = torch.zeros_like(ctx.Pb)
+        gw = cw_scale_rows_backward(ctx.P, ctx.Pb, ctx.ms, gM.contiguous().float(),
+                                    None if gy is None else gy.contiguous().float())
+        return gw, None, None, None
 
 
 class Batch:

@@ -63,6 +63,10 @@ int lsqr_run(const cw_csr* A, const float* b, int64_t m, uint64_t seed, double r
 int qr64(const float* SA, int64_t m, int d, const float* Sb, double* R, double* c, cudaStream_t stream,
          const double* SA64 = nullptr);
 int trsv_upper(const double* R, int d, const double* rhs, double* x, cudaStream_t stream);
+// x' = argmin ||SA x - Sb|| by qr64 and trsv_upper; R (nullable) receives the
+// factor.  Synchronises.
+int solve_from_sketch(const float* SA, const float* Sb, int64_t m, int d, double* x, double* R_out,
+                      cudaStream_t stream);
 int trsm_upper(const double* R, int d, const double* B, int k, double* X, cudaStream_t stream);
 int tri_inverse(const double* R, int d, double* M, cudaStream_t stream);
 // [SA | Sb]^T [SA | Sb] (float64, symmetric, nc = d + (Sb != NULL)) on the

@@ -6,7 +6,7 @@
 
 namespace cw {
 
-static int solve_from_sketch(const float* SA, const float* Sb, int64_t m, int d, double* x, double* R_out,
+int solve_from_sketch(const float* SA, const float* Sb, int64_t m, int d, double* x, double* R_out,
                              cudaStream_t stream) {
     Scratch ws(stream);
     const size_t oR = R_out ? 0 : ws.reserve(sizeof(double) * (size_t)d * d);

@@ -269,14 +269,21 @@ def family_basis(d=128, seed=7, device="cpu"):
 
 
 def family_matrix(k, n, V, sigma, device="cpu"):
-    """(A float32 (n, d) row-major, b float32 (n,)) of member k of the family."""
+    """(A float32 (n, d) row-major, b float32 (n,)) of member k of the family:
+    A = U diag(sigma) V^T + 1e-3 N(0, 1), b = A x0 + 0.05 N(0, 1).
+
+    U is the Q factor, with R's diagonal made positive, of an n x d Gaussian
+    Z: that Q is Haar-distributed, and it equals Z R^-1 for the Cholesky
+    factor R of Z^T Z (the positive-diagonal QR factor is unique), so A is
+    formed as Z (R^-1 diag(sigma) V^T) by one matrix product."""
     d = V.shape[0]
     g = _gen(1000003 + k, device)
-    q, r = torch.linalg.qr(torch.randn(n, d, dtype=torch.float32, device=device, generator=g))
-    sg = torch.sign(torch.diagonal(r))
-    sg[sg == 0] = 1.0
-    U = q * sg
-    A = (U * sigma.to(device=device, dtype=torch.float32)) @ V.to(device=device, dtype=torch.float32).T
+    Z = torch.randn(n, d, dtype=torch.float32, device=device, generator=g)
+    R = torch.linalg.cholesky((Z.T @ Z).double()).T
+    Rinv = torch.linalg.solve_triangular(R, torch.eye(d, dtype=torch.float64, device=device), upper=True)
+    mix = (Rinv * sigma.to(device=device, dtype=torch.float64)) @ V.to(device=device, dtype=torch.float64).T
+    A = Z @ mix.to(torch.float32)
+    del Z
     A += 1e-3 * torch.randn(n, d, dtype=torch.float32, device=device, generator=g)
     x0 = torch.randn(d, dtype=torch.float64, device=device, generator=g)
     y = (A.double() @ x0) if n * d <= (1 << 24) else torch.cat(
