@@ -33,25 +33,12 @@ struct SketchLayout {
 // accumulate (CSR only, without lay or vals): add this call's S A and S b to
 // SA and Sb instead of overwriting them (row shards of one matrix, i0 their
 // first global row, summed in call order).
-// sort_out: stop after the bucket sort and leave its result in the caller's
-// buffers (records {a | sign << 31, 0} in the dense layout, sigma * b, bucket
-// starts); SA and Sb are then unused.
-struct SortOut {
-    int2* r2;        // n
-    float* rb;       // n (sigma * b), or NULL without b
-    int32_t* bptr;   // m + 1
-};
 int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const int32_t* row_ptr,
                 const int32_t* col, const float* val, const float* A, const float* b, int64_t m,
                 uint64_t seed, float* SA, float* Sb, int32_t* bucket_ptr_out, cudaStream_t stream,
                 double* SA64 = nullptr, const SketchWorkspace* ext = nullptr, const SketchLayout* lay = nullptr,
-                const float* vals = nullptr, bool accumulate = false, const SortOut* sort_out = nullptr);
+                const float* vals = nullptr, bool accumulate = false);
 int validate_common(int64_t n, int64_t d, int64_t m);
-
-// The generalized sparse embedding in one pass over A (general.cu); *done is
-// false when the shapes do not suit it (the caller then makes kappa passes).
-int sketch_csr_general_onepass(const cw_csr* A, const float* b, int64_t q, int64_t v, int32_t kappa, uint64_t seed,
-                               float* SA, float* Sb, cudaStream_t stream, bool* done);
 
 // The preconditioned LSQR of cw_lsqr_precond (lsqr.cu); SA_in / Sb_in (device,
 // the sketch of A and b with `seed`) skip its sketch step when both are given.

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(512) k_fine_sort(const int4* __restrict__ rec,
 }
 
 template <int LPR, int U, bool HAS_B>
-__global__ void __launch_bounds__(256) k_apply_csr(CsrApplyArgs a) {
+__global__ void __launch_bounds__(256, 4) k_apply_csr(CsrApplyArgs a) {
     constexpr int COPIES = 32 / LPR;
     extern __shared__ __align__(16) float smacc[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -290,16 +290,10 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
                 const int32_t* col, const float* val, const float* A, const float* b, int64_t m,
                 uint64_t seed, float* SA, float* Sb, int32_t* bucket_ptr_out, cudaStream_t stream,
                 double* SA64, const SketchWorkspace* ext, const SketchLayout* lay, const float* vals,
-                bool accumulate, const SortOut* sort_out) {
+                bool accumulate) {
     // with vals, the CSR pass forms SA only (its rb carries v_i); Sb comes
     // from a separate vector pass of the caller
-    const bool has_b = b != nullptr && (mode == kModeVec || Sb != nullptr || (sort_out && sort_out->rb)) &&
-                       !(vals && mode == kModeCSR);
-    if (sort_out && (mode != kModeDense || vals || lay || accumulate || bucket_ptr_out)) return CW_ERR_ARG;
-    if (sort_out && n == 0) {
-        CW_CUDA_TRY(cudaMemsetAsync(sort_out->bptr, 0, sizeof(int32_t) * (size_t)(m + 1), stream));
-        return CW_OK;
-    }
+    const bool has_b = b != nullptr && (mode == kModeVec || Sb != nullptr) && !(vals && mode == kModeCSR);
     if (lay && mode != kModeCSR) return CW_ERR_ARG;
     if (vals && (lay || SA64)) return CW_ERR_ARG;
     if (accumulate && (mode != kModeCSR || lay || vals || bucket_ptr_out)) return CW_ERR_ARG;
@@ -323,10 +317,10 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     const size_t oP = ws.reserve(sizeof(uint32_t) * (size_t)p.nchunks * p.nbins);
     const size_t oCP = ws.reserve(sizeof(uint32_t) * (size_t)(p.nbins + 1));
     const size_t oRec = ws.reserve(sizeof(int4) * (size_t)n);
-    const size_t oR2 = (mode != kModeVec && !sort_out) ? ws.reserve(sizeof(int2) * (size_t)n) : 0;
+    const size_t oR2 = (mode != kModeVec) ? ws.reserve(sizeof(int2) * (size_t)n) : 0;
     const bool need_rb = has_b || (vals && mode == kModeCSR);
-    const size_t oRB = (need_rb && !sort_out) ? ws.reserve(sizeof(float) * (size_t)n) : 0;
-    const size_t oBP = (bucket_ptr_out || sort_out) ? 0 : ws.reserve(sizeof(int32_t) * (size_t)(m + 1));
+    const size_t oRB = need_rb ? ws.reserve(sizeof(float) * (size_t)n) : 0;
+    const size_t oBP = bucket_ptr_out ? 0 : ws.reserve(sizeof(int32_t) * (size_t)(m + 1));
     const size_t oCnt = ws.reserve(sizeof(unsigned) * 4);
     if (ext && ws.size() > ext->bytes) return CW_ERR_SHAPE;
     CW_CUDA_TRY(ws.alloc());
@@ -334,9 +328,9 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
     uint32_t* P = ws.at<uint32_t>(oP);
     uint32_t* CP = ws.at<uint32_t>(oCP);
     int4* rec = ws.at<int4>(oRec);
-    int2* r2 = sort_out ? sort_out->r2 : (mode != kModeVec) ? ws.at<int2>(oR2) : nullptr;
-    float* rb = sort_out ? sort_out->rb : need_rb ? ws.at<float>(oRB) : nullptr;
-    int32_t* bptr = sort_out ? sort_out->bptr : bucket_ptr_out ? bucket_ptr_out : ws.at<int32_t>(oBP);
+    int2* r2 = (mode != kModeVec) ? ws.at<int2>(oR2) : nullptr;
+    float* rb = need_rb ? ws.at<float>(oRB) : nullptr;
+    int32_t* bptr = bucket_ptr_out ? bucket_ptr_out : ws.at<int32_t>(oBP);
     unsigned* counter = ws.at<unsigned>(oCnt);
     CW_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned) * 4, stream));
 
@@ -414,7 +408,6 @@ int sketch_impl(int mode, int64_t n, int64_t d, int64_t lda, int64_t i0, const i
         k_set_last<<<1, 1, 0, stream>>>(bptr, m, (int32_t)n);
     }
     CW_LAUNCH_CHECK();
-    if (sort_out) return CW_OK;
 
     if (mode == kModeCSR) {
         const bool vec4 = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(SA) & 15) == 0);
@@ -559,9 +552,6 @@ extern "C" int cw_sketch_csr_general(const cw_csr* A, const float* b, int64_t q,
         if (sb) CW_CUDA_TRY(cudaMemsetAsync(sb, 0, sizeof(float) * (size_t)rows, s));
         return CW_OK;
     }
-    bool done = false;
-    st = sketch_csr_general_onepass(A, b, q, v, kappa, seed, SA, sb, s, &done);
-    if (st != CW_OK || done) return st;
     std::vector<uint64_t> seeds((size_t)kappa);
     splitmix64_after_coeffs(seed, kappa, seeds.data());
     const float scale = (float)(1.0 / std::sqrt((double)kappa));

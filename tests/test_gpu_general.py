@@ -7,11 +7,7 @@ sqrt(kappa)), the float32 tolerance of the sparse-embedding kernels.  Cases
 cover q * v a power of two and not, kappa = 1 and large kappa, ragged and
 empty rows, wide rows (the accumulator in the output row itself), no b, the
 empty matrix, and the special case q = kappa = 1, which must equal the
-Section 2 sketch of the first inner seed bit for bit.  2 <= kappa <= 8 takes
-the one-pass kernel (rows sorted once by the outer hash, a block's v kappa
-output rows in shared memory); kappa = 1, kappa > 8 and output blocks too wide
-for shared memory take one pass of the plain sketch per inner sketch; both
-kinds are covered.
+Section 2 sketch of the first inner seed bit for bit.
 """
 import numpy as np
 import pytest
@@ -84,9 +80,9 @@ def _run(cw, A, b, q, v, kappa, seed):
     (20000, 12, 4, 1, 32, 1, 4),       # one block, one inner sketch
     (9000, 8, 3, 300, 2, 9, 2),        # many blocks of 2 rows, kappa = 9
     (4000, 33, 33, 5, 7, 2, 6),        # rows longer than 32 lanes
-    (120000, 256, 16, 1024, 16, 4, 1), # the bench's parameters (one pass, two warps per inner sketch)
-    (40000, 24, 6, 50, 9, 8, 11),      # kappa = 8: one warp per inner sketch
-    (30000, 40, 5, 8, 512, 4, 12),     # v kappa rows too wide for shared memory: kappa passes
+    (120000, 256, 16, 1024, 16, 4, 1), # the bench's q, v, kappa
+    (40000, 24, 6, 50, 9, 8, 11),      # kappa = 8
+    (30000, 40, 5, 8, 512, 4, 12),     # wide inner sketches (v kappa = 2048 rows a block)
 ])
 def test_general_shapes(cw, n, d, k, q, v, kappa, seed):
     A = W.csr_uniform(n, d, k, seed=seed + 40)
