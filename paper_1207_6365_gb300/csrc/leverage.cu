@@ -137,7 +137,9 @@ __global__ void __launch_bounds__(kLevWarps * 32) k_leverage(const float* __rest
 // and the accumulators are drained into two-word float32 sums of
 //     2^(E_ic + F_cl - 14 - 7g) D_g(i,l)
 // over levels and chunks (the cancellation between levels, which is where the
-// conditioning of A shows, happens in those sums).  Powers of two are formed in
+// conditioning of A shows, happens in those sums).  The digit slices hold
+// d_s 128^-s and e_t 128^-t (still exact in bf16), so the accumulator of level
+// g already carries the factor 128^-g.  Powers of two are formed in
 // float32: rows whose largest entry is below 2^-90 in magnitude, or columns of
 // M outside 2^+-90, would lose accuracy.
 
@@ -146,6 +148,7 @@ constexpr int kTcK = 64;                           // columns of A per chunk
 constexpr int kTcN = 32;                           // MMA N (k <= 32)
 constexpr int kTcDig = 5;                          // digits per operand
 constexpr int kTcLev = 5;                          // levels kept
+static_assert(kTcDig == 5 && kTcLev == 5, "the drain sums levels 2..4 in float32 before the two-word sums");
 constexpr int kTcLBO = 128;                        // bytes between core matrices along K
 constexpr int kTcSBO = (kTcK / 8) * 128;           // bytes between core matrices along M / N
 constexpr int kTcASlice = kTcRows * kTcK * 2;      // 16 KB per A digit slice
@@ -201,7 +204,9 @@ __global__ void k_m_digits(const double* __restrict__ M, int d, int k, int nchun
         for (int t = 0; t < kTcDig; ++t) {
             const double dg = rint(x);
             x = (x - dg) * 128.0;
-            *reinterpret_cast<__nv_bfloat16*>(base + t * kTcBSlice + tc_off(l, kk)) = __float2bfloat16((float)dg);
+            // digit t is stored as e_t 128^-t (exact in bf16: at most 8 significant bits)
+            *reinterpret_cast<__nv_bfloat16*>(base + t * kTcBSlice + tc_off(l, kk)) =
+                __float2bfloat16((float)ldexp(dg, -7 * t));
         }
     }
 }
@@ -343,14 +348,17 @@ __global__ void __launch_bounds__(kTcThreads) k_leverage_tc(TcLevArgs a) {
                     float x[8] = {x0.x * sc, x0.y * sc, x0.z * sc, x0.w * sc, x1.x * sc, x1.y * sc, x1.z * sc, x1.w * sc};
 #pragma unroll
                     for (int sd = 0; sd < kTcDig; ++sd) {
-                        // digit = x rounded to the nearest integer by adding and subtracting
-                        // 1.5 * 2^23 (|x| < 2^22; float32 adds round to nearest even); a digit
-                        // (|d| <= 128) is a bf16 exactly: the upper half of its float32 bits
+                        // digit sd, kept at its weight: d_sd 128^-sd = x rounded to a multiple
+                        // of 128^-sd by adding and subtracting 1.5 * 2^(23 - 7 sd) (|x| is
+                        // at most 2^(6 - 7 sd) by now; float32 adds round to nearest even),
+                        // and x keeps the exact remainder.  |d_sd| <= 128, so the digit is a
+                        // bf16 exactly: the upper half of its float32 bits.
+                        const float mg = __uint_as_float((uint32_t)(150 - 7 * sd) << 23) * 1.5f;
                         uint32_t db[8];
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
-                            const float dg = __fsub_rn(__fadd_rn(x[u], 12582912.f), 12582912.f);
-                            x[u] = (x[u] - dg) * 128.f;
+                            const float dg = __fsub_rn(__fadd_rn(x[u], mg), mg);
+                            x[u] = __fsub_rn(x[u], dg);
                             db[u] = __float_as_uint(dg);
                         }
                         uint4 pk;
@@ -415,12 +423,19 @@ __global__ void __launch_bounds__(kTcThreads) k_leverage_tc(TcLevArgs a) {
                         : "r"(taddr));
                 }
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                // both operands' digits carry their weights 128^-s, 128^-t, so level g
+                // holds D_g 128^-g, exact.  Levels 0 and 1 enter the two-word sums on
+                // their own; levels 2..4 (at most 2^-14 of level 0) are added in float32
+                // first, an error below 2^-38 of the largest product.
 #pragma unroll
-                for (int g = 0; g < kTcLev; ++g) {
-                    const float rsg = rs0 * __uint_as_float((127u - 7u * (uint32_t)g) << 23);   // * 2^-7g
+                for (int l = 0; l < 16; ++l) {
+                    const float sl = csb[l] * rs0;
+                    const float small =
+                        (__uint_as_float(r[2][l]) + __uint_as_float(r[3][l])) + __uint_as_float(r[4][l]);
+                    const float terms[3] = {__uint_as_float(r[0][l]) * sl, __uint_as_float(r[1][l]) * sl, small * sl};
 #pragma unroll
-                    for (int l = 0; l < 16; ++l) {
-                        const float term = (__uint_as_float(r[g][l]) * csb[l]) * rsg;
+                    for (int g = 0; g < 3; ++g) {
+                        const float term = terms[g];
                         const float t = acc_hi[l] + term;
                         const float bpv = t - acc_hi[l];
                         acc_lo[l] += (acc_hi[l] - (t - bpv)) + (term - bpv);
