@@ -497,7 +497,10 @@ int lsqr_run(const cw_csr* A, const float* b, int64_t m, uint64_t seed, double r
     if (st != CW_OK) return st;
     // iterations in batches of four: each pass and post step returns at once
     // when the state says done, so a batch may run past convergence at the
-    // cost of a few empty launches; the host reads the state between batches
+    // cost of a few empty launches; the host reads the state between batches.
+    // x = x0 + M dy is queued behind every batch, before the state is read, so
+    // a call that converges within a batch waits on the device only once (a
+    // later batch overwrites x).
     struct Flags {
         unsigned rank, timeout;
         float klb, pad;
@@ -515,6 +518,10 @@ int lsqr_run(const cw_csr* A, const float* b, int64_t m, uint64_t seed, double r
             }
             st = post();
             if (st != CW_OK) return st;
+        }
+        {
+            CW_PROF("k_upper_matvec", stream);
+            k_upper_matvec<<<(d + 7) / 8, 256, 0, stream>>>(M, d, ws.at<double>(ody), x, x0);
         }
         CW_LAUNCH_CHECK();
         launched += nb;
@@ -539,13 +546,6 @@ int lsqr_run(const cw_csr* A, const float* b, int64_t m, uint64_t seed, double r
         }
         if (hs.done || launched >= max_iter) break;
     }
-    // x = x0 + M dy
-    {
-        CW_PROF("k_upper_matvec", stream);
-        k_upper_matvec<<<(d + 7) / 8, 256, 0, stream>>>(M, d, ws.at<double>(ody), x, x0);
-    }
-    CW_LAUNCH_CHECK();
-    CW_CUDA_TRY(cudaStreamSynchronize(stream));
     if (iters) *iters = hs.iters;
     if (final_test) *final_test = hs.test2;
     return hs.converged ? CW_OK : CW_ERR_NOCONV;
