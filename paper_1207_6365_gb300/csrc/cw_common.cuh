@@ -363,6 +363,22 @@ inline int num_sms() {
     return n > 0 ? n : 1;
 }
 
+// ---- gathers of short row segments (CSR rows visited in bucket order)
+// A random 64-byte segment read with a plain load also pulls the other half
+// of its 128-byte line from DRAM (measured on GB300: 2.0x the useful bytes for
+// random 64-byte segments).  These loads skip L1 and limit the L2 prefetch to
+// 64 bytes (1.05x); the data must not change during the kernel.
+__device__ __forceinline__ int ld_gather(const int32_t* p) {
+    int r;
+    asm("ld.global.nc.L1::no_allocate.L2::64B.s32 %0, [%1];\n" : "=r"(r) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ float ld_gather(const float* p) {
+    float r;
+    asm("ld.global.nc.L1::no_allocate.L2::64B.f32 %0, [%1];\n" : "=f"(r) : "l"(p));
+    return r;
+}
+
 // ---- cp.async helpers (global -> shared without passing through registers)
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);

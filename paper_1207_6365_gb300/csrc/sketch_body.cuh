@@ -428,13 +428,22 @@ __device__ __forceinline__ void apply_csr_bucket(const CsrApplyArgs& a, unsigned
         }
         __syncwarp();
         float sbacc = 0.f;
+        // records of up to 32 rows: lane l holds row k0 + l; the next chunk's
+        // records are loaded while this chunk's rows are gathered
+        int2 rr_next = make_int2(0, 0);
+        float rbv_next = 0.f;
+        if (s + lane < e) {
+            rr_next = __ldg(&a.rs[s + lane]);
+            if (HAS_B || VALS) rbv_next = __ldg(&a.rb[s + lane]);
+        }
         for (int k0 = s; k0 < e; k0 += 32) {
-            // records of up to 32 rows: lane l holds row k0 + l
-            int2 rr = make_int2(0, 0);
-            float rbv = 0.f;
-            if (k0 + lane < e) {
-                rr = __ldg(&a.rs[k0 + lane]);
-                if (HAS_B || VALS) rbv = __ldg(&a.rb[k0 + lane]);
+            const int2 rr = rr_next;
+            const float rbv = rbv_next;
+            rr_next = make_int2(0, 0);
+            rbv_next = 0.f;
+            if (k0 + 32 + lane < e) {
+                rr_next = __ldg(&a.rs[k0 + 32 + lane]);
+                if (HAS_B || VALS) rbv_next = __ldg(&a.rb[k0 + 32 + lane]);
             }
             if (HAS_B) {
                 float t = rbv;
@@ -464,8 +473,8 @@ __device__ __forceinline__ void apply_csr_bucket(const CsrApplyArgs& a, unsigned
                     cc[u] = 0;
                     vv[u] = 0.f;
                     if ((uint32_t)sl < (ln[u] & 0x7FFFFFFFu)) {
-                        cc[u] = __ldg(a.col + st[u] + sl);
-                        vv[u] = __ldg(a.val + st[u] + sl);
+                        cc[u] = ld_gather(a.col + st[u] + sl);
+                        vv[u] = ld_gather(a.val + st[u] + sl);
                     }
                 }
 #pragma unroll
@@ -481,8 +490,8 @@ __device__ __forceinline__ void apply_csr_bucket(const CsrApplyArgs& a, unsigned
                             flag_error(a.status, kDevBadColumn);
                     }
                     for (uint32_t t = sl + LPR; t < L; t += LPR) {  // rows longer than LPR
-                        const int c = __ldg(a.col + st[u] + t);
-                        const float v = __ldg(a.val + st[u] + t);
+                        const int c = ld_gather(a.col + st[u] + t);
+                        const float v = ld_gather(a.val + st[u] + t);
                         if ((unsigned)c < (unsigned)a.d)
                             myacc[c] += VALS ? wt[VALS ? u : 0] * v : (neg ? -v : v);
                         else
