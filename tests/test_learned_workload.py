@@ -20,3 +20,14 @@ def test_family_basis_and_member():
     assert torch.equal(A, A2) and torch.equal(b, b2)
     A3, _ = W.family_matrix(6, 8192, V, sig)
     assert not torch.equal(A, A3)
+
+
+def test_haar_rinv_gives_the_sign_fixed_householder_q():
+    """Z R^-1 (R the Cholesky factor of Z^T Z) is the Q of Z's Householder QR with
+    R's diagonal made positive, to the rounding of the float32 Gram matrix."""
+    Z = torch.randn(4096, 24, generator=torch.Generator().manual_seed(5))
+    U = Z.double() @ W.haar_rinv(Z)
+    q, r = torch.linalg.qr(Z.double())
+    sg = torch.sign(torch.diagonal(r))
+    assert (U - q * sg).abs().max() < 1e-5
+    assert (U.T @ U - torch.eye(24, dtype=torch.float64)).abs().max() < 1e-5

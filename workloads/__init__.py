@@ -268,6 +268,15 @@ def family_basis(d=128, seed=7, device="cpu"):
     return V, sigma
 
 
+def haar_rinv(Z):
+    """R^-1 (float64, d x d) for the Cholesky factor R of Z^T Z: Z R^-1 is the Q
+    factor of Z's QR with R's diagonal positive (the two are the same matrix),
+    Haar-distributed for a Gaussian Z."""
+    d = Z.shape[1]
+    R = torch.linalg.cholesky((Z.T @ Z).double()).T
+    return torch.linalg.solve_triangular(R, torch.eye(d, dtype=torch.float64, device=Z.device), upper=True)
+
+
 def family_matrix(k, n, V, sigma, device="cpu"):
     """(A float32 (n, d) row-major, b float32 (n,)) of member k of the family:
     A = U diag(sigma) V^T + 1e-3 N(0, 1), b = A x0 + 0.05 N(0, 1).
@@ -279,8 +288,7 @@ def family_matrix(k, n, V, sigma, device="cpu"):
     d = V.shape[0]
     g = _gen(1000003 + k, device)
     Z = torch.randn(n, d, dtype=torch.float32, device=device, generator=g)
-    R = torch.linalg.cholesky((Z.T @ Z).double()).T
-    Rinv = torch.linalg.solve_triangular(R, torch.eye(d, dtype=torch.float64, device=device), upper=True)
+    Rinv = haar_rinv(Z)
     mix = (Rinv * sigma.to(device=device, dtype=torch.float64)) @ V.to(device=device, dtype=torch.float64).T
     A = Z @ mix.to(torch.float32)
     del Z
