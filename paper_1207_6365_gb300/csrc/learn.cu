@@ -39,18 +39,28 @@ constexpr size_t kLnSmemMax = 200 * 1024;
 // pivot is not above 1e-14 of its original diagonal G_kk (left at n when
 // none); the last column (b) may end with a zero pivot, b then lying in the
 // range of A.
+// Thread 0 forms each pivot's square root and reciprocal (float64 square roots
+// and divisions are long sequences on this part) and the block reads them.
 __device__ void chol_upper_block(double* W, int n, const double* G, int* bad) {
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __shared__ double s_piv[3];
     for (int k = 0; k < n; ++k) {
-        const double piv = W[(int64_t)k * n + k];
-        const double tol = k < n - 1 ? 1e-14 * G[(int64_t)k * n + k] : -INFINITY;
+        if (threadIdx.x == 0) {
+            const double piv = W[(int64_t)k * n + k];
+            const double tol = k < n - 1 ? 1e-14 * G[(int64_t)k * n + k] : -INFINITY;
+            const bool okp = piv > tol;   // also false for NaN
+            const double rk = sqrt(piv > 0.0 ? piv : 0.0);
+            s_piv[0] = okp ? 1.0 : 0.0;
+            s_piv[1] = rk;
+            s_piv[2] = rk > 0.0 ? 1.0 / rk : 0.0;
+        }
         __syncthreads();
-        if (!(piv > tol)) {  // also catches NaN; every thread sees the same piv
+        if (s_piv[0] == 0.0) {
             if (threadIdx.x == 0) *bad = k;
             return;
         }
-        const double rk = sqrt(piv > 0.0 ? piv : 0.0);
-        const double inv = rk > 0.0 ? 1.0 / rk : 0.0;
+        const double rk = s_piv[1];
+        const double inv = s_piv[2];
         for (int j = k + threadIdx.x; j < n; j += blockDim.x)
             W[(int64_t)k * n + j] = j == k ? rk : W[(int64_t)k * n + j] * inv;
         __syncthreads();
@@ -69,11 +79,17 @@ __device__ void chol_upper_block(double* W, int n, const double* G, int* bad) {
 // sx (shared, d doubles) receives x.  Step j: every thread forms x_j from the
 // settled sw[j] (unchanged during the step), the owner of j stores it, the
 // owners of i < j subtract R_ij x_j: one barrier a step.
-__device__ void back_substitute(const double* W, int d, int ldw, const double* c, double* sw, double* sx) {
-    for (int i = threadIdx.x; i < d; i += blockDim.x) sw[i] = c[(int64_t)i * ldw];
+// rinv (shared, d doubles) receives the reciprocals of the diagonal first, one
+// division per thread in parallel (float64 divisions are long on this part).
+__device__ void back_substitute(const double* W, int d, int ldw, const double* c, double* sw, double* sx,
+                                double* rinv) {
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        sw[i] = c[(int64_t)i * ldw];
+        rinv[i] = 1.0 / W[(int64_t)i * ldw + i];
+    }
     __syncthreads();
     for (int j = d - 1; j >= 0; --j) {
-        const double xj = sw[j] / W[(int64_t)j * ldw + j];
+        const double xj = sw[j] * rinv[j];
         for (int i = threadIdx.x; i < d; i += blockDim.x) {
             if (i == j) sx[i] = xj;
             else if (i < j) sw[i] -= W[(int64_t)i * ldw + j] * xj;
@@ -84,8 +100,8 @@ __device__ void back_substitute(const double* W, int d, int ldw, const double* c
 
 // x* and ||A x* - b||^2 (and R, when Rout is given) from the bordered Gram
 // matrix G ((d+1) x (d+1)).  SMEM: the factor is formed in shared memory
-// (n^2 + 2 d doubles), otherwise in the global workspace Wg (n^2 doubles;
-// shared memory then holds 2 d doubles).
+// (n^2 + 3 d doubles), otherwise in the global workspace Wg (n^2 doubles;
+// shared memory then holds 3 d doubles).
 template <bool SMEM>
 __global__ void __launch_bounds__(kLnThreads) k_normal_solve(const double* __restrict__ G, int d, double* Wg,
                                                              double* __restrict__ x, double* __restrict__ r2,
@@ -100,7 +116,7 @@ __global__ void __launch_bounds__(kLnThreads) k_normal_solve(const double* __res
     chol_upper_block(W, n, G, bad);
     __syncthreads();
     if (*bad != n) return;
-    back_substitute(W, d, n, W + d, sx + d, sx);
+    back_substitute(W, d, n, W + d, sx + d, sx, sx + 2 * d);
     for (int i = threadIdx.x; i < d; i += blockDim.x) x[i] = sx[i];
     if (Rout)
         for (int64_t e = threadIdx.x; e < (int64_t)d * d; e += blockDim.x) {
@@ -134,8 +150,10 @@ __global__ void __launch_bounds__(kLnThreads) k_excess(const double* __restrict_
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
         if (lane == 0) Ge[i] = acc;
     }
+    if (threadIdx.x == 0) red[0] = 1.0 / *r2;   // one division for the block
     __syncthreads();
-    const double inv = 1.0 / *r2;
+    const double inv = red[0];
+    __syncthreads();   // red is reused below
     double part = 0.0;
     for (int i = threadIdx.x; i < d; i += blockDim.x) {
         part = fma(e[i], Ge[i], part);
@@ -153,7 +171,8 @@ __global__ void __launch_bounds__(kLnThreads) k_excess(const double* __restrict_
 }
 
 // z = R^-1 R^-T g (R upper, row-major d x d); one CTA, shared memory: two
-// d-vectors (SMEM: then R, d^2 more doubles).
+// d-vectors (SMEM: then R, d^2 more doubles, and the reciprocals of its
+// diagonal, d more).
 template <bool SMEM>
 __global__ void __launch_bounds__(kLnThreads) k_gram_inv_apply(const double* __restrict__ Rg, int d,
                                                                const double* __restrict__ g, double* __restrict__ z) {
@@ -165,14 +184,18 @@ __global__ void __launch_bounds__(kLnThreads) k_gram_inv_apply(const double* __r
         for (int64_t e = threadIdx.x; e < (int64_t)d * d; e += blockDim.x) Rs[e] = Rg[e];
         R = Rs;
     }
-    for (int i = threadIdx.x; i < d; i += blockDim.x) sz[i] = g[i];
+    double* rinv = SMEM ? sz + 2 * d + (size_t)d * d : nullptr;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        sz[i] = g[i];
+        if (SMEM) rinv[i] = 1.0 / R[(int64_t)i * d + i];   // one division per thread, in parallel
+    }
     __syncthreads();
     // R^T y = g: forward substitution along the rows of R.  Step j: every
     // thread forms y_j from the settled sz[j] (left unchanged during the
     // step), the owner of entry j stores it in yv, the owners of i > j subtract
     // R_ji y_j from sz[i]: one barrier a step.
     for (int j = 0; j < d; ++j) {
-        const double yj = sz[j] / R[(int64_t)j * d + j];
+        const double yj = SMEM ? sz[j] * rinv[j] : sz[j] / R[(int64_t)j * d + j];
         for (int i = threadIdx.x; i < d; i += blockDim.x) {
             if (i == j) yv[i] = yj;
             else if (i > j) sz[i] -= R[(int64_t)j * d + i] * yj;
@@ -182,7 +205,7 @@ __global__ void __launch_bounds__(kLnThreads) k_gram_inv_apply(const double* __r
     // R z = y: back substitution along the columns of R, yv the work vector
     // and sz the result
     for (int j = d - 1; j >= 0; --j) {
-        const double zj = yv[j] / R[(int64_t)j * d + j];
+        const double zj = SMEM ? yv[j] * rinv[j] : yv[j] / R[(int64_t)j * d + j];
         for (int i = threadIdx.x; i < d; i += blockDim.x) {
             if (i == j) sz[i] = zj;
             else if (i < j) yv[i] -= R[(int64_t)i * d + j] * zj;
@@ -297,7 +320,7 @@ extern "C" int cw_solve_sketched_backward(const float* SA, const float* Sb, int6
     const size_t oz = ws.reserve(sizeof(double) * (size_t)d);
     CW_CUDA_TRY(ws.alloc());
     double* z = ws.at<double>(oz);
-    const size_t sm = sizeof(double) * (size_t)(2 * d + d * d);
+    const size_t sm = sizeof(double) * (size_t)(3 * d + d * d);
     // one thread per entry of z (fewer warps make the barriers cheaper)
     const int th = (int)std::min<int64_t>(kLnThreads, (d + 31) & ~31ll);
     if (sm <= kLnSmemMax) {
@@ -323,7 +346,7 @@ extern "C" int cw_normal_solve(const double* G, int64_t d, double* x, double* r2
     if (d < 1 || d > 1024) return CW_ERR_SHAPE;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = d + 1;
-    const size_t sm = sizeof(double) * (size_t)(n * n + 2 * d);
+    const size_t sm = sizeof(double) * (size_t)(n * n + 3 * d);
     const bool in_smem = sm <= kLnSmemMax;
     Scratch ws(s);
     const size_t oW = in_smem ? 0 : ws.reserve(sizeof(double) * (size_t)(n * n));
@@ -336,7 +359,7 @@ extern "C" int cw_normal_solve(const double* G, int64_t d, double* x, double* r2
         k_normal_solve<true><<<1, kNsThreads, sm, s>>>(G, (int)d, nullptr, x, r2, R, bad);
     } else {
         CW_PROF("k_normal_solve", s);
-        k_normal_solve<false><<<1, kNsThreads, sizeof(double) * 2 * (size_t)d, s>>>(G, (int)d, ws.at<double>(oW), x,
+        k_normal_solve<false><<<1, kNsThreads, sizeof(double) * 3 * (size_t)d, s>>>(G, (int)d, ws.at<double>(oW), x,
                                                                                    r2, R, bad);
     }
     CW_LAUNCH_CHECK();

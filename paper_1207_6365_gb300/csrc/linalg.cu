@@ -97,27 +97,30 @@ __global__ void __launch_bounds__(1024) k_qr_householder(QrArgs a) {
     for (int j = 0; j < a.d; ++j) {
         // reflector for column j: every block forms the same scalars (lanes
         // over blocks, then the warp's tree: the same fixed order everywhere)
+        // (the scalars formed by one thread: float64 square roots and divisions
+        // are long sequences on this part)
         if (warp == 0) {
             double t = 0.0;
             for (unsigned c = lane; c < G; c += 32) t += a.normp[c];
             t = warp_sum(t);
-            if (lane == 0) s_red[0] = t;
+            if (lane == 0) {
+                const double sig2 = t;
+                const double ajj = a.W[(int64_t)j * a.m + j];
+                double beta = 0.0, tau = 0.0, vscale = 0.0;
+                if (sig2 != 0.0) {
+                    const double sig = sqrt(sig2);
+                    beta = ajj >= 0.0 ? -sig : sig;
+                    tau = (beta - ajj) / beta;
+                    vscale = 1.0 / (ajj - beta);
+                }
+                s_red[0] = beta;
+                s_red[1] = tau;
+                s_red[2] = vscale;
+            }
         }
         __syncthreads();
-        const double sig2 = s_red[0];
+        const double beta = s_red[0], tau = s_red[1], vscale = s_red[2];
         __syncthreads();
-        const double ajj = a.W[(int64_t)j * a.m + j];
-        double beta, tau, vscale;
-        if (sig2 == 0.0) {
-            beta = 0.0;
-            tau = 0.0;
-            vscale = 0.0;
-        } else {
-            const double sig = sqrt(sig2);
-            beta = ajj >= 0.0 ? -sig : sig;
-            tau = (beta - ajj) / beta;
-            vscale = 1.0 / (ajj - beta);
-        }
         // v for my rows (0 above the diagonal, 1 at it)
         const double* colj = a.W + (int64_t)j * a.m;
         for (int64_t q = threadIdx.x; q < rows; q += blockDim.x) {
@@ -246,11 +249,13 @@ __global__ void __launch_bounds__(1024) k_qr_blocked(QrbArgs a) {
         const int buf = j & 1;
         const double* colj = a.W + (int64_t)j * a.m + r0;
         double s = 0.0;
-        for (int q = tid; q < rows; q += blockDim.x) {
-            const int64_t i = r0 + q;
-            if (i >= j) s = fma(colj[q], colj[q], s);
+        if (warp * 32 < rows) {   // warps without rows skip the float64 shuffle tree
+            for (int q = tid; q < rows; q += blockDim.x) {
+                const int64_t i = r0 + q;
+                if (i >= j) s = fma(colj[q], colj[q], s);
+            }
+            s = warp_sum(s);
         }
-        s = warp_sum(s);
         if (lane == 0) s_red[warp] = s;
         for (int k = j + 1 + warp; k < kend; k += nwarps) {
             const double* colk = a.W + (int64_t)k * a.m + r0;
@@ -286,27 +291,31 @@ __global__ void __launch_bounds__(1024) k_qr_blocked(QrbArgs a) {
             const int jl = j - j0, buf = j & 1;
             // ||column j||^2: lanes over blocks, then the warp's tree (the same
             // fixed order in every block)
+            // and the reflector's scalars, formed once: float64 square roots and
+            // divisions are long sequences on a part with little float64 rate, so
+            // one thread forms them and the block reads them from shared memory
             if (warp == 0) {
                 double t = 0.0;
                 for (unsigned c = lane; c < G; c += 32) t += a.normp[buf * G + c];
                 t = warp_sum(t);
-                if (lane == 0) s_red[0] = t;
+                if (lane == 0) {
+                    const double sig2 = t;
+                    const double ajj = a.rowv[buf * kQrB + jl];
+                    double beta = 0.0, tau = 0.0, vscale = 0.0;
+                    if (sig2 != 0.0) {
+                        const double sig = sqrt(sig2);
+                        beta = ajj >= 0.0 ? -sig : sig;
+                        tau = (beta - ajj) / beta;
+                        vscale = 1.0 / (ajj - beta);
+                    }
+                    s_red[0] = beta;
+                    s_red[1] = tau;
+                    s_red[2] = vscale;
+                    stau[jl] = tau;
+                }
             }
             __syncthreads();
-            const double sig2 = s_red[0];
-            const double ajj = a.rowv[buf * kQrB + jl];
-            double beta, tau, vscale;
-            if (sig2 == 0.0) {
-                beta = 0.0;
-                tau = 0.0;
-                vscale = 0.0;
-            } else {
-                const double sig = sqrt(sig2);
-                beta = ajj >= 0.0 ? -sig : sig;
-                tau = (beta - ajj) / beta;
-                vscale = 1.0 / (ajj - beta);
-            }
-            if (tid == 0) stau[jl] = tau;
+            const double beta = s_red[0], tau = s_red[1], vscale = s_red[2];
             const double* colj = a.W + (int64_t)j * a.m;
             for (int q = tid; q < rows; q += blockDim.x) {
                 const int64_t i = r0 + q;

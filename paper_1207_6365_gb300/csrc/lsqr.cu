@@ -113,17 +113,23 @@ __global__ void __launch_bounds__(256) k_lsqr_post_mc(PostMcArgs a) {
         if (lane == 0) a.gsum[j] = make_float2(hi, lo);
     }
     // ||z||^2 (and ||b||^2 on the first step): every CTA the same sums
+    // (beta and its reciprocal formed by one thread: float64 square roots and
+    // divisions are long sequences on this part)
+    __shared__ double s_beta[2];
     if (warp == 0) {
         const double zz = warp_sum_fixed(q.zpart, q.nblk, lane);
         const double bb = q.first ? warp_sum_fixed(q.bpart, q.nblk, lane) : 0.0;
         if (lane == 0) {
             s_sc[6] = zz;
             s_sc[7] = bb;
+            const double be = sqrt(zz);
+            s_beta[0] = be;
+            s_beta[1] = be > 0.0 ? (q.first ? -1.0 / be : 1.0 / be) : 0.0;
         }
     }
     if (!grid_barrier(a.bar, (unsigned)P, a.tflag)) return;
-    const double beta = sqrt(s_sc[6]);
-    const double s_new = beta > 0.0 ? (q.first ? -1.0 / beta : 1.0 / beta) : 0.0;
+    const double beta = s_beta[0];
+    const double s_new = s_beta[1];
 
     // 2. t = M^T g for the CTA's columns (warp per column, lanes over rows i <= j)
     for (int j = j0 + warp; j < j1; j += nwarp) {
@@ -171,10 +177,10 @@ __global__ void __launch_bounds__(256) k_lsqr_post_mc(PostMcArgs a) {
     // 3. alpha, the rotation, the vector updates for the CTA's columns
     if (warp == 0) {
         const double t = warp_sum_fixed(a.share, P, lane);
-        if (lane == 0) s_a2 = t;
+        if (lane == 0) s_a2 = sqrt(t);
     }
     __syncthreads();
-    const double alpha = sqrt(s_a2);
+    const double alpha = s_a2;
     if (q.first) {
         for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
             const double vj = alpha > 0.0 ? a.tv[j] / alpha : 0.0;
