@@ -472,14 +472,20 @@ __global__ void k_qr_finalize(const double* __restrict__ W, int64_t m, int d, in
 
 // ---------------------------------------------------------------- triangular solves (float64)
 
-// x = R^-1 rhs for upper-triangular row-major R (one CTA, column sweep).
+// x = R^-1 rhs for upper-triangular row-major R (one CTA, column sweep).  The
+// reciprocals of the diagonal are formed first, one division per thread in
+// parallel (float64 divisions are long sequences on this part).
 __global__ void k_trsv_upper(const double* __restrict__ R, int d, const double* __restrict__ rhs,
                              double* __restrict__ x) {
     extern __shared__ double sx[];
-    for (int i = threadIdx.x; i < d; i += blockDim.x) sx[i] = rhs[i];
+    double* rinv = sx + d;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        sx[i] = rhs[i];
+        rinv[i] = 1.0 / R[(int64_t)i * d + i];
+    }
     __syncthreads();
     for (int j = d - 1; j >= 0; --j) {
-        if (threadIdx.x == 0) sx[j] = sx[j] / R[(int64_t)j * d + j];
+        if (threadIdx.x == 0) sx[j] = sx[j] * rinv[j];
         __syncthreads();
         const double xj = sx[j];
         for (int i = threadIdx.x; i < j; i += blockDim.x) sx[i] -= R[(int64_t)i * d + j] * xj;
@@ -493,11 +499,15 @@ __global__ void k_trsv_upper(const double* __restrict__ R, int d, const double* 
 __global__ void k_trsm_upper(const double* __restrict__ R, int d, const double* __restrict__ B, int k,
                              double* __restrict__ X) {
     extern __shared__ double sx[];
+    double* rinv = sx + d;   // reciprocals of the diagonal, formed in parallel
     const int col = blockIdx.x;
-    for (int i = threadIdx.x; i < d; i += blockDim.x) sx[i] = B ? B[(int64_t)i * k + col] : (i == col ? 1.0 : 0.0);
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        sx[i] = B ? B[(int64_t)i * k + col] : (i == col ? 1.0 : 0.0);
+        rinv[i] = 1.0 / R[(int64_t)i * d + i];
+    }
     __syncthreads();
     for (int j = d - 1; j >= 0; --j) {
-        if (threadIdx.x == 0) sx[j] = sx[j] / R[(int64_t)j * d + j];
+        if (threadIdx.x == 0) sx[j] = sx[j] * rinv[j];
         __syncthreads();
         const double xj = sx[j];
         if (xj != 0.0)
@@ -1490,7 +1500,7 @@ int gram_chol_inverse(const float* SA, int64_t m, int d, const float* Sb, double
 int trsv_upper(const double* R, int d, const double* rhs, double* x, cudaStream_t stream) {
     {
         CW_PROF("k_trsv_upper", stream);
-        k_trsv_upper<<<1, 256, sizeof(double) * d, stream>>>(R, d, rhs, x);
+        k_trsv_upper<<<1, 256, sizeof(double) * 2 * (size_t)d, stream>>>(R, d, rhs, x);
     }
     CW_LAUNCH_CHECK();
     return CW_OK;
@@ -1519,7 +1529,7 @@ int tri_inverse(const double* R, int d, double* M, cudaStream_t stream) {
 int trsm_upper(const double* R, int d, const double* B, int k, double* X, cudaStream_t stream) {
     {
         CW_PROF("k_trsm_upper", stream);
-        k_trsm_upper<<<k, 256, sizeof(double) * d, stream>>>(R, d, B, k, X);
+        k_trsm_upper<<<k, 256, sizeof(double) * 2 * (size_t)d, stream>>>(R, d, B, k, X);
     }
     CW_LAUNCH_CHECK();
     return CW_OK;
