@@ -183,8 +183,8 @@ __device__ __forceinline__ void apply_csr_range(const CsrApplyArgs& a, int bk0, 
                 cc[u] = 0;
                 vv[u] = 0.f;
                 if ((uint32_t)lane < (ln[u] & 0x7FFFFFFFu)) {
-                    cc[u] = ld_gather(a.col + st[u] + lane);
-                    vv[u] = ld_gather(a.val + st[u] + lane);
+                    cc[u] = __ldg(a.col + st[u] + lane);
+                    vv[u] = __ldg(a.val + st[u] + lane);
                 }
             }
 #pragma unroll
@@ -198,8 +198,8 @@ __device__ __forceinline__ void apply_csr_range(const CsrApplyArgs& a, int bk0, 
                     else flag_error(a.status, kDevBadColumn);
                 }
                 for (uint32_t t = lane + 32; t < L; t += 32) {  // rows longer than 32
-                    const int c = ld_gather(a.col + st[u] + t);
-                    const float v = ld_gather(a.val + st[u] + t);
+                    const int c = __ldg(a.col + st[u] + t);
+                    const float v = __ldg(a.val + st[u] + t);
                     if ((unsigned)c < (unsigned)a.d) row[c] += neg ? -v : v;
                     else flag_error(a.status, kDevBadColumn);
                 }

@@ -367,7 +367,8 @@ inline int num_sms() {
 // A random 64-byte segment read with a plain load also pulls the other half
 // of its 128-byte line from DRAM (measured on GB300: 2.0x the useful bytes for
 // random 64-byte segments).  These loads skip L1 and limit the L2 prefetch to
-// 64 bytes (1.05x); the data must not change during the kernel.
+// 64 bytes (1.05x); the data must not change during the kernel.  For segments
+// that cross a 64-byte boundary the default fetch is faster.
 __device__ __forceinline__ int ld_gather(const int32_t* p) {
     int r;
     asm("ld.global.nc.L1::no_allocate.L2::64B.s32 %0, [%1];\n" : "=r"(r) : "l"(p));

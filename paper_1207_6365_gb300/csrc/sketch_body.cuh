@@ -472,9 +472,19 @@ __device__ __forceinline__ void apply_csr_bucket(const CsrApplyArgs& a, unsigned
                 for (int u = 0; u < U; ++u) {
                     cc[u] = 0;
                     vv[u] = 0.f;
-                    if ((uint32_t)sl < (ln[u] & 0x7FFFFFFFu)) {
-                        cc[u] = ld_gather(a.col + st[u] + sl);
-                        vv[u] = ld_gather(a.val + st[u] + sl);
+                    const uint32_t L = ln[u] & 0x7FFFFFFFu;
+                    if ((uint32_t)sl < L) {
+                        // a row inside one 64-byte block of col and of val: fetch just
+                        // that block; other rows keep the default L2 fetch (for
+                        // unaligned or longer rows the 64-byte limit splits what one
+                        // 128-byte fetch would bring: measured slower)
+                        if ((uint32_t)(st[u] & 15) + L <= 16u) {
+                            cc[u] = ld_gather(a.col + st[u] + sl);
+                            vv[u] = ld_gather(a.val + st[u] + sl);
+                        } else {
+                            cc[u] = __ldg(a.col + st[u] + sl);
+                            vv[u] = __ldg(a.val + st[u] + sl);
+                        }
                     }
                 }
 #pragma unroll
@@ -490,8 +500,8 @@ __device__ __forceinline__ void apply_csr_bucket(const CsrApplyArgs& a, unsigned
                             flag_error(a.status, kDevBadColumn);
                     }
                     for (uint32_t t = sl + LPR; t < L; t += LPR) {  // rows longer than LPR
-                        const int c = ld_gather(a.col + st[u] + t);
-                        const float v = ld_gather(a.val + st[u] + t);
+                        const int c = __ldg(a.col + st[u] + t);
+                        const float v = __ldg(a.val + st[u] + t);
                         if ((unsigned)c < (unsigned)a.d)
                             myacc[c] += VALS ? wt[VALS ? u : 0] * v : (neg ? -v : v);
                         else
