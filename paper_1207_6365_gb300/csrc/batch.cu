@@ -348,20 +348,29 @@ __device__ void chol_solve(const SolveArgs& S, int p, double* sm) {
     const int64_t nt = tri(d);
     double* G = sm;         // packed lower [nt]
     double* v = sm + nt;    // [d]
+    double* dinv = v + kMaxBatchD + 16;   // [d] reciprocals of L's diagonal
     __shared__ int ok;
     for (int64_t e = tid; e < nt; e += kSolveThreads) G[e] = sum_units(S.Gp, P.g0, P.gstride, P.nunits, e);
     for (int j = tid; j < d; j += kSolveThreads) v[j] = sum_units(S.Vp, P.v0, P.vstride, P.nunits, j);
     if (tid == 0) ok = 1;
     __syncthreads();
+    __shared__ double s_rl;
     for (int j = 0; j < d; ++j) {
+        // thread 0 forms the pivot's root and its reciprocal: float64 square roots
+        // and divisions are long sequences on this part, so the block reads them
         if (tid == 0) {
             const double piv = G[tri(j) + j];
             if (!(piv > 0.0)) ok = 0;
-            else G[tri(j) + j] = sqrt(piv);
+            else {
+                const double r = sqrt(piv);
+                G[tri(j) + j] = r;
+                s_rl = 1.0 / r;
+                dinv[j] = s_rl;
+            }
         }
         __syncthreads();
         if (!ok) break;
-        const double rl = 1.0 / G[tri(j) + j];  // one division per column (float64 divides are long)
+        const double rl = s_rl;
         for (int i = j + 1 + tid; i < d; i += kSolveThreads) G[tri(i) + j] *= rl;
         __syncthreads();
         for (int i = j + 1 + warp; i < d; i += kSolveThreads / 32) {
@@ -380,13 +389,13 @@ __device__ void chol_solve(const SolveArgs& S, int p, double* sm) {
     }
     // L y = v, then L^T x = y (v overwritten)
     for (int j = 0; j < d; ++j) {
-        if (tid == 0) v[j] /= G[tri(j) + j];
+        if (tid == 0) v[j] *= dinv[j];
         __syncthreads();
         for (int i = j + 1 + tid; i < d; i += kSolveThreads) v[i] -= G[tri(i) + j] * v[j];
         __syncthreads();
     }
     for (int j = d - 1; j >= 0; --j) {
-        if (tid == 0) v[j] /= G[tri(j) + j];
+        if (tid == 0) v[j] *= dinv[j];
         __syncthreads();
         for (int i = tid; i < j; i += kSolveThreads) v[i] -= G[tri(j) + i] * v[j];
         __syncthreads();
@@ -509,17 +518,19 @@ __device__ void refine_update(const SolveArgs& S, int p, bool first, bool last, 
     double* G = sm;
     double* v = sm + nt;
     double* red = v + kMaxBatchD;  // [2 * 8]
+    double* dinv = red + 16;       // [d] reciprocals of L's diagonal, one division per thread
     for (int64_t e = tid; e < nt; e += kSolveThreads) G[e] = P.L[e];
+    for (int j = tid; j < d; j += kSolveThreads) dinv[j] = 1.0 / P.L[tri(j) + j];
     for (int j = tid; j < d; j += kSolveThreads) v[j] = sum_units(S.Vp, P.v0, P.vstride, P.nunits, j);
     __syncthreads();
     for (int j = 0; j < d; ++j) {
-        if (tid == 0) v[j] /= G[tri(j) + j];
+        if (tid == 0) v[j] *= dinv[j];
         __syncthreads();
         for (int i = j + 1 + tid; i < d; i += kSolveThreads) v[i] -= G[tri(i) + j] * v[j];
         __syncthreads();
     }
     for (int j = d - 1; j >= 0; --j) {
-        if (tid == 0) v[j] /= G[tri(j) + j];
+        if (tid == 0) v[j] *= dinv[j];
         __syncthreads();
         for (int i = tid; i < j; i += kSolveThreads) v[i] -= G[tri(j) + i] * v[j];
         __syncthreads();
@@ -619,7 +630,7 @@ size_t solve_smem_bytes() {
     const int ldt = std::max(16 * 8 + 4, kMaxBatchD + 8);
     const size_t unit = sizeof(int) * kMaxSlab + sizeof(float) * kStages * kChunkRows * (ldt + 1) +
                         sizeof(int) * 16 + sizeof(double) * (3 * kMaxBatchD + kChunkRows);
-    const size_t chol = sizeof(double) * ((size_t)kMaxBatchD * (kMaxBatchD + 1) / 2 + kMaxBatchD + 16);
+    const size_t chol = sizeof(double) * ((size_t)kMaxBatchD * (kMaxBatchD + 1) / 2 + 2 * kMaxBatchD + 16);
     return std::max(unit, chol);
 }
 
