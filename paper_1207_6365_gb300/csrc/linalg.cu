@@ -1220,6 +1220,11 @@ __global__ void __launch_bounds__(256) k_tri_inv_blk(const float* __restrict__ W
 // M = R^-1 for upper-triangular row-major R (float64); one warp per column of
 // M, RT = R^T (column j of R contiguous) for coalesced reads.
 __global__ void k_tri_inverse(const double* __restrict__ RT, int d, double* __restrict__ M) {
+    // reciprocals of the diagonal, one division per thread in parallel (float64
+    // divisions are long sequences on this part; the sweep below multiplies)
+    __shared__ double rinv[1024];
+    for (int i = threadIdx.x; i < d; i += blockDim.x) rinv[i] = 1.0 / RT[(int64_t)i * d + i];
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int col = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (col >= d) return;
@@ -1237,7 +1242,7 @@ __global__ void k_tri_inverse(const double* __restrict__ RT, int d, double* __re
 #pragma unroll
         for (int q = 0; q < kMaxPer; ++q)
             if (q == qj) sj = s[q];
-        const double xj = __shfl_sync(0xFFFFFFFFu, sj, oj) / RT[(int64_t)j * d + j];
+        const double xj = __shfl_sync(0xFFFFFFFFu, sj, oj) * rinv[j];
 #pragma unroll
         for (int q = 0; q < kMaxPer; ++q) {
             if (q < per) {
