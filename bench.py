@@ -413,6 +413,25 @@ def _timed(fn, stream, reps=3, warm=1):
     return e0.elapsed_time(e1) / reps
 
 
+def gather_ceiling(cw, stream, device):
+    """Read throughput (GB/s) of 64-byte segments at random places of a 2 GiB
+    array (larger than L2), issued like the segmented sum's row gathers, and of
+    the same kernel on consecutive segments; the better of 4 and 8 CTAs per SM."""
+    import torch
+    a = torch.ones(1 << 29, dtype=torch.float32, device=device)
+    nseg = a.numel() // 16
+    out = torch.zeros(1, dtype=torch.float32, device=device)
+    res = {}
+    for key, seq in (("random_64B_GBps", False), ("sequential_64B_GBps", True)):
+        best = 0.0
+        for k in (4, 8):
+            ms = _timed(lambda: cw.probe_gather64(a, nseg, seq, k, out), stream, reps=3, warm=1)
+            best = max(best, nseg * 64 / (ms / 1000.0) / 1e9)
+        res[key] = best
+    del a
+    return res
+
+
 def _stage_ms(cw, names, reps):
     out = {}
     for nm in names:
@@ -817,6 +836,14 @@ def run_cw(args):
                        "nnz_per_s": nnz / (sk_ms / 1000.0), "traffic": ncu_traffic("k_apply_csr"),
                        "traffic_of": "k_apply_csr (the segmented sum)", "stages_ms": sk_stages}
     del SA, Sb
+    # the segmented sum reads each row's col and val as 64-byte segments at
+    # random places: its ceiling is the random segment read rate, not the copy
+    gc = gather_ceiling(cw, stream, device)
+    sketch_roofline["gather_ceiling"] = gc
+    if sk_stages.get("k_apply_csr"):
+        g = nnz * 8 / (sk_stages["k_apply_csr"] / 1000.0) / 1e9
+        sketch_roofline["apply_gather_GBps"] = g
+        sketch_roofline["apply_frac_of_random_64B"] = g / gc["random_64B_GBps"]
 
     # end to end through the C ABI from pinned host buffers
     e2e = None

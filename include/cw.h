@@ -501,6 +501,23 @@ int cw_profile_enable(int enable);
 int cw_profile_get(const char *kernel, long long *launches, double *total_ms);
 int cw_profile_reset(void);
 
+/*
+ * cw_probe_gather64 (measurement probe, not part of the paper's method): reads
+ * nseg 64-byte segments of the device array a (nseg_total * 16 floats,
+ * nseg_total a power of two) the way the CSR segmented sum gathers its rows
+ * (16 lanes of 4 bytes per segment, 16 segments per half-warp in flight,
+ * 64-byte L2 fetches), at segment indices spread over the array by a 64-bit
+ * mixing function (sequential == 0) or consecutive (sequential != 0, the
+ * calibration).  One launch of ctas_per_sm (1..8) CTAs of 256 threads per SM
+ * on `stream`; time it with events on that stream: nseg * 64 bytes / time is
+ * the segment read throughput.  out: one device float, written only if the
+ * data hold a NaN.  Errors: CW_ERR_ARG (null pointer, ctas_per_sm out of
+ * range), CW_ERR_SHAPE (nseg_total not a power of two, nseg < 0),
+ * CW_ERR_OVERFLOW (nseg_total > 2^40), CW_ERR_CUDA.
+ */
+int cw_probe_gather64(const float *a, int64_t nseg_total, int64_t nseg, int sequential, int ctas_per_sm,
+                      float *out, cw_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

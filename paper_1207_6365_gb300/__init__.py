@@ -35,7 +35,7 @@ EXPORTS = (
     "cw_sketch_values_backward_csr", "cw_sketch_values_backward_dense", "cw_solve_sketch_dense", "cw_lsqr_precond",
     "cw_lsqr_precond_host", "cw_leverage", "cw_launch_count", "cw_profile_enable", "cw_profile_get", "cw_profile_reset",
     "cw_solve_sketched", "cw_solve_sketched_backward", "cw_normal_solve", "cw_excess_residual", "cw_scale_rows",
-    "cw_scale_rows_backward",
+    "cw_scale_rows_backward", "cw_probe_gather64",
 )
 
 
@@ -105,6 +105,7 @@ _SIGS = {
     "cw_profile_enable": ([ctypes.c_int], ctypes.c_int),
     "cw_profile_get": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_f64)], ctypes.c_int),
     "cw_profile_reset": ([], ctypes.c_int),
+    "cw_probe_gather64": ([_p, _i64, _i64, ctypes.c_int, ctypes.c_int, _p, _p], ctypes.c_int),
 }
 
 
@@ -661,3 +662,16 @@ def profile_get(kernel):
     ms = ctypes.c_double(0.0)
     _check(load().cw_profile_get(kernel.encode(), ctypes.byref(n), ctypes.byref(ms)), "cw_profile_get")
     return int(n.value), float(ms.value)
+
+
+def probe_gather64(a, nseg, sequential=False, ctas_per_sm=4, out=None):
+    """One launch of the 64-byte segment read probe over the float32 device
+    tensor ``a`` (a power-of-two multiple of 16 elements) on the current
+    stream; time it with events on that stream (nseg * 64 bytes per launch)."""
+    if a.dtype != torch.float32 or not a.is_cuda or not a.is_contiguous() or a.numel() % 16:
+        raise ValueError("a: a contiguous float32 CUDA tensor of 16 * 2^k elements")
+    out = torch.zeros(1, dtype=torch.float32, device=a.device) if out is None else out
+    _check(load().cw_probe_gather64(_ptr(a, torch.float32, "a"), a.numel() // 16, int(nseg),
+                                    1 if sequential else 0, int(ctas_per_sm), _ptr(out, torch.float32, "out"),
+                                    _stream()), "cw_probe_gather64")
+    return out

@@ -10,14 +10,18 @@
 //   K3  k_coarse_scatter stable scatter of per-row records (key, row start,
 //                       row length, sigma*b) into coarse-bin order.  Rows are
 //                       read coalesced here, once.
-//   K4  k_apply_*       one CTA per coarse bin (a group of G buckets): stable
-//                       counting sort of the group's records by bucket in
-//                       shared memory (this is the permutation P of Section
-//                       5.2: rows of h^-1(1) first, then h^-1(2), ...), then
-//                       warps take whole buckets and add sigma(i) A_i into the
-//                       bucket's row in ascending row order; the finished SA
-//                       row is written once.  No global atomics, no floating
-//                       point atomics: results are bitwise reproducible.
+//   K4a k_fine_sort     one CTA per coarse bin (a group of G buckets): stable
+//                       counting sort of the bin's records by bucket, the bin
+//                       staged in shared memory (this is the permutation P of
+//                       Section 5.2: rows of h^-1(1) first, then h^-1(2), ...),
+//                       written as bucket-ordered {row start, length | sign}
+//                       and sigma*b, with the bucket starts.
+//   K4b k_apply_*       persistent warps take whole buckets from a counter and
+//                       add sigma(i) A_i into the bucket's row in ascending row
+//                       order (per-warp shared-memory copies summed in a fixed
+//                       order); the finished SA row is written once.  No
+//                       floating-point atomics: results are bitwise
+//                       reproducible.
 #include <algorithm>
 #include <vector>
 #include <cmath>
