@@ -836,14 +836,6 @@ def run_cw(args):
                        "nnz_per_s": nnz / (sk_ms / 1000.0), "traffic": ncu_traffic("k_apply_csr"),
                        "traffic_of": "k_apply_csr (the segmented sum)", "stages_ms": sk_stages}
     del SA, Sb
-    # the segmented sum reads each row's col and val as 64-byte segments at
-    # random places: its ceiling is the random segment read rate, not the copy
-    gc = gather_ceiling(cw, stream, device)
-    sketch_roofline["gather_ceiling"] = gc
-    if sk_stages.get("k_apply_csr"):
-        g = nnz * 8 / (sk_stages["k_apply_csr"] / 1000.0) / 1e9
-        sketch_roofline["apply_gather_GBps"] = g
-        sketch_roofline["apply_frac_of_random_64B"] = g / gc["random_64B_GBps"]
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -881,6 +873,15 @@ def run_cw(args):
                "d2h_bytes_per_step": d2h, "steps": esteps, "ms_per_step": ems / esteps,
                "call": "cw_lsqr_precond_host (page-locked host CSR and b, x back to host memory)"}
         del A_h, x_h, rp_h, col_h, val_h, b_h
+
+    # the segmented sum reads each row's col and val as 64-byte segments at
+    # random places: its ceiling is the random segment read rate, not the copy
+    gc = gather_ceiling(cw, stream, device)
+    sketch_roofline["gather_ceiling"] = gc
+    if sk_stages.get("k_apply_csr"):
+        g = nnz * 8 / (sk_stages["k_apply_csr"] / 1000.0) / 1e9
+        sketch_roofline["apply_gather_GBps"] = g
+        sketch_roofline["apply_frac_of_random_64B"] = g / gc["random_64B_GBps"]
 
     rows = None
     if rank == 0 and not args.no_rows:
