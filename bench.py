@@ -413,7 +413,7 @@ def _timed(fn, stream, reps=3, warm=1):
     return e0.elapsed_time(e1) / reps
 
 
-def gather_ceiling(cw, stream, device):
+def segment_read_rates(cw, stream, device):
     """Read throughput (GB/s) of 64-byte segments at random places of a 2 GiB
     array (larger than L2), issued like the segmented sum's row gathers, and of
     the same kernel on consecutive segments; the better of 4 and 8 CTAs per SM."""
@@ -875,9 +875,10 @@ def run_cw(args):
         del A_h, x_h, rp_h, col_h, val_h, b_h
 
     # the segmented sum reads each row's col and val as 64-byte segments at
-    # random places: its ceiling is the random segment read rate, not the copy
-    gc = gather_ceiling(cw, stream, device)
-    sketch_roofline["gather_ceiling"] = gc
+    # random places: the rate to compare it with is the random segment read
+    # rate, about half the copy rate
+    gc = segment_read_rates(cw, stream, device)
+    sketch_roofline["segment_read_rates"] = gc
     if sk_stages.get("k_apply_csr"):
         g = nnz * 8 / (sk_stages["k_apply_csr"] / 1000.0) / 1e9
         sketch_roofline["apply_gather_GBps"] = g

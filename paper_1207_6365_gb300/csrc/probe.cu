@@ -4,7 +4,7 @@
 // 4 bytes a lane, 16 segments per half-warp in flight, the 64-byte L2 fetch
 // size), and the same kernel on consecutive segments as its calibration.
 // The bucket-ordered sum reads each row's col and val as such segments, so
-// this rate, not the copy bandwidth, is the ceiling of that kernel.
+// its read rate belongs beside this one rather than beside the copy rate.
 #include <cstdint>
 
 #include "cw_common.cuh"
