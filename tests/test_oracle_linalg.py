@@ -214,3 +214,40 @@ def test_distortion_reported_in_band():
     R_A = np.linalg.qr(Ad, mode="r")
     sv = oracle.distortion(SA, R_A)
     assert 0.7 < sv.min() <= sv.max() < 1.3
+
+
+def test_distortion_identity_and_injective_sketch_are_isometries():
+    # S = I: SA R_A^-1 = Q has orthonormal columns, every singular value is 1.
+    # A hash without collisions makes S a signed row selection, S Q keeps
+    # orthonormal columns, so again all ones.  A transposed or lower-triangular
+    # R, or R in place of its inverse, breaks both.
+    rng = np.random.default_rng(5)
+    Ad = rng.standard_normal((60, 7)) @ np.diag([1.0, 3.0, 0.2, 10.0, 1.5, 0.5, 4.0])
+    R_A = np.linalg.qr(Ad, mode="r")
+    np.testing.assert_allclose(oracle.distortion(Ad, R_A), np.ones(7), rtol=0, atol=1e-12)
+    m = 1 << 20
+    for seed in range(1, 50):
+        h, _ = oracle.hash(seed, m, 0, Ad.shape[0])
+        if len(set(h.tolist())) == Ad.shape[0]:
+            break
+    else:
+        pytest.fail("no collision-free seed")
+    rp = np.arange(0, Ad.size + 1, Ad.shape[1], dtype=np.int32)
+    col = np.tile(np.arange(Ad.shape[1], dtype=np.int32), Ad.shape[0])
+    SA, _ = oracle.sketch_csr(rp, col, Ad.ravel().astype(np.float32), Ad.shape[1], None, m, seed=seed)
+    Af = Ad.astype(np.float32).astype(np.float64)
+    np.testing.assert_allclose(oracle.distortion(SA, np.linalg.qr(Af, mode="r")), np.ones(7), rtol=0, atol=1e-10)
+
+
+def test_distortion_equals_generalized_eigenvalues():
+    # The singular values of SA R_A^-1 squared are the eigenvalues of
+    # R_A^-T (SA^T SA) R_A^-1, i.e. the generalized eigenvalues of the pencil
+    # (SA^T SA, A^T A): a route with no triangular factor at all.
+    A, b, SA, _ = _problem(n=3000, d=6, m=64, seed=9)
+    Ad = A.to_dense().numpy().astype(np.float64)
+    R_A = np.linalg.qr(Ad, mode="r")
+    lam = sla.eigh(SA.T @ SA, Ad.T @ Ad, eigvals_only=True)
+    want = np.sort(np.sqrt(lam))[::-1]
+    got = oracle.distortion(SA, R_A)
+    np.testing.assert_allclose(got, want, rtol=1e-9)
+    assert got.max() > 1.05 and got.min() < 0.95   # m = 64 distorts visibly
