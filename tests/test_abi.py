@@ -92,6 +92,17 @@ def test_host_side_validation_rejects_bad_arguments():
                                ctypes.byref(it), ctypes.byref(ft), null) == -1
     assert lib.cw_leverage(ctypes.c_void_p(16), 100, 8, 8, 64, 1, 0, ctypes.c_void_p(16), ctypes.c_void_p(16),
                            null) == -2
+    # the segment read probe: pointers, a power-of-two segment count, 1..8 CTAs per SM
+    p16 = ctypes.c_void_p(16)
+    assert lib.cw_probe_gather64(null, 64, 64, 0, 4, p16, null) == -1
+    assert lib.cw_probe_gather64(p16, 64, 64, 0, 4, null, null) == -1
+    assert lib.cw_probe_gather64(p16, 48, 64, 0, 4, p16, null) == -2
+    assert lib.cw_probe_gather64(p16, 0, 64, 0, 4, p16, null) == -2
+    assert lib.cw_probe_gather64(p16, 64, -1, 0, 4, p16, null) == -2
+    assert lib.cw_probe_gather64(p16, 1 << 41, 64, 0, 4, p16, null) == -3
+    assert lib.cw_probe_gather64(p16, 64, 64, 0, 0, p16, null) == -1
+    assert lib.cw_probe_gather64(p16, 64, 64, 1, 9, p16, null) == -1
+    assert lib.cw_probe_gather64(p16, 64, 0, 0, 4, p16, null) == 0   # nothing to read: no launch
 
 
 def test_built_for_sm103a():
