@@ -233,6 +233,8 @@ class Selection:
 def select_or_fallback(sketch, selection_members, m, seed_P):
     """Keep the trained sketch only if its mean residual ratio on the selection
     members is below the plain sketch's; otherwise fall back to plain."""
+    if not selection_members:
+        raise ValueError("select_or_fallback needs at least one selection member")
     plain, learned = evaluate(sketch, selection_members)
     mp, ml = sum(plain) / len(plain), sum(learned) / len(learned)
     return Selection(sketch, ml < mp, m, seed_P, mp, ml)
