@@ -419,7 +419,8 @@ int cw_normal_solve(const double *G, int64_t d, double *x, double *r2, double *R
  * the range of A), and gx = dloss/dx = 2 G_AA (x - x*) / r2.  G as for
  * cw_normal_solve (its leading d x d block is used), xstar and r2 from that
  * call, x: d float64.  loss: one float64; gx: d float64 or NULL (device).
- * Requires 1 <= d <= 1024.  Asynchronous.
+ * r2 = 0 (b in the range of A) leaves the ratio undefined: loss and gx are
+ * then infinite or NaN.  Requires 1 <= d <= 1024.  Asynchronous.
  */
 int cw_excess_residual(const double *G, int64_t d, const double *xstar, const double *r2, const double *x,
                        double *loss, double *gx, cw_stream stream);
