@@ -432,6 +432,20 @@ def segment_read_rates(cw, stream, device):
     return res
 
 
+def with_sa_sketch(roofline, sketch_roofline):
+    """The dominant kernel's roofline with the SA sketch's own figures nested
+    under "sa_sketch" (cw_sketch_csr alone: time, achieved GB/s and fraction of
+    the copy peak on its algorithmic bytes, the segment read rates), so that a
+    record keeping only the line's standard keys keeps them too."""
+    if roofline is None or not sketch_roofline:
+        return roofline
+    keep = ("call", "ms", "achieved", "frac", "alg_bytes_per_call", "nnz_per_s", "traffic",
+            "segment_read_rates", "apply_gather_GBps", "apply_frac_of_random_64B")
+    out = dict(roofline)
+    out["sa_sketch"] = {k: sketch_roofline[k] for k in keep if k in sketch_roofline}
+    return out
+
+
 def _stage_ms(cw, names, reps):
     out = {}
     for nm in names:
@@ -932,7 +946,8 @@ def run_cw(args):
                            "n": n, "d": D, "nnz": nnz, "m": M, "rtol": RTOL,
                            "l2": "inputs (2.3 GB of CSR and b) larger than the 129 MB L2; no flush",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e, "clocks": clk,
+                "roofline": with_sa_sketch(roofline, sketch_roofline), "cpu_baseline": cpu_baseline, "e2e": e2e,
+                "clocks": clk,
                 "gpu_launches": int(launches_all), "lsqr_iters": iters[-1] if iters else None,
                 "sketch_roofline": sketch_roofline,
                 "cpu_baseline_all_cores": cpu_all,
